@@ -1,0 +1,335 @@
+"""Benchmark: matrix-free Helmholtz apply throughput (GDOF/s) on one GB300.
+
+Default workload: 32^3 curved hexahedra (periodic sine map), P = 4, Q = 6,
+FP64 fused Helmholtz apply (lambda = 1), coefficients uniform[-1,1] seed 0.
+A step is one Helmholtz apply over all elements (BwdTrans, collocation
+gradient, metric, transposed gradient and IProductWRTBase fused in one
+launch).  Throughput = elements x modes / time (the paper's DOF/s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nir|reference]
+                    [--workload NAME] [--prec f64|f32|bf16]
+
+Under torchrun each rank applies the operator to its own copy of the
+workload (element-parallel, no data-path collective: weak scaling); rank 0
+prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+L2_BYTES = 129 * 2 ** 20
+
+
+def helm_flops_per_elem(shape: str, N: int, Q: int) -> int:
+    """Algorithmic flops of one sum-factorised Helmholtz apply (hex: 3 contraction
+    stages each way, collocation gradient and its transpose, metric)."""
+    if shape == "hex":
+        return 4 * N * (N * N * Q + N * Q * Q + Q ** 3) + 12 * Q ** 4 + 20 * Q ** 3
+    raise ValueError("roofline accounting implemented for the hexahedral workloads")
+
+
+def helm_bytes_per_elem(shape: str, N: int, Q: int, wb: int, deformed: bool) -> int:
+    M = N ** 3
+    geo = 7 * Q ** 3 if deformed else 7
+    return 2 * M * wb + geo * wb
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "_fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "nir" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v: float, device=None) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, ws, rank):
+    """The FP64 oracle on a bounded sample of the workload, on the host cores."""
+    import oracle
+    if rank != 0:
+        return
+    wl = W.workload(args.workload)
+    shape, P, Q, g = wl["shape"], wl["P"], wl["Q"], wl["gorder"]
+    M = oracle.num_modes(shape, P)
+    k = args.sample
+    ids = W.sample_elements(wl["nodes"].shape[0], k, seed=0)
+    nodes = np.ascontiguousarray(wl["nodes"][ids])
+    u = W.coefficients(wl["nodes"].shape[0], M, seed=0)[ids]
+    for _ in range(args.warmup):
+        oracle.helmholtz(shape, P, Q, g, nodes, 1.0, u)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.helmholtz(shape, P, Q, g, nodes, 1.0, u)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = k * M / dt / 1e9
+    cores = oracle.threads()
+    line = {"impl": "reference", "metric": "Helmholtz apply GDOF/s", "value": v, "unit": "GDOF/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, wl),
+            "cpu_baseline": {"value": v, "unit": "GDOF/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{k} seeded elements of {wl['nodes'].shape[0]} per step"},
+            "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, wl):
+    E = wl["nodes"].shape[0]
+    return {"workload": args.workload, "shape": wl["shape"], "nelem": E, "P": wl["P"], "Q": wl["Q"],
+            "geometry": "curved (per-point factors)" if wl["deformed"] else "affine",
+            "lambda": 1.0, "precision": args.prec}
+
+
+def cpu_baseline(args, wl, budget_s: float = 15.0):
+    """Oracle timed on a bounded seeded sample (rank 0, N = 1 only)."""
+    import oracle
+    shape, P, Q, g = wl["shape"], wl["P"], wl["Q"], wl["gorder"]
+    M = oracle.num_modes(shape, P)
+    E = wl["nodes"].shape[0]
+    k = 64
+    u_all = W.coefficients(E, M, seed=0)
+    while True:
+        ids = W.sample_elements(E, k, seed=0)
+        t0 = time.perf_counter()
+        oracle.helmholtz(shape, P, Q, g, np.ascontiguousarray(wl["nodes"][ids]), 1.0, u_all[ids])
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or k >= E:
+            break
+        k = min(E, int(k * max(2.0, budget_s / 4 / max(dt, 1e-3))))
+    return {"value": k * M / dt / 1e9, "unit": "GDOF/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{k} seeded elements of {E}, one dense-matrix Helmholtz apply each"}
+
+
+def run_nir(args, ws, rank, local):
+    import torch
+    import paper_2606_20917_gb300 as nir
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ctx = nir.Context(local, stream)
+    wl = W.workload(args.workload)
+    shape, P, Q, g = wl["shape"], wl["P"], wl["Q"], wl["gorder"]
+    E = wl["nodes"].shape[0]
+    blk = nir.Block(ctx, shape, E, P, deformed=wl["deformed"])
+    blk.set_geometry(g, torch.from_numpy(wl["nodes"]).to(dev))
+    M = blk.M
+    dt_t = nir.DTYPE[args.prec]
+    u = torch.from_numpy(W.coefficients(E, M, seed=0)).to(dev, dt_t)
+    y = torch.empty_like(u)
+    wb = u.element_size()
+    work_bytes = E * M * wb * 2 + (E * Q ** 3 * 7 * wb if wl["deformed"] else 0)
+
+    for _ in range(args.warmup):
+        blk.helmholtz(u, lam=1.0, prec=args.prec, out=y)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_all0 = torch.cuda.Event(enable_timing=True)
+        t_all1 = torch.cuda.Event(enable_timing=True)
+        t_all0.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            blk.helmholtz(u, lam=1.0, prec=args.prec, out=y)
+            ev[k][1].record(stream)
+        t_all1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+    ms_total = t_all0.elapsed_time(t_all1)
+    ms_total = max_over_ranks(ws, ms_total, dev)
+    per_launch = [a.elapsed_time(b) for a, b in ev]
+    ms_step = ms_total / args.steps
+    dof = E * M
+    value = ws * dof * args.steps / (ms_total * 1e-3) / 1e9
+
+    # e2e: the same apply through the host-buffer C-ABI call (H2D + apply + D2H)
+    uh = u.cpu().pin_memory()
+    yh = torch.empty_like(uh).pin_memory()
+    for _ in range(2):
+        blk.helmholtz_host(uh, yh, lam=1.0, prec=args.prec)
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        blk.helmholtz_host(uh, yh, lam=1.0, prec=args.prec)
+    e2e_s = max_over_ranks(ws, (time.perf_counter() - t0) / args.steps, dev)
+    e2e = {"value": ws * dof / e2e_s / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": uh.numel() * wb,
+           "d2h_bytes_per_step": yh.numel() * wb}
+
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    avg_launch_s = statistics.mean(per_launch) * 1e-3
+    roof = None
+    if shape == "hex":
+        flops = helm_flops_per_elem(shape, P + 1, Q) * E
+        if args.prec == "f64":
+            fp64 = ctx.probe_fp64_peak()
+            roof = {"bound": "alu", "achieved": flops / avg_launch_s / 1e12, "peak": fp64, "unit": "TFLOP/s",
+                    "frac": flops / avg_launch_s / 1e12 / fp64, "traffic": None,
+                    "peak_source": "FP64 FMA throughput measured in this run by nir_probe_fp64_peak "
+                                   "(register-resident DFMA chains); nominal GB300 FP64 is 1.25 TFLOP/s",
+                    "flops_per_elem": flops // E,
+                    "hbm_gbs_at_this_rate": work_bytes / avg_launch_s / 1e9}
+        else:
+            gbs = work_bytes / avg_launch_s / 1e9
+            peak = peaks.get("hbm_gbs", 6800.0)
+            roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                    "traffic": None, "bytes_per_elem": work_bytes // E,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "_fallback" not in peaks else "fallback 6.8 TB/s"}
+    extras = {}
+    if args.extras and ws == 1:
+        for p in ("f32", "bf16"):
+            if p == args.prec:
+                continue
+            up = u.to(nir.DTYPE[p])
+            yp = torch.empty_like(up)
+            for _ in range(3):
+                blk.helmholtz(up, prec=p, out=yp)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            for _ in range(10):
+                blk.helmholtz(up, prec=p, out=yp)
+            b.record(stream)
+            torch.cuda.synchronize()
+            extras[f"{p}_apply_gdofs"] = dof / (a.elapsed_time(b) / 10 * 1e-3) / 1e9
+    line = {"metric": "Helmholtz apply GDOF/s", "value": value, "unit": "GDOF/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": dict(workload_config(args, wl),
+                           l2=f"no flush: {work_bytes / 2**20:.0f} MiB streamed per step > 129 MiB L2"),
+            "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk.summary(),
+            "kernel_ms_per_launch": statistics.mean(per_launch)}
+    if extras:
+        line["extras"] = extras
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, wl)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["nir", "reference"], default="nir")
+    ap.add_argument("--workload", default="hex32_curved_p4")
+    ap.add_argument("--prec", choices=["f64", "f32", "bf16"], default="f64")
+    ap.add_argument("--sample", type=int, default=256, help="reference arm: elements per step")
+    ap.add_argument("--extras", action="store_true", help="also time the FP32/BF16 applies")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_nir(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

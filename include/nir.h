@@ -1,0 +1,196 @@
+/*
+ * nir.h -- C ABI of the GB300 spectral/hp elemental-operator library.
+ *
+ * The library evaluates the matrix-free, sum-factorised elemental operators
+ * of the spectral/hp element method (Sec. 2.1-2.2 of the NektarIR paper,
+ * arXiv 2606.20917) on blocks of alike elements (Sec. 3.1, the `block` type):
+ * BwdTrans, IProductWRTBase, PhysDeriv, IProductWRTDerivBase, the mass
+ * operator and the weak Helmholtz operator H = L + lambda M
+ * (Eqs. weakmatrixhelm, laplacian), for quadrilaterals, triangles, hexahedra,
+ * prisms and tetrahedra, in FP64, FP32 and BF16 storage with FP32 arithmetic.
+ * On top of them it provides a hybrid mixed-shape/mixed-order mesh applied in
+ * one persistent launch and a conjugate-gradient Helmholtz solve with FP64
+ * iterative refinement around an FP32/BF16 operator.
+ *
+ * Conventions
+ *   - Every call returns NIR_OK (0) or a negative NIR_ERR_* code; nir_strerror
+ *     gives a message.  Invalid arguments are rejected before any GPU work.
+ *   - Array arguments of the operator calls are DEVICE pointers owned by the
+ *     caller (e.g. torch tensors' data_ptr()).  They must not alias each other.
+ *     Basis tables, geometric factors and scratch are owned by the library.
+ *   - Operator calls are asynchronous on the context's CUDA stream; errors of
+ *     the launch itself are returned, device-side errors surface at the next
+ *     synchronising call of the caller.
+ *   - P is the polynomial degree (N = P+1 modes per direction), Q the number of
+ *     quadrature points per direction; supported: 1 <= P <= 8, Q = P + 2.
+ *   - Layouts (element-major):
+ *       coefficients [E][M], modes packed p outermost, then q, then r, with
+ *         quad  q < N;            M = N^2
+ *         tri   q < N-p;          M = N(N+1)/2
+ *         hex   q, r < N;         M = N^3
+ *         prism q < N, r < N-p;   M = N^2(N+1)/2
+ *         tet   q < N-p, r < N-p-q; M = N(N+1)(N+2)/6     (Eq. bwdsumfactet bounds)
+ *       physical values [E][Nq], Nq = Q^d, point index i + Q*(j + Q*k), the
+ *         first direction (xi1 / eta1) fastest.
+ *   - Basis: modified C0 expansion (psiA, psiB, psiC of Sec. 2.2); collapsed
+ *     vertex/edge modes whose eta factor is not a polynomial in xi are defined
+ *     with that factor replaced by 1.
+ *   - Quadrature: Gauss-Lobatto-Legendre on quad/hex directions and the prism's
+ *     eta1, eta2; Gauss-Jacobi(alpha,0) on collapsed directions (tri eta1 a=0,
+ *     eta2 a=1; tet eta1 a=0, eta2 a=1, eta3 a=2; prism eta3 a=1), with the
+ *     collapse Jacobian absorbed in the weights.
+ */
+#ifndef NIR_H
+#define NIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { NIR_QUAD = 0, NIR_TRI = 1, NIR_HEX = 2, NIR_PRISM = 3, NIR_TET = 4 } nir_shape;
+
+/* Storage/arithmetic precision of an operator call.  NIR_BF16 stores
+ * coefficients, physical values and geometric factors in bfloat16 and computes
+ * in FP32. */
+typedef enum { NIR_F64 = 0, NIR_F32 = 1, NIR_BF16 = 2 } nir_prec;
+
+enum {
+    NIR_OK = 0,
+    NIR_ERR_INVALID_ARG = -1,   /* null/aliased pointer, bad size or enum */
+    NIR_ERR_UNSUPPORTED = -2,   /* shape/P/Q combination not compiled */
+    NIR_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+    NIR_ERR_NOT_CONVERGED = -4, /* CG hit its iteration cap or broke down */
+    NIR_ERR_NONFINITE = -5,     /* NaN/Inf met in a CG scalar */
+    NIR_ERR_NO_MEMORY = -6,     /* device or host allocation failed */
+    NIR_ERR_GEOMETRY = -7,      /* non-positive Jacobian determinant */
+    NIR_ERR_STATE = -8          /* geometry not set / object in wrong state */
+};
+
+typedef struct nir_ctx nir_ctx;
+typedef struct nir_block nir_block;
+typedef struct nir_mesh nir_mesh;
+
+/* A block: alike elements sharing shape, order, quadrature and deformation
+ * (Sec. 3.1, the block type's SEShape/Basis/Quadrature/Deformed/Size). */
+typedef struct {
+    int shape;       /* nir_shape */
+    int64_t nelem;   /* E >= 1 */
+    int P;           /* polynomial degree */
+    int Q;           /* quadrature points per direction (= P + 2) */
+    int deformed;    /* 1: per-point geometric factors; 0: the element maps are
+                        affine and quad/hex factors are stored once per element */
+} nir_block_desc;
+
+/* Create a context on CUDA device `device` issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out owns nothing of
+ * the caller.  Errors: INVALID_ARG, CUDA. */
+int nir_ctx_create(nir_ctx **out, int device, void *cuda_stream);
+/* Re-target subsequent calls of all blocks of this context to another stream. */
+int nir_ctx_set_stream(nir_ctx *ctx, void *cuda_stream);
+void nir_ctx_destroy(nir_ctx *ctx);
+
+/* Create a block; builds the FP64 basis/quadrature tables (Eqs. basis matrix,
+ * bwdsumfachex, bwdsumfactet, stdderiv) and uploads them.  Errors:
+ * INVALID_ARG, UNSUPPORTED, NO_MEMORY, CUDA. */
+int nir_block_create(nir_ctx *ctx, const nir_block_desc *desc, nir_block **out);
+void nir_block_destroy(nir_block *blk);
+/* M (modes per element, Sec. 3.1 storage size) and Nq (points per element). */
+int nir_block_num_modes(const nir_block *blk, int64_t *M);
+int nir_block_num_points(const nir_block *blk, int64_t *Nq);
+/* Reference coordinates of the quadrature points: eta_out [Nq][d] (collapsed
+ * coordinates) and xi_out [Nq][d] (standard element, Eq. eta-space); HOST
+ * pointers, either may be NULL. */
+int nir_block_points(const nir_block *blk, double *eta_out, double *xi_out);
+
+/* Geometry (Sec. 2.1: the weights matrix W and Lambda(d xi/d x)).  `nodes` is
+ * a DEVICE FP64 array, read during the call only:
+ *   quad/hex: [E][(g+1)^d][d] coordinates of an equispaced lattice of degree
+ *             g = gorder per direction (node a + (g+1)(b + (g+1) c) at
+ *             xi = -1 + 2(a,b,c)/g); the element map is its Lagrange interpolant.
+ *   tri/tet/prism: gorder = 1, vertices [E][nv][d] in the order
+ *             tri (-1,-1),(1,-1),(-1,1); tet (-1,-1,-1),(1,-1,-1),(-1,1,-1),(-1,-1,1);
+ *             prism (-1,-1,-1),(1,-1,-1),(1,1,-1),(-1,1,-1),(-1,-1,1),(-1,1,1).
+ * The library computes, in FP64 on the GPU, per point (or per element for an
+ * undeformed quad/hex block) the Jacobian, W = w|J|, d eta/d x and the metric
+ * G = W (d eta/d x)(d eta/d x)^T, and derives FP32/BF16 copies on first use.
+ * Synchronises the context stream.  Errors: INVALID_ARG, GEOMETRY (some
+ * det J <= 0 or non-finite), NO_MEMORY, CUDA. */
+int nir_block_set_geometry(nir_block *blk, int gorder, const double *nodes);
+
+/* BwdTrans u = B u_hat (Eqs. bwdstd, bwdsumfachex, bwdsumfactet).
+ * coeff [E][M] -> phys [E][Nq]. */
+int nir_bwd_trans(nir_block *blk, int prec, const void *coeff, void *phys);
+/* IProductWRTBase u_hat = B^T W u (Eqs. iprodhex, iprodtet).
+ * phys [E][Nq] -> coeff [E][M]. */
+int nir_iproduct_wrt_base(nir_block *blk, int prec, const void *phys, void *coeff);
+/* PhysDeriv du/dx_l = sum_j Lambda(d eta_j/d x_l) D_eta_j u (Eqs. physderiv,
+ * stdderiv).  phys [E][Nq] -> d0, d1 (, d2) [E][Nq]; d2 must be NULL in 2-D. */
+int nir_phys_deriv(nir_block *blk, int prec, const void *phys, void *d0, void *d1, void *d2);
+/* IProductWRTDerivBase: coeff = sum_l (D_xl B)^T W f_l (the test_grad
+ * operation, Sec. 3.1).  f0, f1 (, f2) [E][Nq] -> coeff [E][M]. */
+int nir_iproduct_wrt_deriv_base(nir_block *blk, int prec, const void *f0, const void *f1,
+                                const void *f2, void *coeff);
+/* Mass operator M u_hat = B^T W B u_hat (Eq. laplacian). [E][M] -> [E][M]. */
+int nir_mass(nir_block *blk, int prec, const void *coeff_in, void *coeff_out);
+/* Helmholtz operator (L + lambda M) u_hat (Eqs. weakmatrixhelm, laplacian),
+ * one fused launch.  [E][M] -> [E][M]; lambda > 0 for an SPD operator. */
+int nir_helmholtz(nir_block *blk, int prec, double lambda, const void *coeff_in, void *coeff_out);
+/* nir_helmholtz on HOST buffers: copies h_in to the device, applies, copies
+ * the result to h_out, and synchronises.  Pinned host memory gives full
+ * copy bandwidth.  Device staging buffers are library-owned. */
+int nir_helmholtz_host(nir_block *blk, int prec, double lambda, const void *h_in, void *h_out);
+
+/* Hybrid mesh: the concatenation of blocks (each with geometry set), applied
+ * by one persistent launch (Sec. 2.2: operators batched over blocks of alike
+ * elements).  Vectors are the concatenation of the blocks' coefficient arrays
+ * in block order.  The mesh keeps pointers to the blocks, which must outlive it. */
+int nir_mesh_create(nir_ctx *ctx, nir_block *const *blocks, int nblocks, nir_mesh **out);
+void nir_mesh_destroy(nir_mesh *mesh);
+int nir_mesh_num_dofs(const nir_mesh *mesh, int64_t *ndof);
+/* Helmholtz apply over all blocks in one persistent kernel launch, replayed
+ * from a CUDA graph captured on first use for each (prec, buffers) pair. */
+int nir_mesh_helmholtz(nir_mesh *mesh, int prec, double lambda, const void *in, void *out);
+/* Autotune elements-per-CTA and grid size of every (shape, P, prec) of the mesh
+ * by timing candidates; reads/writes a JSON cache when cache_path != NULL. */
+int nir_tune(nir_mesh *mesh, const char *cache_path);
+
+typedef struct {
+    int inner_prec;        /* nir_prec of the operator inside CG (F64: plain CG) */
+    double tol;            /* target ||b - H x|| / ||b|| (FP64 residual) */
+    int max_outer;         /* refinement sweeps (ignored for plain FP64 CG) */
+    int max_inner;         /* CG iterations per sweep (total for plain CG) */
+    double inner_tol;      /* relative residual reduction per refinement sweep */
+    int jacobi;            /* 1: diagonal (Jacobi) preconditioner */
+} nir_cg_opts;
+
+typedef struct {
+    int outer;             /* refinement sweeps done */
+    int inner_total;       /* operator applies in the inner solver */
+    double rel_residual;   /* final ||b - H x|| / ||b|| in FP64 */
+    double seconds;        /* wall time of the solve */
+} nir_cg_stats;
+
+/* Solve (L + lambda M) x = b on the mesh's broken (element-block-diagonal)
+ * operator.  b, x: DEVICE FP64 [ndof]; x holds the initial guess on entry.
+ * Plain CG when inner_prec == NIR_F64; otherwise CG in inner_prec on the
+ * defect equation inside FP64 iterative refinement.  Residuals, dot products
+ * and the refinement update are FP64 on the GPU.  Synchronous.  Errors:
+ * INVALID_ARG, NOT_CONVERGED, NONFINITE, CUDA, NO_MEMORY. */
+int nir_cg_solve(nir_mesh *mesh, double lambda, const double *b, double *x, const nir_cg_opts *opts,
+                 nir_cg_stats *stats);
+
+/* Measure the FP64 FMA throughput of the device (TFLOP/s) with a register-
+ * resident DFMA loop; used as the FP64 roofline ceiling. Synchronous. */
+int nir_probe_fp64_peak(nir_ctx *ctx, double *tflops);
+
+const char *nir_strerror(int code);
+/* Library version string. */
+const char *nir_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NIR_H */

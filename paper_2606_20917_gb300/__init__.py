@@ -1,0 +1,299 @@
+"""Python binding of the GB300 spectral/hp elemental-operator library (libnir.so).
+
+Argument marshalling only: every operator runs in the library's CUDA kernels.
+PyTorch provides device memory and the stream; tensors are passed by
+``data_ptr()``.  There is no CPU fallback: importing this package without a
+built ``libnir.so`` raises.
+
+    ctx = Context()                                   # device 0, current torch stream
+    blk = Block(ctx, "hex", nelem, P=4, deformed=True)
+    blk.set_geometry(gorder, nodes_f64_cuda)          # [E][(g+1)^3][3]
+    y = blk.helmholtz(u, lam=1.0)                     # u: [E][M] cuda tensor
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnir.so")
+SHAPES = {"quad": 0, "tri": 1, "hex": 2, "prism": 3, "tet": 4}
+DIM = {"quad": 2, "tri": 2, "hex": 3, "prism": 3, "tet": 3}
+PREC = {"f64": 0, "f32": 1, "bf16": 2}
+DTYPE = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: run `python paper_2606_20917_gb300/build.py` "
+                      "(the library has no CPU fallback)")
+
+_lib = C.CDLL(LIB_PATH)
+_vp, _i, _d, _i64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+
+
+class BlockDesc(C.Structure):
+    _fields_ = [("shape", C.c_int), ("nelem", C.c_int64), ("P", C.c_int), ("Q", C.c_int),
+                ("deformed", C.c_int)]
+
+
+class CGOpts(C.Structure):
+    _fields_ = [("inner_prec", C.c_int), ("tol", C.c_double), ("max_outer", C.c_int),
+                ("max_inner", C.c_int), ("inner_tol", C.c_double), ("jacobi", C.c_int)]
+
+
+class CGStats(C.Structure):
+    _fields_ = [("outer", C.c_int), ("inner_total", C.c_int), ("rel_residual", C.c_double),
+                ("seconds", C.c_double)]
+
+
+_SIGS = {
+    "nir_ctx_create": [C.POINTER(_vp), _i, _vp],
+    "nir_ctx_set_stream": [_vp, _vp],
+    "nir_block_create": [_vp, C.POINTER(BlockDesc), C.POINTER(_vp)],
+    "nir_block_num_modes": [_vp, C.POINTER(_i64)],
+    "nir_block_num_points": [_vp, C.POINTER(_i64)],
+    "nir_block_points": [_vp, _vp, _vp],
+    "nir_block_set_geometry": [_vp, _i, _vp],
+    "nir_bwd_trans": [_vp, _i, _vp, _vp],
+    "nir_iproduct_wrt_base": [_vp, _i, _vp, _vp],
+    "nir_phys_deriv": [_vp, _i, _vp, _vp, _vp, _vp],
+    "nir_iproduct_wrt_deriv_base": [_vp, _i, _vp, _vp, _vp, _vp],
+    "nir_mass": [_vp, _i, _vp, _vp],
+    "nir_helmholtz": [_vp, _i, _d, _vp, _vp],
+    "nir_helmholtz_host": [_vp, _i, _d, _vp, _vp],
+    "nir_mesh_create": [_vp, C.POINTER(_vp), _i, C.POINTER(_vp)],
+    "nir_mesh_num_dofs": [_vp, C.POINTER(_i64)],
+    "nir_mesh_helmholtz": [_vp, _i, _d, _vp, _vp],
+    "nir_tune": [_vp, C.c_char_p],
+    "nir_cg_solve": [_vp, _d, _vp, _vp, C.POINTER(CGOpts), C.POINTER(CGStats)],
+    "nir_probe_fp64_peak": [_vp, C.POINTER(_d)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _i
+for _name in ("nir_ctx_destroy", "nir_block_destroy", "nir_mesh_destroy"):
+    getattr(_lib, _name).argtypes = [_vp]
+    getattr(_lib, _name).restype = None
+_lib.nir_strerror.argtypes = [_i]
+_lib.nir_strerror.restype = C.c_char_p
+_lib.nir_version.restype = C.c_char_p
+
+
+class NirError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {_lib.nir_strerror(code).decode()} ({code})")
+        self.code = code
+
+
+def _chk(rc: int, what: str):
+    if rc != 0:
+        raise NirError(rc, what)
+
+
+def lib():
+    return _lib
+
+
+def version() -> str:
+    return _lib.nir_version().decode()
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A device plus the CUDA stream every call is issued on."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.device = device
+        with torch.cuda.device(device):
+            h = _vp()
+            _chk(_lib.nir_ctx_create(C.byref(h), device, _stream_handle(stream)), "nir_ctx_create")
+        self.h = h
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        _chk(_lib.nir_ctx_set_stream(self.h, _stream_handle(stream)), "nir_ctx_set_stream")
+
+    def probe_fp64_peak(self) -> float:
+        v = _d()
+        _chk(_lib.nir_probe_fp64_peak(self.h, C.byref(v)), "nir_probe_fp64_peak")
+        return v.value
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            _lib.nir_ctx_destroy(h)
+            self.h = None
+
+
+class Block:
+    """A block of alike elements (shape, P, Q = P + 2, deformed flag)."""
+
+    def __init__(self, ctx: Context, shape: str, nelem: int, P: int, Q: int | None = None,
+                 deformed: bool = False):
+        self.ctx, self.shape, self.nelem, self.P = ctx, shape, int(nelem), int(P)
+        self.Q = int(P) + 2 if Q is None else int(Q)
+        self.dim = DIM[shape]
+        d = BlockDesc(SHAPES[shape], self.nelem, self.P, self.Q, int(bool(deformed)))
+        h = _vp()
+        _chk(_lib.nir_block_create(ctx.h, C.byref(d), C.byref(h)), "nir_block_create")
+        self.h = h
+        m, n = _i64(), _i64()
+        _chk(_lib.nir_block_num_modes(h, C.byref(m)), "num_modes")
+        _chk(_lib.nir_block_num_points(h, C.byref(n)), "num_points")
+        self.M, self.NQ = m.value, n.value
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            _lib.nir_block_destroy(h)
+            self.h = None
+
+    def points(self):
+        import numpy as np
+        eta = np.zeros((self.NQ, self.dim))
+        xi = np.zeros((self.NQ, self.dim))
+        _chk(_lib.nir_block_points(self.h, eta.ctypes.data_as(_vp), xi.ctypes.data_as(_vp)), "points")
+        return eta, xi
+
+    def set_geometry(self, gorder: int, nodes: torch.Tensor):
+        nodes = self._dev(nodes, torch.float64, "nodes")
+        if self.shape in ("quad", "hex"):
+            npe = (int(gorder) + 1) ** self.dim
+        else:
+            npe = {"tri": 3, "tet": 4, "prism": 6}[self.shape]
+        if nodes.numel() != self.nelem * npe * self.dim:
+            raise ValueError(f"nodes must be [{self.nelem}][{npe}][{self.dim}]")
+        _chk(_lib.nir_block_set_geometry(self.h, int(gorder), _ptr(nodes)), "nir_block_set_geometry")
+
+    # -- helpers
+    def _dev(self, t, dtype, name):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return t
+
+    def _chk_shape(self, t, n, name):
+        if t.numel() != self.nelem * n:
+            raise ValueError(f"{name} must hold {self.nelem} x {n} values")
+
+    def _out(self, n, prec, out):
+        if out is None:
+            return torch.empty((self.nelem, n), dtype=DTYPE[prec], device=f"cuda:{self.ctx.device}")
+        self._dev(out, DTYPE[prec], "out")
+        self._chk_shape(out, n, "out")
+        return out
+
+    # -- operators
+    def bwd_trans(self, coeff, prec="f64", out=None):
+        self._dev(coeff, DTYPE[prec], "coeff"); self._chk_shape(coeff, self.M, "coeff")
+        out = self._out(self.NQ, prec, out)
+        _chk(_lib.nir_bwd_trans(self.h, PREC[prec], _ptr(coeff), _ptr(out)), "nir_bwd_trans")
+        return out
+
+    def iproduct_wrt_base(self, phys, prec="f64", out=None):
+        self._dev(phys, DTYPE[prec], "phys"); self._chk_shape(phys, self.NQ, "phys")
+        out = self._out(self.M, prec, out)
+        _chk(_lib.nir_iproduct_wrt_base(self.h, PREC[prec], _ptr(phys), _ptr(out)), "nir_iproduct_wrt_base")
+        return out
+
+    def phys_deriv(self, phys, prec="f64", outs=None):
+        self._dev(phys, DTYPE[prec], "phys"); self._chk_shape(phys, self.NQ, "phys")
+        outs = outs or [self._out(self.NQ, prec, None) for _ in range(self.dim)]
+        for o in outs:
+            self._dev(o, DTYPE[prec], "out"); self._chk_shape(o, self.NQ, "out")
+        d2 = _ptr(outs[2]) if self.dim == 3 else None
+        _chk(_lib.nir_phys_deriv(self.h, PREC[prec], _ptr(phys), _ptr(outs[0]), _ptr(outs[1]), d2),
+             "nir_phys_deriv")
+        return outs
+
+    def iproduct_wrt_deriv_base(self, fields, prec="f64", out=None):
+        if len(fields) != self.dim:
+            raise ValueError(f"need {self.dim} fields")
+        for f in fields:
+            self._dev(f, DTYPE[prec], "field"); self._chk_shape(f, self.NQ, "field")
+        out = self._out(self.M, prec, out)
+        f2 = _ptr(fields[2]) if self.dim == 3 else None
+        _chk(_lib.nir_iproduct_wrt_deriv_base(self.h, PREC[prec], _ptr(fields[0]), _ptr(fields[1]), f2,
+                                              _ptr(out)), "nir_iproduct_wrt_deriv_base")
+        return out
+
+    def mass(self, coeff, prec="f64", out=None):
+        self._dev(coeff, DTYPE[prec], "coeff"); self._chk_shape(coeff, self.M, "coeff")
+        out = self._out(self.M, prec, out)
+        _chk(_lib.nir_mass(self.h, PREC[prec], _ptr(coeff), _ptr(out)), "nir_mass")
+        return out
+
+    def helmholtz(self, coeff, lam=1.0, prec="f64", out=None):
+        self._dev(coeff, DTYPE[prec], "coeff"); self._chk_shape(coeff, self.M, "coeff")
+        out = self._out(self.M, prec, out)
+        _chk(_lib.nir_helmholtz(self.h, PREC[prec], float(lam), _ptr(coeff), _ptr(out)), "nir_helmholtz")
+        return out
+
+    def helmholtz_host(self, coeff_host, out_host, lam=1.0, prec="f64"):
+        """Helmholtz on host tensors (pinned for full bandwidth); synchronous."""
+        for t in (coeff_host, out_host):
+            if t.is_cuda or t.dtype != DTYPE[prec] or not t.is_contiguous():
+                raise TypeError("host tensors of the precision's dtype expected")
+            self._chk_shape(t, self.M, "host tensor")
+        _chk(_lib.nir_helmholtz_host(self.h, PREC[prec], float(lam), _ptr(coeff_host), _ptr(out_host)),
+             "nir_helmholtz_host")
+        return out_host
+
+
+class Mesh:
+    """Hybrid mesh over several blocks (concatenated coefficient vectors)."""
+
+    def __init__(self, ctx: Context, blocks: list[Block]):
+        self.ctx, self.blocks = ctx, list(blocks)
+        arr = (_vp * len(blocks))(*[b.h for b in blocks])
+        h = _vp()
+        _chk(_lib.nir_mesh_create(ctx.h, arr, len(blocks), C.byref(h)), "nir_mesh_create")
+        self.h = h
+        n = _i64()
+        _chk(_lib.nir_mesh_num_dofs(h, C.byref(n)), "nir_mesh_num_dofs")
+        self.ndof = n.value
+        self.offsets = []
+        o = 0
+        for b in blocks:
+            self.offsets.append(o)
+            o += b.nelem * b.M
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            _lib.nir_mesh_destroy(h)
+            self.h = None
+
+    def helmholtz(self, x, lam=1.0, prec="f64", out=None):
+        if x.numel() != self.ndof or x.dtype != DTYPE[prec] or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous CUDA vector of the mesh's dofs")
+        out = torch.empty_like(x) if out is None else out
+        _chk(_lib.nir_mesh_helmholtz(self.h, PREC[prec], float(lam), _ptr(x), _ptr(out)), "nir_mesh_helmholtz")
+        return out
+
+    def tune(self, cache_path: str | None = None):
+        _chk(_lib.nir_tune(self.h, None if cache_path is None else cache_path.encode()), "nir_tune")
+
+    def cg_solve(self, b, x, lam=1.0, inner_prec="f32", tol=1e-10, max_outer=50, max_inner=2000,
+                 inner_tol=1e-4, jacobi=True):
+        for t in (b, x):
+            if t.dtype != torch.float64 or not t.is_cuda or t.numel() != self.ndof:
+                raise ValueError("b and x must be FP64 CUDA vectors of the mesh's dofs")
+        o = CGOpts(PREC[inner_prec], float(tol), int(max_outer), int(max_inner), float(inner_tol), int(jacobi))
+        s = CGStats()
+        rc = _lib.nir_cg_solve(self.h, float(lam), _ptr(b), _ptr(x), C.byref(o), C.byref(s))
+        return rc, dict(outer=s.outer, inner_total=s.inner_total, rel_residual=s.rel_residual,
+                        seconds=s.seconds)

@@ -1,0 +1,483 @@
+// nir_api.cu -- C ABI: contexts, blocks, geometry set-up, operator dispatch,
+// the host-buffer Helmholtz entry point and the FP64 peak probe.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nir_basis.h"
+#include "nir_geom.h"
+#include "nir_internal.h"
+#include "nir_kernels.cuh"
+#include "nir_layout.h"
+
+// --------------------------------------------------------------------------- registry
+#define NIR_DECL(s, p) KInfo nir_kinfo_s##s##_p##p(int P, int op);
+NIR_DECL(0, 0) NIR_DECL(0, 1) NIR_DECL(0, 2)
+NIR_DECL(1, 0) NIR_DECL(1, 1) NIR_DECL(1, 2)
+NIR_DECL(2, 0) NIR_DECL(2, 1) NIR_DECL(2, 2)
+NIR_DECL(3, 0) NIR_DECL(3, 1) NIR_DECL(3, 2)
+NIR_DECL(4, 0) NIR_DECL(4, 1) NIR_DECL(4, 2)
+#undef NIR_DECL
+
+KInfo nir_kinfo(int shape, int P, int prec, int op)
+{
+    typedef KInfo (*F)(int, int);
+    static const F tab[5][3] = {
+        {nir_kinfo_s0_p0, nir_kinfo_s0_p1, nir_kinfo_s0_p2}, {nir_kinfo_s1_p0, nir_kinfo_s1_p1, nir_kinfo_s1_p2},
+        {nir_kinfo_s2_p0, nir_kinfo_s2_p1, nir_kinfo_s2_p2}, {nir_kinfo_s3_p0, nir_kinfo_s3_p1, nir_kinfo_s3_p2},
+        {nir_kinfo_s4_p0, nir_kinfo_s4_p1, nir_kinfo_s4_p2}};
+    if (shape < 0 || shape > 4 || prec < 0 || prec > 2) return KInfo{};
+    return tab[shape][prec](P, op);
+}
+
+size_t nir_prec_size(int prec) { return prec == NIR_F64 ? 8 : prec == NIR_F32 ? 4 : 2; }
+
+int nir_occupancy(nir_ctx *ctx, const KInfo &ki)
+{
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->occupancy.find(ki.fn);
+    if (it != ctx->occupancy.end()) return it->second;
+    if (ki.smem > 48 * 1024) {
+        if (cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ki.smem) != cudaSuccess)
+            return -1;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ki.fn, ki.nt, ki.smem) != cudaSuccess) return -1;
+    if (n < 1) n = 1;
+    ctx->occupancy[ki.fn] = n;
+    return n;
+}
+
+// --------------------------------------------------------------------------- helpers
+namespace {
+
+bool valid_prec(int p) { return p == NIR_F64 || p == NIR_F32 || p == NIR_BF16; }
+
+template <class T>
+void dfree(T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+int ensure_lowp(nir_block *b, int prec)
+{
+    if (prec == NIR_F64 || !b->geo_set) return NIR_OK;
+    const size_t ng = (size_t)(b->geo_pp ? b->epad * b->NQ : b->epad) * b->ng;
+    const size_t nl = (size_t)(b->geo_pp ? b->epad * b->NQ : b->epad) * b->nl;
+    cudaStream_t st = b->ctx->stream;
+    if (prec == NIR_F32 && !b->G32) {
+        if (cudaMalloc(&b->G32, ng * 4) != cudaSuccess || cudaMalloc(&b->L32, nl * 4) != cudaSuccess)
+            return NIR_ERR_NO_MEMORY;
+        if (nir_convert_launch(b->G64, b->G32, nullptr, (long long)ng, st)) return NIR_ERR_CUDA;
+        if (nir_convert_launch(b->L64, b->L32, nullptr, (long long)nl, st)) return NIR_ERR_CUDA;
+    }
+    if (prec == NIR_BF16 && !b->G16) {
+        if (cudaMalloc(&b->G16, ng * 2) != cudaSuccess || cudaMalloc(&b->L16, nl * 2) != cudaSuccess)
+            return NIR_ERR_NO_MEMORY;
+        if (nir_convert_launch(b->G64, nullptr, b->G16, (long long)ng, st)) return NIR_ERR_CUDA;
+        if (nir_convert_launch(b->L64, nullptr, b->L16, (long long)nl, st)) return NIR_ERR_CUDA;
+    }
+    return NIR_OK;
+}
+
+}  // namespace
+
+const void *nir_geo_ptr(nir_block *b, int prec, bool lam)
+{
+    if (prec == NIR_F64) return lam ? (const void *)b->L64 : (const void *)b->G64;
+    if (prec == NIR_F32) return lam ? (const void *)b->L32 : (const void *)b->G32;
+    return lam ? b->L16 : b->G16;
+}
+
+const void *nir_tab_ptr(nir_block *b, int prec) { return prec == NIR_F64 ? (const void *)b->tab64 : (const void *)b->tab32; }
+
+int nir_launch_op(nir_block *b, int prec, int op, double lambda, const void *in0, const void *in1, const void *in2,
+                  void *out0, void *out1, void *out2, cudaStream_t stream, int grid_override)
+{
+    KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, op);
+    if (!ki.fn) return NIR_ERR_UNSUPPORTED;
+    int rc = ensure_lowp(b, prec);
+    if (rc) return rc;
+    int occ = nir_occupancy(b->ctx, ki);
+    if (occ < 0) return NIR_ERR_CUDA;
+    const long long groups = (b->d.nelem + ki.epb - 1) / ki.epb;
+    long long grid = (long long)occ * b->ctx->num_sms;
+    if (grid_override > 0) grid = grid_override;
+    if (grid > groups) grid = groups;
+    nirk::KArgs a;
+    a.in0 = in0; a.in1 = in1; a.in2 = in2;
+    a.out0 = out0; a.out1 = out1; a.out2 = out2;
+    const bool lam = (op == nirk::OP_PHYSDERIV || op == nirk::OP_IPROD_DERIV);
+    a.geo = nir_geo_ptr(b, prec, lam);
+    a.tab = nir_tab_ptr(b, prec);
+    a.nelem = b->d.nelem;
+    a.lambda = lambda;
+    a.geo_pp = b->geo_pp;
+    a.pad = 0;
+    void *args[] = {&a};
+    if (cudaLaunchKernel(ki.fn, dim3((unsigned)grid), dim3(ki.nt), args, (size_t)ki.smem, stream) != cudaSuccess)
+        return NIR_ERR_CUDA;
+    return NIR_OK;
+}
+
+// --------------------------------------------------------------------------- context
+extern "C" int nir_ctx_create(nir_ctx **out, int device, void *stream)
+{
+    if (!out) return NIR_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return NIR_ERR_INVALID_ARG;
+    NIR_CUDA_TRY(cudaSetDevice(device));
+    nir_ctx *c = new (std::nothrow) nir_ctx();
+    if (!c) return NIR_ERR_NO_MEMORY;
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return NIR_ERR_CUDA;
+    }
+    *out = c;
+    return NIR_OK;
+}
+
+extern "C" int nir_ctx_set_stream(nir_ctx *ctx, void *stream)
+{
+    if (!ctx) return NIR_ERR_INVALID_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return NIR_OK;
+}
+
+extern "C" void nir_ctx_destroy(nir_ctx *ctx) { delete ctx; }
+
+// --------------------------------------------------------------------------- blocks
+extern "C" int nir_block_create(nir_ctx *ctx, const nir_block_desc *d, nir_block **out)
+{
+    if (!ctx || !d || !out) return NIR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (d->shape < NIR_QUAD || d->shape > NIR_TET || d->nelem < 1) return NIR_ERR_INVALID_ARG;
+    if (d->P < 1 || d->P > 8 || d->Q != d->P + 2) return NIR_ERR_UNSUPPORTED;
+    nir_block *b = new (std::nothrow) nir_block();
+    if (!b) return NIR_ERR_NO_MEMORY;
+    b->ctx = ctx;
+    b->d = *d;
+    b->dim = nirk::dim(d->shape);
+    b->N = d->P + 1;
+    b->M = nirk::nmodes(d->shape, b->N);
+    b->NQ = nirk::npts(d->shape, d->Q);
+    b->ng = nirk::ngeo(d->shape);
+    b->nl = nirk::nlam(d->shape);
+    b->epad = ((d->nelem + 63) / 64) * 64;
+    b->geo_pp = (d->deformed || d->shape == NIR_TRI || d->shape == NIR_TET || d->shape == NIR_PRISM) ? 1 : 0;
+    const int ntab = nirb_table_size(d->shape, d->P, d->Q);
+    b->tab_h.assign(ntab, 0.0);
+    if (!nirb_build_tables(d->shape, d->P, d->Q, b->tab_h.data())) {
+        delete b;
+        return NIR_ERR_CUDA;
+    }
+    std::vector<float> t32(ntab);
+    for (int i = 0; i < ntab; ++i) t32[i] = (float)b->tab_h[i];
+    if (cudaSetDevice(ctx->device) != cudaSuccess || cudaMalloc(&b->tab64, ntab * 8) != cudaSuccess ||
+        cudaMalloc(&b->tab32, ntab * 4) != cudaSuccess) {
+        nir_block_destroy(b);
+        return NIR_ERR_NO_MEMORY;
+    }
+    if (cudaMemcpy(b->tab64, b->tab_h.data(), ntab * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->tab32, t32.data(), ntab * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        nir_block_destroy(b);
+        return NIR_ERR_CUDA;
+    }
+    *out = b;
+    return NIR_OK;
+}
+
+extern "C" void nir_block_destroy(nir_block *b)
+{
+    if (!b) return;
+    dfree(b->tab64); dfree(b->tab32);
+    dfree(b->G64); dfree(b->L64); dfree(b->G32); dfree(b->L32);
+    if (b->G16) cudaFree(b->G16);
+    if (b->L16) cudaFree(b->L16);
+    if (b->stage_in) cudaFree(b->stage_in);
+    if (b->stage_out) cudaFree(b->stage_out);
+    delete b;
+}
+
+extern "C" int nir_block_num_modes(const nir_block *b, int64_t *M)
+{
+    if (!b || !M) return NIR_ERR_INVALID_ARG;
+    *M = b->M;
+    return NIR_OK;
+}
+
+extern "C" int nir_block_num_points(const nir_block *b, int64_t *Nq)
+{
+    if (!b || !Nq) return NIR_ERR_INVALID_ARG;
+    *Nq = b->NQ;
+    return NIR_OK;
+}
+
+extern "C" int nir_block_points(const nir_block *b, double *eta, double *xi)
+{
+    if (!b) return NIR_ERR_INVALID_ARG;
+    const int Q = b->d.Q, d = b->dim;
+    std::vector<double> z(3 * Q), w(3 * Q);
+    if (!nirb_shape_rules(b->d.shape, Q, z.data(), w.data())) return NIR_ERR_CUDA;
+    for (int n = 0; n < b->NQ; ++n) {
+        const int ii[3] = {n % Q, (n / Q) % Q, n / (Q * Q)};
+        double e[3] = {0, 0, 0}, x[3] = {0, 0, 0};
+        for (int c = 0; c < d; ++c) e[c] = z[c * Q + ii[c]];
+        switch (b->d.shape) {
+        case NIR_TRI: x[0] = 0.5 * (1 + e[0]) * (1 - e[1]) - 1; x[1] = e[1]; break;
+        case NIR_PRISM: x[0] = 0.5 * (1 + e[0]) * (1 - e[2]) - 1; x[1] = e[1]; x[2] = e[2]; break;
+        case NIR_TET:
+            x[0] = 0.25 * (1 + e[0]) * (1 - e[1]) * (1 - e[2]) - 1;
+            x[1] = 0.5 * (1 + e[1]) * (1 - e[2]) - 1;
+            x[2] = e[2];
+            break;
+        default: for (int c = 0; c < d; ++c) x[c] = e[c];
+        }
+        for (int c = 0; c < d; ++c) {
+            if (eta) eta[n * d + c] = e[c];
+            if (xi) xi[n * d + c] = x[c];
+        }
+    }
+    return NIR_OK;
+}
+
+extern "C" int nir_block_set_geometry(nir_block *b, int gorder, const double *nodes)
+{
+    if (!b || !nodes) return NIR_ERR_INVALID_ARG;
+    const int shape = b->d.shape, Q = b->d.Q, d = b->dim;
+    const bool tensor = (shape == NIR_QUAD || shape == NIR_HEX);
+    if (tensor ? (gorder < 1 || gorder > 12) : gorder != 1) return NIR_ERR_INVALID_ARG;
+    NIR_CUDA_TRY(cudaSetDevice(b->ctx->device));
+    cudaStream_t st = b->ctx->stream;
+    // host tables: per-direction points, weights, lattice Lagrange tables
+    std::vector<double> z(3 * Q), w(3 * Q);
+    if (!nirb_shape_rules(shape, Q, z.data(), w.data())) return NIR_ERR_CUDA;
+    const nirk::TabLayout L = nirk::layout(shape, b->N, Q);
+    const int g1 = gorder + 1;
+    std::vector<double> host(3 * Q + b->NQ + 2 * (Q + 1) * g1, 0.0);
+    double *hz = host.data(), *hw = hz + 3 * Q, *hL = hw + b->NQ, *hdL = hL + (Q + 1) * g1;
+    std::memcpy(hz, z.data(), sizeof(double) * 3 * Q);
+    std::memcpy(hw, b->tab_h.data() + L.wq, sizeof(double) * b->NQ);
+    if (tensor) {
+        std::vector<double> zz(Q + 1);
+        for (int q = 0; q < Q; ++q) zz[q] = z[q];
+        zz[Q] = 0.0;  // element centre, for per-element factors
+        nirb_lagrange_equi(gorder, Q + 1, zz.data(), hL, hdL);
+    }
+    double *dtab = nullptr;
+    int *derr = nullptr;
+    NIR_CUDA_TRY(cudaMalloc(&dtab, sizeof(double) * host.size()));
+    if (cudaMalloc(&derr, sizeof(int)) != cudaSuccess) {
+        cudaFree(dtab);
+        return NIR_ERR_NO_MEMORY;
+    }
+    const long long units = b->geo_pp ? b->epad * b->NQ : b->epad;
+    if (!b->G64) {
+        if (cudaMalloc(&b->G64, sizeof(double) * units * b->ng) != cudaSuccess ||
+            cudaMalloc(&b->L64, sizeof(double) * units * b->nl) != cudaSuccess) {
+            cudaFree(dtab); cudaFree(derr);
+            return NIR_ERR_NO_MEMORY;
+        }
+    }
+    int rc = NIR_OK;
+    if (cudaMemcpyAsync(dtab, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(derr, 0, sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(b->G64, 0, sizeof(double) * units * b->ng, st) != cudaSuccess ||
+        cudaMemsetAsync(b->L64, 0, sizeof(double) * units * b->nl, st) != cudaSuccess)
+        rc = NIR_ERR_CUDA;
+    if (!rc) {
+        nirk::GeoArgs ga;
+        ga.nodes = nodes;
+        ga.z = dtab;
+        ga.wq = dtab + 3 * Q;
+        ga.Lg = dtab + 3 * Q + b->NQ;
+        ga.dLg = ga.Lg + (Q + 1) * g1;
+        ga.G = b->G64;
+        ga.Lam = b->L64;
+        ga.err = derr;
+        ga.nelem = b->d.nelem;
+        ga.shape = shape;
+        ga.Q = Q;
+        ga.g = gorder;
+        ga.pp = b->geo_pp;
+        rc = nir_geom_launch(ga, st);
+    }
+    int herr = 0;
+    if (!rc && (cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess))
+        rc = NIR_ERR_CUDA;
+    cudaFree(dtab);
+    cudaFree(derr);
+    if (rc) return rc;
+    // drop stale low-precision copies
+    dfree(b->G32); dfree(b->L32);
+    if (b->G16) { cudaFree(b->G16); b->G16 = nullptr; }
+    if (b->L16) { cudaFree(b->L16); b->L16 = nullptr; }
+    if (herr) {
+        b->geo_set = false;
+        return NIR_ERR_GEOMETRY;
+    }
+    b->geo_set = true;
+    (void)d;
+    return NIR_OK;
+}
+
+// --------------------------------------------------------------------------- operators
+namespace {
+
+int check_block(nir_block *b, int prec)
+{
+    if (!b || !valid_prec(prec)) return NIR_ERR_INVALID_ARG;
+    if (!b->geo_set) return NIR_ERR_STATE;
+    return NIR_OK;
+}
+
+bool distinct(std::initializer_list<const void *> ps)
+{
+    std::vector<const void *> v;
+    for (const void *p : ps)
+        if (p) v.push_back(p);
+    for (size_t i = 0; i < v.size(); ++i)
+        for (size_t j = i + 1; j < v.size(); ++j)
+            if (v[i] == v[j]) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" int nir_bwd_trans(nir_block *b, int prec, const void *coeff, void *phys)
+{
+    if (!b || !valid_prec(prec) || !coeff || !phys || coeff == phys) return NIR_ERR_INVALID_ARG;
+    return nir_launch_op(b, prec, nirk::OP_BWD, 0.0, coeff, nullptr, nullptr, phys, nullptr, nullptr,
+                         b->ctx->stream, 0);
+}
+
+extern "C" int nir_iproduct_wrt_base(nir_block *b, int prec, const void *phys, void *coeff)
+{
+    int rc = check_block(b, prec);
+    if (rc) return rc;
+    if (!phys || !coeff || phys == coeff) return NIR_ERR_INVALID_ARG;
+    return nir_launch_op(b, prec, nirk::OP_IPROD, 0.0, phys, nullptr, nullptr, coeff, nullptr, nullptr,
+                         b->ctx->stream, 0);
+}
+
+extern "C" int nir_phys_deriv(nir_block *b, int prec, const void *phys, void *d0, void *d1, void *d2)
+{
+    int rc = check_block(b, prec);
+    if (rc) return rc;
+    if (!phys || !d0 || !d1 || (b->dim == 3) != (d2 != nullptr)) return NIR_ERR_INVALID_ARG;
+    if (!distinct({phys, d0, d1, d2})) return NIR_ERR_INVALID_ARG;
+    return nir_launch_op(b, prec, nirk::OP_PHYSDERIV, 0.0, phys, nullptr, nullptr, d0, d1, d2, b->ctx->stream, 0);
+}
+
+extern "C" int nir_iproduct_wrt_deriv_base(nir_block *b, int prec, const void *f0, const void *f1,
+                                           const void *f2, void *coeff)
+{
+    int rc = check_block(b, prec);
+    if (rc) return rc;
+    if (!f0 || !f1 || !coeff || (b->dim == 3) != (f2 != nullptr)) return NIR_ERR_INVALID_ARG;
+    if (!distinct({f0, f1, f2, coeff})) return NIR_ERR_INVALID_ARG;
+    return nir_launch_op(b, prec, nirk::OP_IPROD_DERIV, 0.0, f0, f1, f2, coeff, nullptr, nullptr,
+                         b->ctx->stream, 0);
+}
+
+extern "C" int nir_mass(nir_block *b, int prec, const void *in, void *out)
+{
+    int rc = check_block(b, prec);
+    if (rc) return rc;
+    if (!in || !out || in == out) return NIR_ERR_INVALID_ARG;
+    return nir_launch_op(b, prec, nirk::OP_MASS, 0.0, in, nullptr, nullptr, out, nullptr, nullptr,
+                         b->ctx->stream, 0);
+}
+
+extern "C" int nir_helmholtz(nir_block *b, int prec, double lambda, const void *in, void *out)
+{
+    int rc = check_block(b, prec);
+    if (rc) return rc;
+    if (!in || !out || in == out || !std::isfinite(lambda)) return NIR_ERR_INVALID_ARG;
+    return nir_launch_op(b, prec, nirk::OP_HELM, lambda, in, nullptr, nullptr, out, nullptr, nullptr,
+                         b->ctx->stream, 0);
+}
+
+extern "C" int nir_helmholtz_host(nir_block *b, int prec, double lambda, const void *h_in, void *h_out)
+{
+    int rc = check_block(b, prec);
+    if (rc) return rc;
+    if (!h_in || !h_out || h_in == h_out || !std::isfinite(lambda)) return NIR_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)b->d.nelem * b->M * nir_prec_size(prec);
+    if (b->stage_bytes < bytes) {
+        if (b->stage_in) cudaFree(b->stage_in);
+        if (b->stage_out) cudaFree(b->stage_out);
+        b->stage_in = b->stage_out = nullptr;
+        b->stage_bytes = 0;
+        if (cudaMalloc(&b->stage_in, bytes) != cudaSuccess || cudaMalloc(&b->stage_out, bytes) != cudaSuccess)
+            return NIR_ERR_NO_MEMORY;
+        b->stage_bytes = bytes;
+    }
+    cudaStream_t st = b->ctx->stream;
+    NIR_CUDA_TRY(cudaMemcpyAsync(b->stage_in, h_in, bytes, cudaMemcpyHostToDevice, st));
+    rc = nir_launch_op(b, prec, nirk::OP_HELM, lambda, b->stage_in, nullptr, nullptr, b->stage_out, nullptr,
+                       nullptr, st, 0);
+    if (rc) return rc;
+    NIR_CUDA_TRY(cudaMemcpyAsync(h_out, b->stage_out, bytes, cudaMemcpyDeviceToHost, st));
+    NIR_CUDA_TRY(cudaStreamSynchronize(st));
+    return NIR_OK;
+}
+
+// --------------------------------------------------------------------------- probe / misc
+extern "C" int nir_probe_fp64_peak(nir_ctx *ctx, double *tflops)
+{
+    if (!ctx || !tflops) return NIR_ERR_INVALID_ARG;
+    NIR_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    double *sink = nullptr;
+    NIR_CUDA_TRY(cudaMalloc(&sink, sizeof(double) * 65536));
+    const int grid = ctx->num_sms * 8, iters = 4096;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = nir_probe_launch(sink, grid, iters / 8, st);  // warm-up
+    float best = 1e30f;
+    for (int rep = 0; rep < 3 && !rc; ++rep) {
+        cudaEventRecord(e0, st);
+        rc = nir_probe_launch(sink, grid, iters, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = NIR_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (rc) return rc;
+    const double flops = 2.0 * 8.0 * iters * (double)grid * 256.0;
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return NIR_OK;
+}
+
+extern "C" const char *nir_strerror(int code)
+{
+    switch (code) {
+    case NIR_OK: return "success";
+    case NIR_ERR_INVALID_ARG: return "invalid argument";
+    case NIR_ERR_UNSUPPORTED: return "unsupported shape/order/quadrature combination";
+    case NIR_ERR_CUDA: return "CUDA runtime error";
+    case NIR_ERR_NOT_CONVERGED: return "solver did not converge";
+    case NIR_ERR_NONFINITE: return "non-finite value in solver";
+    case NIR_ERR_NO_MEMORY: return "out of memory";
+    case NIR_ERR_GEOMETRY: return "non-positive or non-finite Jacobian determinant";
+    case NIR_ERR_STATE: return "object not ready (geometry not set?)";
+    default: return "unknown error";
+    }
+}
+
+extern "C" const char *nir_version(void) { return "nir-gb300 0.1 (sm_103a)"; }

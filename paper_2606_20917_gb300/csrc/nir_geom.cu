@@ -1,0 +1,231 @@
+// nir_geom.cu -- FP64 geometric factors on the GPU, precision conversion of
+// the factors, and the FP64 FMA throughput probe.
+//
+// Per point (or once per element for undeformed quad/hex blocks) the kernel
+// forms the Jacobian J = dx/dxi of the element map, W = w |J| (the weights
+// matrix of Sec. 2.1), d xi/d x = J^{-1} (Lambda of Eq. physderiv), the
+// collapsed-coordinate factors d eta/d xi (Sec. 2.2, D_xi = Lambda(d eta/d xi)
+// D_eta) and their product d eta/d x, and the symmetric metric
+//   G_ij = W sum_l (d eta_i/d x_l)(d eta_j/d x_l).
+#include <cuda_bf16.h>
+
+#include "nir_geom.h"
+#include "nir_internal.h"
+#include "nir_layout.h"
+
+namespace nirk {
+
+__device__ void vertex_grads(int shape, const double *xi, double G[6][3], int &nv)
+{
+    for (int v = 0; v < 6; ++v) G[v][0] = G[v][1] = G[v][2] = 0.0;
+    if (shape == TRI) {
+        nv = 3;
+        G[0][0] = G[0][1] = -0.5;
+        G[1][0] = 0.5;
+        G[2][1] = 0.5;
+    } else if (shape == TET) {
+        nv = 4;
+        G[0][0] = G[0][1] = G[0][2] = -0.5;
+        G[1][0] = 0.5;
+        G[2][1] = 0.5;
+        G[3][2] = 0.5;
+    } else {  // prism: triangle (xi1, xi3) times segment xi2
+        nv = 6;
+        const double T[3] = {-0.5 * (xi[0] + xi[2]), 0.5 * (1.0 + xi[0]), 0.5 * (1.0 + xi[2])};
+        const double dT1[3] = {-0.5, 0.5, 0.0}, dT3[3] = {-0.5, 0.0, 0.5};
+        const double Sg[2] = {0.5 * (1.0 - xi[1]), 0.5 * (1.0 + xi[1])}, dS[2] = {-0.5, 0.5};
+        const int tv[6] = {0, 1, 1, 0, 2, 2}, sv[6] = {0, 0, 1, 1, 0, 1};
+        for (int v = 0; v < 6; ++v) {
+            G[v][0] = dT1[tv[v]] * Sg[sv[v]];
+            G[v][1] = T[tv[v]] * dS[sv[v]];
+            G[v][2] = dT3[tv[v]] * Sg[sv[v]];
+        }
+    }
+}
+
+__global__ void k_geometry(GeoArgs a)
+{
+    const int d = dim(a.shape);
+    const int NQ = npts(a.shape, a.Q);
+    const int ng = ngeo(a.shape), nl = nlam(a.shape);
+    const long long total = a.pp ? a.nelem * NQ : a.nelem;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long e = a.pp ? t / NQ : t;
+        const int n = a.pp ? (int)(t - e * NQ) : 0;
+        const int Q = a.Q;
+        const int ii[3] = {n % Q, (n / Q) % Q, n / (Q * Q)};
+        double eta[3] = {0, 0, 0}, xi[3] = {0, 0, 0};
+        for (int c = 0; c < d; ++c) eta[c] = a.z[c * Q + ii[c]];
+        // collapsed coordinates -> standard element (Eq. eta-space and its inverse)
+        if (a.shape == TRI) {
+            xi[0] = 0.5 * (1.0 + eta[0]) * (1.0 - eta[1]) - 1.0;
+            xi[1] = eta[1];
+        } else if (a.shape == PRISM) {
+            xi[0] = 0.5 * (1.0 + eta[0]) * (1.0 - eta[2]) - 1.0;
+            xi[1] = eta[1];
+            xi[2] = eta[2];
+        } else if (a.shape == TET) {
+            xi[0] = 0.25 * (1.0 + eta[0]) * (1.0 - eta[1]) * (1.0 - eta[2]) - 1.0;
+            xi[1] = 0.5 * (1.0 + eta[1]) * (1.0 - eta[2]) - 1.0;
+            xi[2] = eta[2];
+        } else {
+            for (int c = 0; c < d; ++c) xi[c] = eta[c];
+        }
+        // J[l][i] = d x_l / d xi_i
+        double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        if (a.shape == QUAD || a.shape == HEX) {
+            const int g1 = a.g + 1;
+            const int rows[3] = {a.pp ? ii[0] : Q, a.pp ? ii[1] : Q, a.pp ? ii[2] : Q};
+            const int nn = d == 2 ? g1 * g1 : g1 * g1 * g1;
+            const double *X = a.nodes + (size_t)e * nn * d;
+            for (int v = 0; v < nn; ++v) {
+                const int ab[3] = {v % g1, (v / g1) % g1, v / (g1 * g1)};
+                double Lv[3], dLv[3];
+                for (int c = 0; c < d; ++c) {
+                    Lv[c] = a.Lg[rows[c] * g1 + ab[c]];
+                    dLv[c] = a.dLg[rows[c] * g1 + ab[c]];
+                }
+                double gr[3];
+                for (int i = 0; i < d; ++i) {
+                    double p = 1.0;
+                    for (int c = 0; c < d; ++c) p *= (c == i) ? dLv[c] : Lv[c];
+                    gr[i] = p;
+                }
+                for (int l = 0; l < d; ++l) {
+                    const double xl = X[v * d + l];
+                    for (int i = 0; i < d; ++i) J[l][i] = fma(xl, gr[i], J[l][i]);
+                }
+            }
+        } else {
+            double Gv[6][3];
+            int nv = 0;
+            vertex_grads(a.shape, xi, Gv, nv);
+            const double *X = a.nodes + (size_t)e * nv * d;
+            for (int v = 0; v < nv; ++v)
+                for (int l = 0; l < d; ++l)
+                    for (int i = 0; i < d; ++i) J[l][i] = fma(X[v * d + l], Gv[v][i], J[l][i]);
+        }
+        // determinant and inverse (Ji[i][l] = d xi_i / d x_l)
+        double det, Ji[3][3];
+        if (d == 2) {
+            det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+            Ji[0][0] = J[1][1] / det; Ji[0][1] = -J[0][1] / det;
+            Ji[1][0] = -J[1][0] / det; Ji[1][1] = J[0][0] / det;
+        } else {
+            const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+            const double c10 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+            const double c20 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+            det = J[0][0] * c00 + J[0][1] * c10 + J[0][2] * c20;
+            const double r = 1.0 / det;
+            Ji[0][0] = c00 * r;
+            Ji[1][0] = c10 * r;
+            Ji[2][0] = c20 * r;
+            Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * r;
+            Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * r;
+            Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * r;
+            Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * r;
+            Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * r;
+            Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * r;
+        }
+        if (!(det > 0.0) || !isfinite(det)) atomicExch(a.err, 1);
+        // A[j][i] = d eta_j / d xi_i
+        double A[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        if (a.shape == TRI) {
+            A[0][0] = 2.0 / (1.0 - eta[1]);
+            A[0][1] = (1.0 + eta[0]) / (1.0 - eta[1]);
+        } else if (a.shape == PRISM) {
+            A[0][0] = 2.0 / (1.0 - eta[2]);
+            A[0][2] = (1.0 + eta[0]) / (1.0 - eta[2]);
+        } else if (a.shape == TET) {
+            const double s = (1.0 - eta[1]) * (1.0 - eta[2]);
+            A[0][0] = 4.0 / s;
+            A[0][1] = A[0][2] = 2.0 * (1.0 + eta[0]) / s;
+            A[1][1] = 2.0 / (1.0 - eta[2]);
+            A[1][2] = (1.0 + eta[1]) / (1.0 - eta[2]);
+        }
+        double Lm[3][3];
+        for (int j = 0; j < d; ++j)
+            for (int l = 0; l < d; ++l) {
+                double s = 0.0;
+                for (int i = 0; i < d; ++i) s = fma(A[j][i], Ji[i][l], s);
+                Lm[j][l] = s;
+            }
+        const double W = (a.pp ? a.wq[n] : 1.0) * det;
+        double gv[7];
+        int c = 0;
+        for (int i = 0; i < d; ++i)
+            for (int j = i; j < d; ++j) {
+                double s = 0.0;
+                for (int l = 0; l < d; ++l) s = fma(Lm[i][l], Lm[j][l], s);
+                gv[c++] = W * s;
+            }
+        gv[c] = W;
+        if (a.pp) {
+            const long long base = (e >> 5) * NQ + n;
+            for (int q = 0; q < ng; ++q) a.G[((base * ng + q) << 5) + (e & 31)] = gv[q];
+            for (int j = 0; j < d; ++j)
+                for (int l = 0; l < d; ++l) a.Lam[((base * nl + j * d + l) << 5) + (e & 31)] = Lm[j][l];
+            a.Lam[((base * nl + nl - 1) << 5) + (e & 31)] = W;
+        } else {
+            for (int q = 0; q < ng; ++q) a.G[e * ng + q] = gv[q];
+            for (int j = 0; j < d; ++j)
+                for (int l = 0; l < d; ++l) a.Lam[e * nl + j * d + l] = Lm[j][l];
+            a.Lam[e * nl + nl - 1] = W;
+        }
+    }
+}
+
+__global__ void k_to_f32(const double *src, float *dst, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = __double2float_rn(src[i]);
+}
+
+__global__ void k_to_bf16(const double *src, __nv_bfloat16 *dst, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = __double2bfloat16(src[i]);
+}
+
+// Register-resident FP64 FMA chains: 8 independent recurrences per thread.
+__global__ void __launch_bounds__(256) k_dfma_probe(double *sink, int iters, double a, double b)
+{
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = 1e-3 * (threadIdx.x + k);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == -1.2345) sink[blockIdx.x] = s;  // never true; keeps the chains live
+}
+
+}  // namespace nirk
+
+int nir_geom_launch(const nirk::GeoArgs &a, cudaStream_t st)
+{
+    const long long total = a.pp ? a.nelem * nirk::npts(a.shape, a.Q) : a.nelem;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 65535LL * 8) blocks = 65535LL * 8;
+    nirk::k_geometry<<<(unsigned)blocks, 256, 0, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? NIR_OK : NIR_ERR_CUDA;
+}
+
+int nir_convert_launch(const double *src, float *d32, void *d16, long long n, cudaStream_t st)
+{
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65535LL * 8) blocks = 65535LL * 8;
+    if (d32) nirk::k_to_f32<<<(unsigned)blocks, 256, 0, st>>>(src, d32, n);
+    if (d16) nirk::k_to_bf16<<<(unsigned)blocks, 256, 0, st>>>(src, reinterpret_cast<__nv_bfloat16 *>(d16), n);
+    return cudaGetLastError() == cudaSuccess ? NIR_OK : NIR_ERR_CUDA;
+}
+
+int nir_probe_launch(double *sink, int grid, int iters, cudaStream_t st)
+{
+    nirk::k_dfma_probe<<<grid, 256, 0, st>>>(sink, iters, 0.9999999, 1e-7);
+    return cudaGetLastError() == cudaSuccess ? NIR_OK : NIR_ERR_CUDA;
+}

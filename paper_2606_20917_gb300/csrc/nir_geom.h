@@ -1,0 +1,22 @@
+// nir_geom.h -- launchers of the geometry, conversion and probe kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace nirk {
+struct GeoArgs {
+    const double *nodes;
+    const double *z;
+    const double *wq;
+    const double *Lg;
+    const double *dLg;
+    double *G;
+    double *Lam;
+    int *err;
+    long long nelem;
+    int shape, Q, g, pp;
+};
+}  // namespace nirk
+
+int nir_geom_launch(const nirk::GeoArgs &a, cudaStream_t st);
+int nir_convert_launch(const double *src, float *d32, void *d16, long long n, cudaStream_t st);
+int nir_probe_launch(double *sink, int grid, int iters, cudaStream_t st);

@@ -1,0 +1,66 @@
+// nir_internal.h -- library-internal objects of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/nir.h"
+
+namespace nirk {
+struct KArgs;
+}
+
+// Kernel registry entry of one (shape, P, precision, operator) instantiation.
+struct KInfo {
+    const void *fn = nullptr;  // __global__ function
+    int smem = 0;              // dynamic shared memory bytes
+    int epb = 0;               // elements per CTA group
+    int nt = 0;                // threads per CTA
+};
+
+// Provided by the instantiation units (one per shape x precision).
+KInfo nir_kinfo(int shape, int P, int prec, int op);
+
+struct nir_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    std::mutex mu;
+    std::map<const void *, int> occupancy;  // CTAs per SM per kernel
+    std::map<std::string, int> tuned_grid;  // autotuner overrides (key: shape/P/prec/op)
+};
+
+struct nir_block {
+    nir_ctx *ctx = nullptr;
+    nir_block_desc d{};
+    int dim = 0, N = 0, M = 0, NQ = 0, ng = 0, nl = 0;
+    long long epad = 0;                       // element count padded to 64
+    std::vector<double> tab_h;                // FP64 table blob (host)
+    double *tab64 = nullptr;                  // table blob, device, FP64
+    float *tab32 = nullptr;                   // table blob, device, FP32
+    int geo_pp = 1;                           // per-point (1) or per-element (0) factors
+    bool geo_set = false;
+    double *G64 = nullptr, *L64 = nullptr;    // metric (ng) and d eta/d x + W (nl)
+    float *G32 = nullptr, *L32 = nullptr;
+    void *G16 = nullptr, *L16 = nullptr;      // bfloat16 copies
+    void *stage_in = nullptr, *stage_out = nullptr;
+    size_t stage_bytes = 0;
+};
+
+int nir_launch_op(nir_block *blk, int prec, int op, double lambda, const void *in0, const void *in1,
+                  const void *in2, void *out0, void *out1, void *out2, cudaStream_t stream, int grid_override);
+const void *nir_geo_ptr(nir_block *blk, int prec, bool lam);
+const void *nir_tab_ptr(nir_block *blk, int prec);
+int nir_occupancy(nir_ctx *ctx, const KInfo &ki);
+size_t nir_prec_size(int prec);
+
+#define NIR_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) return NIR_ERR_CUDA;          \
+    } while (0)

@@ -1,0 +1,102 @@
+// nir_layout.h -- compile-time sizes and table layout shared by the host table
+// builder and the device kernels of the library (not by the oracle).
+//
+// Notation: N = P+1 modes per direction, Q points per direction, d = 2 or 3.
+// Modes are packed p outermost, then q, then r; the collapsed shapes bound
+// q < N-p (tri, tet) and r < N-p-q (tet) or r < N-p (prism), as in the
+// sum-factorised loops of Sec. 2.2 (Eq. bwdsumfactet).  Points are indexed
+// i + Q*(j + Q*k) with the first (eta1/xi1) direction fastest.
+#pragma once
+
+#ifdef __CUDACC__
+#define NIR_HD __host__ __device__
+#else
+#define NIR_HD
+#endif
+
+namespace nirk {
+
+enum Shape { QUAD = 0, TRI = 1, HEX = 2, PRISM = 3, TET = 4 };
+
+NIR_HD constexpr int dim(int s) { return (s == QUAD || s == TRI) ? 2 : 3; }
+
+NIR_HD constexpr int nmodes(int s, int N)
+{
+    return s == QUAD ? N * N : s == TRI ? N * (N + 1) / 2 : s == HEX ? N * N * N
+         : s == PRISM ? N * N * (N + 1) / 2 : N * (N + 1) * (N + 2) / 6;
+}
+
+NIR_HD constexpr int npts(int s, int Q) { return dim(s) == 2 ? Q * Q : Q * Q * Q; }
+
+// Number of metric values per point: upper triangle of G plus W = w|J|.
+NIR_HD constexpr int ngeo(int s) { return dim(s) == 2 ? 4 : 7; }
+// Number of PhysDeriv factors per point: d eta_j / d x_l (row j) plus W.
+NIR_HD constexpr int nlam(int s) { return dim(s) == 2 ? 5 : 10; }
+
+// Ragged class tables: class c holds Q x (N - c) values.
+NIR_HD constexpr int cls_cols(int N, int c) { return N - c; }
+NIR_HD constexpr int cls_off(int N, int Q, int c)
+{
+    int o = 0;
+    for (int k = 0; k < c; ++k) o += Q * cls_cols(N, k);
+    return o;
+}
+NIR_HD constexpr int cls_size(int N, int Q) { return cls_off(N, Q, N); }
+
+// Packed-mode helpers for the collapsed shapes.
+// tet: first mode of pair (p,q); pairs ordered p outer, q inner, q < N-p.
+NIR_HD constexpr int tet_pair(int N, int p, int q)
+{
+    int o = 0;
+    for (int k = 0; k < p; ++k) o += N - k;
+    return o + q;
+}
+NIR_HD constexpr int tet_m0(int N, int p, int q)
+{
+    int o = 0;
+    for (int a = 0; a < p; ++a) o += (N - a) * (N - a + 1) / 2;
+    for (int b = 0; b < q; ++b) o += N - p - b;
+    return o;
+}
+NIR_HD constexpr int tri_m0(int N, int p)
+{
+    int o = 0;
+    for (int a = 0; a < p; ++a) o += N - a;
+    return o;
+}
+NIR_HD constexpr int prism_m0(int N, int p, int q)
+{
+    int o = 0;
+    for (int a = 0; a < p; ++a) o += N * (N - a);
+    return o + q * (N - p);
+}
+
+// Table blob layout (units of the compute type).
+//  Ba : Q x N, Ba[k*N + r] = psiA_r(z1_k)           (first direction)
+//  Bb : ragged classes p = 0..N-1, Q x (N-p): psiB_pq(z2_j)  (tri/tet eta2; prism eta3)
+//  Bc : ragged classes c = 0..N-1, Q x (N-c): psiB_cr(z3_k)  (tet eta3; c = p+q)
+//  D1, D2, D3 : Q x Q collocation derivative matrices, D[i*Q + i'] = l'_i'(z_i)
+//  wq : reference quadrature weight per point (collapse factors included)
+struct TabLayout {
+    int Ba, Bb, Bc, D1, D2, D3, wq, total;
+};
+
+NIR_HD constexpr TabLayout layout(int s, int N, int Q)
+{
+    TabLayout L{0, 0, 0, 0, 0, 0, 0, 0};
+    int o = 0;
+    L.Ba = o; o += Q * N;
+    L.Bb = o; if (s == TRI || s == TET || s == PRISM) o += cls_size(N, Q);
+    L.Bc = o; if (s == TET) o += cls_size(N, Q);
+    L.D1 = o; o += Q * Q;
+    L.D2 = o; if (s == TRI || s == TET) o += Q * Q;
+    L.D3 = o; if (s == TET || s == PRISM) o += Q * Q;
+    L.wq = o; o += npts(s, Q);
+    L.total = o;
+    // directions sharing a rule share a table
+    if (s == QUAD || s == HEX) { L.D2 = L.D1; L.D3 = L.D1; }
+    if (s == PRISM) L.D2 = L.D1;
+    return L;
+}
+
+}  // namespace nirk

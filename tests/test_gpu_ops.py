@@ -1,0 +1,280 @@
+"""GPU parity of every elemental operator against the FP64 oracle.
+
+Through the C ABI (Python binding over libnir.so) on seeded synthetic meshes:
+  * every operator x every shape x P in {1..8} in FP64, element by element
+    (norm-wise relative error <= 1e-12 per block, <= 1e-11 per element);
+  * FP32 single apply <= 1e-5, BF16 (bf16 storage, FP32 arithmetic) <= 3e-2;
+  * element counts chosen to span several CTAs plus a ragged tail, E = 1, and
+    the full-size workloads on sampled elements in the benchmark's launch
+    configuration;
+  * error paths: in-place calls, missing geometry, inverted elements.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DIM = {"quad": 2, "tri": 2, "hex": 3, "prism": 3, "tet": 3}
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 3e-2}
+TDT = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
+
+
+@pytest.fixture(scope="module")
+def nir():
+    import paper_2606_20917_gb300 as nir
+    return nir
+
+
+@pytest.fixture(scope="module")
+def ctx(nir):
+    torch.cuda.set_device(0)
+    return nir.Context(0)
+
+
+def curved_quads(n, g, amp=0.04):
+    off = W.lattice_offsets(g, 2)
+    h = 1.0 / n
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    org = np.stack([ii.ravel(), jj.ravel()], axis=1) * h
+    X = org[:, None, :] + off[None] * h
+    x, y = X[..., 0].copy(), X[..., 1].copy()
+    X[..., 0] = x + amp * np.sin(2 * np.pi * y)
+    X[..., 1] = y + amp * np.sin(2 * np.pi * x)
+    return X
+
+
+def make_mesh(shape, E, deformed, seed=0):
+    """(gorder, nodes[E]) for a test mesh of E elements."""
+    if shape == "hex":
+        if deformed:
+            n = int(np.ceil(E ** (1 / 3))) + 1
+            return 2, W.hex_grid(n, 2, amp=0.05)[:E]
+        n = int(np.ceil(E ** (1 / 3))) + 1
+        return 1, W.perturb_vertices(W.hex_grid(n, 1, amp=0.0)[:E], 0.15, seed)
+    if shape == "quad":
+        n = int(np.ceil(E ** 0.5)) + 1
+        if deformed:
+            return 3, curved_quads(n, 3)[:E]
+        return 1, W.perturb_vertices(W.quad_grid(n, n)[:E], 0.15, seed)
+    if shape == "tri":
+        n = int(np.ceil((E / 2) ** 0.5)) + 1
+        return 1, W.perturb_vertices(W.tri_grid(n, n)[:E], 0.15, seed)
+    if shape == "tet":
+        n = int(np.ceil((E / 6) ** (1 / 3))) + 1
+        return 1, W.perturb_vertices(W.tet_kuhn(n)[:E], 0.1, seed)
+    if shape == "prism":
+        n = int(np.ceil((E / 2) ** (1 / 3))) + 1
+        return 1, W.perturb_vertices(W.prism_split(n, n, n)[:E], 0.1, seed)
+    raise KeyError(shape)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def per_elem_rel(a, b):
+    a = a.reshape(a.shape[0], -1) if a.ndim == 2 else np.moveaxis(a, 1, 0).reshape(a.shape[1], -1)
+    b = b.reshape(b.shape[0], -1) if b.ndim == 2 else np.moveaxis(b, 1, 0).reshape(b.shape[1], -1)
+    return (np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)).max()
+
+
+def nelem_for(shape, P):
+    if DIM[shape] == 2:
+        return 150
+    return 37 if P <= 4 else 11
+
+
+def setup(nir, ctx, shape, P, E, deformed, seed=0):
+    g, nodes = make_mesh(shape, E, deformed, seed)
+    blk = nir.Block(ctx, shape, E, P, deformed=deformed)
+    blk.set_geometry(g, torch.from_numpy(np.ascontiguousarray(nodes)).cuda())
+    assert blk.M == oracle.num_modes(shape, P) and blk.NQ == oracle.num_points(shape, P + 2)
+    return g, nodes, blk
+
+
+def run_op(blk, op, prec, x, lam):
+    t = [torch.from_numpy(np.ascontiguousarray(v)).to("cuda", TDT[prec]) for v in x] if op in (
+        "iprod_deriv",) else torch.from_numpy(np.ascontiguousarray(x)).to("cuda", TDT[prec])
+    if op == "bwd":
+        out = blk.bwd_trans(t, prec=prec)
+    elif op == "iprod":
+        out = blk.iproduct_wrt_base(t, prec=prec)
+    elif op == "physderiv":
+        out = torch.stack(blk.phys_deriv(t, prec=prec))
+    elif op == "iprod_deriv":
+        out = blk.iproduct_wrt_deriv_base(t, prec=prec)
+    elif op == "mass":
+        out = blk.mass(t, prec=prec)
+    else:
+        out = blk.helmholtz(t, lam=lam, prec=prec)
+    torch.cuda.synchronize()
+    return out.to(torch.float64).cpu().numpy()
+
+
+def oracle_op(shape, P, g, nodes, op, x, lam):
+    Q = P + 2
+    if op == "bwd":
+        return oracle.bwd(shape, P, Q, x)
+    if op == "iprod":
+        return oracle.iprod(shape, P, Q, g, nodes, x)
+    if op == "physderiv":
+        return oracle.physderiv(shape, Q, g, nodes, x)
+    if op == "iprod_deriv":
+        return oracle.iprod_deriv(shape, P, Q, g, nodes, x)
+    if op == "mass":
+        return oracle.mass(shape, P, Q, g, nodes, x)
+    return oracle.helmholtz(shape, P, Q, g, nodes, lam, x)
+
+
+def inputs(blk, op, seed=0):
+    if op in ("bwd", "mass", "helm"):
+        return W.coefficients(blk.nelem, blk.M, seed)
+    if op == "iprod_deriv":
+        return W.phys_samples(blk.nelem, blk.NQ, seed + 1, ncomp=blk.dim)
+    return W.phys_samples(blk.nelem, blk.NQ, seed + 1)
+
+
+OPS = ["bwd", "iprod", "physderiv", "iprod_deriv", "mass", "helm"]
+
+
+@pytest.mark.parametrize("shape", ["quad", "tri", "hex", "prism", "tet"])
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_fp64_all_ops(nir, ctx, shape, P):
+    deformed = shape in ("hex", "quad")
+    E = nelem_for(shape, P)
+    g, nodes, blk = setup(nir, ctx, shape, P, E, deformed)
+    lam = 1.3
+    for op in OPS:
+        x = inputs(blk, op)
+        got = run_op(blk, op, "f64", x, lam)
+        ref = oracle_op(shape, P, g, nodes, op, x, lam)
+        assert got.shape == ref.shape, op
+        assert rel(got, ref) <= TOL["f64"], (op, rel(got, ref))
+        assert per_elem_rel(got, ref) <= 1e-11, (op, per_elem_rel(got, ref))
+
+
+@pytest.mark.parametrize("shape", ["quad", "hex"])
+@pytest.mark.parametrize("P", [2, 4, 6])
+def test_fp64_affine_tensor_blocks(nir, ctx, shape, P):
+    """Undeformed quad/hex blocks keep one set of factors per element."""
+    E = nelem_for(shape, P)
+    g, nodes, blk = setup(nir, ctx, shape, P, E, deformed=False)
+    for op in OPS:
+        x = inputs(blk, op, seed=3)
+        got = run_op(blk, op, "f64", x, 0.7)
+        ref = oracle_op(shape, P, g, nodes, op, x, 0.7)
+        assert rel(got, ref) <= TOL["f64"], (op, rel(got, ref))
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("shape", ["quad", "tri", "hex", "prism", "tet"])
+@pytest.mark.parametrize("P", [1, 4, 8])
+def test_low_precision_all_ops(nir, ctx, prec, shape, P):
+    deformed = shape in ("hex", "quad")
+    E = nelem_for(shape, P)
+    g, nodes, blk = setup(nir, ctx, shape, P, E, deformed)
+    for op in OPS:
+        x = inputs(blk, op)
+        got = run_op(blk, op, prec, x, 1.0)
+        ref = oracle_op(shape, P, g, nodes, op, x, 1.0)
+        assert rel(got, ref) <= TOL[prec], (op, prec, rel(got, ref))
+
+
+@pytest.mark.parametrize("shape", ["quad", "tri", "hex", "prism", "tet"])
+def test_single_element_and_exact_group(nir, ctx, shape):
+    P = 3
+    for E in (1, 32, 64):
+        g, nodes, blk = setup(nir, ctx, shape, P, E, shape in ("hex", "quad"))
+        x = inputs(blk, "helm")
+        got = run_op(blk, "helm", "f64", x, 2.0)
+        ref = oracle_op(shape, P, g, nodes, "helm", x, 2.0)
+        assert rel(got, ref) <= TOL["f64"]
+
+
+def test_laplacian_of_constant_vanishes_on_full_mesh(nir, ctx):
+    """Property check at the benchmark's full size: L 1 = 0 for every element."""
+    wl = W.workload("hex32_curved_p4")
+    E = wl["nodes"].shape[0]
+    blk = nir.Block(ctx, "hex", E, wl["P"], deformed=True)
+    blk.set_geometry(wl["gorder"], torch.from_numpy(wl["nodes"]).cuda())
+    one = torch.zeros((E, blk.M), dtype=torch.float64, device="cuda")
+    # vertex modes (p, q, r in {0, 1}) of the packed hex ordering m = (p N + q) N + r
+    N = wl["P"] + 1
+    for p in (0, 1):
+        for q in (0, 1):
+            for r in (0, 1):
+                one[:, (p * N + q) * N + r] = 1.0
+    y = blk.helmholtz(one, lam=0.0)
+    mass = blk.helmholtz(one, lam=1.0)
+    torch.cuda.synchronize()
+    assert y.abs().max().item() < 1e-13
+    # 1^T M 1 summed over the mesh = volume of the periodically mapped unit cube
+    vol = (mass * one).sum().item()
+    assert abs(vol - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["hex32_curved_p4", "tet20_kuhn_p4", "prism40x40x20_p4", "quad8x8_p4"])
+def test_full_workloads_sampled(nir, ctx, name):
+    """Full-size blocks in the benchmark's launch configuration; the oracle
+    recomputes a seeded sample of elements one by one."""
+    wl = W.workload(name)
+    nodes, shape, P, Q, g = wl["nodes"], wl["shape"], wl["P"], wl["Q"], wl["gorder"]
+    E = nodes.shape[0]
+    blk = nir.Block(ctx, shape, E, P, deformed=wl["deformed"])
+    blk.set_geometry(g, torch.from_numpy(nodes).cuda())
+    u = W.coefficients(E, blk.M, seed=0)
+    ut = torch.from_numpy(u).cuda()
+    y = blk.helmholtz(ut, lam=1.0).cpu().numpy()
+    b = blk.bwd_trans(ut).cpu().numpy()
+    ids = W.sample_elements(E, 64, seed=1)
+    y_o = oracle.helmholtz(shape, P, Q, g, nodes[ids], 1.0, u[ids])
+    b_o = oracle.bwd(shape, P, Q, u[ids])
+    assert rel(y[ids], y_o) <= 1e-12 and rel(b[ids], b_o) <= 1e-12
+    # FP32 apply on the same sample
+    y32 = blk.helmholtz(ut.float(), lam=1.0, prec="f32").double().cpu().numpy()
+    assert rel(y32[ids], y_o) <= 1e-5
+
+
+def test_full_p6_workload_sampled(nir, ctx):
+    wl = W.workload("hex48_curved_p6")
+    nodes, P, Q, g = wl["nodes"], wl["P"], wl["Q"], wl["gorder"]
+    E = nodes.shape[0]
+    blk = nir.Block(ctx, "hex", E, P, deformed=True)
+    blk.set_geometry(g, torch.from_numpy(nodes).cuda())
+    u = W.coefficients(E, blk.M, seed=0)
+    y = blk.helmholtz(torch.from_numpy(u).cuda(), lam=1.0).cpu().numpy()
+    ids = W.sample_elements(E, 24, seed=2)
+    y_o = oracle.helmholtz("hex", P, Q, g, nodes[ids], 1.0, u[ids])
+    assert rel(y[ids], y_o) <= 1e-12
+
+
+def test_error_paths(nir, ctx):
+    g, nodes, blk = setup(nir, ctx, "tet", 2, 10, False)
+    u = torch.zeros((10, blk.M), dtype=torch.float64, device="cuda")
+    # in-place (aliased) call is rejected before any GPU work
+    assert nir.lib().nir_helmholtz(blk.h, 0, 1.0, nir._ptr(u), nir._ptr(u)) == -1
+    fresh = nir.Block(ctx, "tet", 10, 2)
+    with pytest.raises(nir.NirError) as ei:
+        fresh.helmholtz(u)
+    assert ei.value.code == -8
+    bad = nodes.copy()
+    bad[:, [1, 2]] = bad[:, [2, 1]]  # swap two vertices: negative Jacobian
+    with pytest.raises(nir.NirError) as ei:
+        fresh.set_geometry(1, torch.from_numpy(bad).cuda())
+    assert ei.value.code == -7
+    with pytest.raises(nir.NirError) as ei:
+        nir.Block(ctx, "hex", 10, 9)
+    assert ei.value.code == -2
+
+
+def test_host_buffer_entry_point(nir, ctx):
+    g, nodes, blk = setup(nir, ctx, "hex", 4, 37, True)
+    u = torch.from_numpy(W.coefficients(37, blk.M, 5)).pin_memory()
+    out = torch.empty_like(u).pin_memory()
+    blk.helmholtz_host(u, out, lam=1.0)
+    ref = blk.helmholtz(u.cuda(), lam=1.0).cpu()
+    assert torch.equal(out, ref)
