@@ -66,7 +66,8 @@ enum {
     NIR_ERR_NONFINITE = -5,     /* NaN/Inf met in a CG scalar */
     NIR_ERR_NO_MEMORY = -6,     /* device or host allocation failed */
     NIR_ERR_GEOMETRY = -7,      /* non-positive Jacobian determinant */
-    NIR_ERR_STATE = -8          /* geometry not set / object in wrong state */
+    NIR_ERR_STATE = -8,         /* geometry not set / object in wrong state */
+    NIR_ERR_TOO_LARGE = -9      /* request exceeds a fixed capacity of the library */
 };
 
 typedef struct nir_ctx nir_ctx;
@@ -142,6 +143,31 @@ int nir_helmholtz(nir_block *blk, int prec, double lambda, const void *coeff_in,
  * the result to h_out, and synchronises.  Pinned host memory gives full
  * copy bandwidth.  Device staging buffers are library-owned. */
 int nir_helmholtz_host(nir_block *blk, int prec, double lambda, const void *h_in, void *h_out);
+
+/* Largest coefficient vector (bytes) nir_helmholtz_host_noalloc can stage. */
+#define NIR_NOALLOC_MAX_VECTOR_BYTES ((size_t)16 << 20)
+
+/* nir_helmholtz_host for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this is a deployment variant of the host-buffer
+ * entry point.  It calls no cudaMalloc/cudaFree or any allocating routine;
+ * instead the host arrays are staged through one fixed device array compiled
+ * into the library (2 x NIR_NOALLOC_MAX_VECTOR_BYTES = 32 MiB, held on every
+ * GPU that loads the library until the process exits).  Meant for programs
+ * whose device memory belongs to a pool/caching allocator, loops that must
+ * not stall on an allocation, and hosts that forbid allocation after set-up.
+ *   - h_in, h_out: HOST arrays [E][M] in the precision's type, as for
+ *     nir_helmholtz_host.  Synchronises the context stream before returning.
+ *   - Errors: INVALID_ARG; STATE when geometry is not set, or for NIR_F32 /
+ *     NIR_BF16 when no allocating call in that precision has yet derived the
+ *     block's low-precision factors; TOO_LARGE when E*M*sizeof exceeds
+ *     NIR_NOALLOC_MAX_VECTOR_BYTES (nothing is launched); CUDA.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array and leaves its last contents there;
+ *     calls whose work overlaps on the GPU (other threads or streams) race
+ *     on it, so serialise them. */
+int nir_helmholtz_host_noalloc(nir_block *blk, int prec, double lambda, const void *h_in, void *h_out);
 
 /* Hybrid mesh: the concatenation of blocks (each with geometry set), applied
  * by one persistent launch (Sec. 2.2: operators batched over blocks of alike
