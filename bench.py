@@ -307,6 +307,132 @@ def run_nir(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_solve(args, ws, rank, local):
+    """Helmholtz solve on the P = 6 curved-hex workload: plain FP64 CG versus CG
+    with the operator in FP32 / BF16 inside FP64 iterative refinement."""
+    import torch
+    import paper_2606_20917_gb300 as nir
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = nir.Context(local, torch.cuda.current_stream())
+    wl = W.workload(args.workload)
+    E = wl["nodes"].shape[0]
+    blk = nir.Block(ctx, wl["shape"], E, wl["P"], deformed=wl["deformed"])
+    blk.set_geometry(wl["gorder"], torch.from_numpy(wl["nodes"]).to(dev))
+    mesh = nir.Mesh(ctx, [blk])
+    # right-hand side b = B^T W f for f = (3 pi^2 + lambda) sin(pi x) sin(pi y) sin(pi z)
+    eta, xi = blk.points()
+    lam = 1.0
+    f = manufactured_rhs_points(wl, xi, lam, dev)
+    b = blk.iproduct_wrt_base(f).reshape(-1).contiguous()
+    results = {}
+    for inner in args.solve_precs.split(","):
+        x = torch.zeros_like(b)
+        # warm-up solve (graph capture, preconditioner), then the timed solve
+        mesh.cg_solve(b, torch.zeros_like(b), lam=lam, inner_prec=inner, tol=args.tol, max_outer=60,
+                      max_inner=args.max_inner, inner_tol=args.inner_tol)
+        torch.cuda.synchronize()
+        barrier(ws)
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            rc, st = mesh.cg_solve(b, x, lam=lam, inner_prec=inner, tol=args.tol, max_outer=60,
+                                   max_inner=args.max_inner, inner_tol=args.inner_tol)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        dt = max_over_ranks(ws, dt, dev)
+        results[inner] = dict(rc=rc, wall_seconds=dt, gdofs=ws * b.numel() / dt / 1e9, clocks=clk.summary(),
+                              outer=st["outer"], inner_total=st["inner_total"], rel_residual=st["rel_residual"])
+    if rank != 0:
+        return
+    best = max((r for k, r in results.items() if k != "f64" and r["rc"] == 0), key=lambda r: r["gdofs"],
+               default=None)
+    base = results.get("f64")
+    line = {"metric": "Helmholtz solve GDOF/s to relative residual %g" % args.tol,
+            "value": best["gdofs"] if best else None, "unit": "GDOF/s", "n_gpus": ws, "steps": 1,
+            "warmup": 1, "ms_per_step": best["wall_seconds"] * 1e3 if best else None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 operator / f64 refinement", "data": "synthetic",
+            "config": dict(workload_config(args, wl), solve="CG on the broken operator, Jacobi preconditioner",
+                           rhs="B^T W f, f = (3 pi^2 + 1) sin(pi x) sin(pi y) sin(pi z)"),
+            "solves": results,
+            "speedup_vs_fp64_cg": (best["gdofs"] / base["gdofs"]) if (best and base and base["rc"] == 0) else None}
+    print(json.dumps(line), flush=True)
+
+
+def manufactured_rhs_points(wl, xi, lam, dev):
+    """f at the quadrature points of every element (input generation: the
+    element map is evaluated from the lattice nodes by tensor Lagrange
+    interpolation, with torch on the device)."""
+    import torch
+    g = wl["gorder"]
+    t = np.linspace(-1.0, 1.0, g + 1)
+
+    def lag(x):
+        L = np.ones((x.size, g + 1))
+        for a in range(g + 1):
+            for c in range(g + 1):
+                if c != a:
+                    L[:, a] *= (x - t[c]) / (t[a] - t[c])
+        return L
+
+    L1, L2, L3 = lag(xi[:, 0]), lag(xi[:, 1]), lag(xi[:, 2])
+    Lt = np.einsum("na,nb,nc->ncba", L1, L2, L3).reshape(xi.shape[0], -1)  # node a fastest
+    Lt = torch.from_numpy(Lt).to(dev)
+    nodes = torch.from_numpy(wl["nodes"]).to(dev)
+    X = torch.einsum("nv,evd->end", Lt, nodes)
+    s = torch.sin(np.pi * X)
+    return ((3 * np.pi ** 2 + lam) * s[..., 0] * s[..., 1] * s[..., 2]).contiguous()
+
+
+def run_hybrid(args, ws, rank, local):
+    """Hybrid mesh (~150k hex/prism/tet, P = 2..8) in one persistent launch."""
+    import torch
+    import paper_2606_20917_gb300 as nir
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ctx = nir.Context(local, stream)
+    parts = W.hybrid_mesh(seed=0)
+    blocks = []
+    for p in parts:
+        b = nir.Block(ctx, p["shape"], p["nodes"].shape[0], p["P"], deformed=p["deformed"])
+        b.set_geometry(p["gorder"], torch.from_numpy(p["nodes"]).to(dev))
+        blocks.append(b)
+    mesh = nir.Mesh(ctx, blocks)
+    if args.tune:
+        mesh.tune(os.path.join(ROOT, "gpurun_out", "tune_cache.json") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else None)
+    res = {}
+    nel = sum(b.nelem for b in blocks)
+    for prec in ("f64", "f32"):
+        x = torch.from_numpy(W.coefficients(1, mesh.ndof, seed=0)[0]).to(dev, nir.DTYPE[prec])
+        y = torch.empty_like(x)
+        for _ in range(args.warmup):
+            mesh.helmholtz(x, prec=prec, out=y)
+        torch.cuda.synchronize()
+        barrier(ws)
+        a, bev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            a.record(stream)
+            for _ in range(args.steps):
+                mesh.helmholtz(x, prec=prec, out=y)
+            bev.record(stream)
+            torch.cuda.synchronize()
+        ms = max_over_ranks(ws, a.elapsed_time(bev) / args.steps, dev)
+        res[prec] = {"gdofs": ws * mesh.ndof / (ms * 1e-3) / 1e9, "ms_per_apply": ms, "clocks": clk.summary()}
+    if rank != 0:
+        return
+    line = {"metric": "Helmholtz apply GDOF/s (hybrid mesh, one persistent launch)", "value": res["f64"]["gdofs"],
+            "unit": "GDOF/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["f64"]["ms_per_apply"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "hybrid mesh: 50000 curved hex + 25000 prism + 75000 tet, P ~ U{2..8}, Q = P+2",
+                       "nelem": nel, "ndof": mesh.ndof, "blocks": len(blocks), "tuned": bool(args.tune)},
+            "precisions": res, "gpu_launches": args.steps}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,12 +444,24 @@ def main():
     ap.add_argument("--sample", type=int, default=256, help="reference arm: elements per step")
     ap.add_argument("--extras", action="store_true", help="also time the FP32/BF16 applies")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["apply", "solve", "hybrid"], default="apply")
+    ap.add_argument("--solve-precs", default="f64,f32,bf16")
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--inner-tol", type=float, default=1e-3)
+    ap.add_argument("--max-inner", type=int, default=20000)
+    ap.add_argument("--tune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_setup(args)
+    if args.mode == "solve" and args.workload == "hex32_curved_p4":
+        args.workload = "hex48_curved_p6"
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.mode == "solve":
+        run_solve(args, ws, rank, local)
+    elif args.mode == "hybrid":
+        run_hybrid(args, ws, rank, local)
     else:
         run_nir(args, ws, rank, local)
     if ws > 1:

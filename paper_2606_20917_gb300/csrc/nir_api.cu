@@ -15,7 +15,7 @@
 #include "nir_layout.h"
 
 // --------------------------------------------------------------------------- registry
-#define NIR_DECL(s, p) KInfo nir_kinfo_s##s##_p##p(int P, int op);
+#define NIR_DECL(s, p) KInfo nir_kinfo_s##s##_p##p(int P, int op, int variant);
 NIR_DECL(0, 0) NIR_DECL(0, 1) NIR_DECL(0, 2)
 NIR_DECL(1, 0) NIR_DECL(1, 1) NIR_DECL(1, 2)
 NIR_DECL(2, 0) NIR_DECL(2, 1) NIR_DECL(2, 2)
@@ -23,15 +23,15 @@ NIR_DECL(3, 0) NIR_DECL(3, 1) NIR_DECL(3, 2)
 NIR_DECL(4, 0) NIR_DECL(4, 1) NIR_DECL(4, 2)
 #undef NIR_DECL
 
-KInfo nir_kinfo(int shape, int P, int prec, int op)
+KInfo nir_kinfo(int shape, int P, int prec, int op, int variant)
 {
-    typedef KInfo (*F)(int, int);
+    typedef KInfo (*F)(int, int, int);
     static const F tab[5][3] = {
         {nir_kinfo_s0_p0, nir_kinfo_s0_p1, nir_kinfo_s0_p2}, {nir_kinfo_s1_p0, nir_kinfo_s1_p1, nir_kinfo_s1_p2},
         {nir_kinfo_s2_p0, nir_kinfo_s2_p1, nir_kinfo_s2_p2}, {nir_kinfo_s3_p0, nir_kinfo_s3_p1, nir_kinfo_s3_p2},
         {nir_kinfo_s4_p0, nir_kinfo_s4_p1, nir_kinfo_s4_p2}};
     if (shape < 0 || shape > 4 || prec < 0 || prec > 2) return KInfo{};
-    return tab[shape][prec](P, op);
+    return tab[shape][prec](P, op, variant);
 }
 
 size_t nir_prec_size(int prec) { return prec == NIR_F64 ? 8 : prec == NIR_F32 ? 4 : 2; }
@@ -64,7 +64,9 @@ void dfree(T *&p)
     p = nullptr;
 }
 
-int ensure_lowp(nir_block *b, int prec)
+}  // namespace
+
+int nir_block_ensure_prec(nir_block *b, int prec)
 {
     if (prec == NIR_F64 || !b->geo_set) return NIR_OK;
     const size_t ng = (size_t)(b->geo_pp ? b->epad * b->NQ : b->epad) * b->ng;
@@ -85,8 +87,6 @@ int ensure_lowp(nir_block *b, int prec)
     return NIR_OK;
 }
 
-}  // namespace
-
 const void *nir_geo_ptr(nir_block *b, int prec, bool lam)
 {
     if (prec == NIR_F64) return lam ? (const void *)b->L64 : (const void *)b->G64;
@@ -99,14 +99,17 @@ const void *nir_tab_ptr(nir_block *b, int prec) { return prec == NIR_F64 ? (cons
 int nir_launch_op(nir_block *b, int prec, int op, double lambda, const void *in0, const void *in1, const void *in2,
                   void *out0, void *out1, void *out2, cudaStream_t stream, int grid_override)
 {
-    KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, op);
+    int variant = (op == nirk::OP_HELM && prec >= 0 && prec < 3) ? b->helm_variant[prec] : 0;
+    KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, op, variant);
+    if (!ki.fn) ki = nir_kinfo(b->d.shape, b->d.P, prec, op, 0);
     if (!ki.fn) return NIR_ERR_UNSUPPORTED;
-    int rc = ensure_lowp(b, prec);
+    int rc = nir_block_ensure_prec(b, prec);
     if (rc) return rc;
     int occ = nir_occupancy(b->ctx, ki);
     if (occ < 0) return NIR_ERR_CUDA;
     const long long groups = (b->d.nelem + ki.epb - 1) / ki.epb;
     long long grid = (long long)occ * b->ctx->num_sms;
+    if (grid_override <= 0 && op == nirk::OP_HELM && prec >= 0 && prec < 3) grid_override = b->helm_grid[prec];
     if (grid_override > 0) grid = grid_override;
     if (grid > groups) grid = groups;
     nirk::KArgs a;
@@ -120,8 +123,10 @@ int nir_launch_op(nir_block *b, int prec, int op, double lambda, const void *in0
     a.geo_pp = b->geo_pp;
     a.pad = 0;
     void *args[] = {&a};
-    if (cudaLaunchKernel(ki.fn, dim3((unsigned)grid), dim3(ki.nt), args, (size_t)ki.smem, stream) != cudaSuccess)
+    if (cudaLaunchKernel(ki.fn, dim3((unsigned)grid), dim3(ki.nt), args, (size_t)ki.smem, stream) != cudaSuccess) {
+        (void)cudaGetLastError();  // consume the launch error so it does not surface in a later call
         return NIR_ERR_CUDA;
+    }
     return NIR_OK;
 }
 
@@ -317,6 +322,7 @@ extern "C" int nir_block_set_geometry(nir_block *b, int gorder, const double *no
     cudaFree(dtab);
     cudaFree(derr);
     if (rc) return rc;
+    b->geo_version += 1;
     // drop stale low-precision copies
     dfree(b->G32); dfree(b->L32);
     if (b->G16) { cudaFree(b->G16); b->G16 = nullptr; }

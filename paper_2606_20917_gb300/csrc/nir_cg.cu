@@ -1,0 +1,565 @@
+// nir_cg.cu -- conjugate-gradient Helmholtz solve on a mesh's broken
+// (element-block-diagonal) operator, plain FP64 or mixed precision with FP64
+// iterative refinement (defect correction).
+//
+// The paper uses the Helmholtz operator inside CG iterations (Sec. 4, first
+// paragraph); the solver itself is not described there.  Mixed precision:
+//   r = b - H64 x                      (FP64 operator, FP64 vectors)
+//   repeat: solve H_lo d = r / |r| by preconditioned CG with the operator in
+//           FP32 (or BF16 storage), FP32 vectors and FP64 dot products;
+//           x += |r| d;  r = b - H64 x   until |r| / |b| <= tol.
+// The Jacobi preconditioner's diagonal is extracted by probing: the operator
+// is block diagonal per element with the same mode numbering in every element
+// of a block, so applying it to the vector that is 1 at mode m of every
+// element returns column m of every element matrix, whose mode-m entries are
+// diagonal entries.
+//
+// Scalars (alpha, beta, r.z, r.r) live on the device.  Every reduction writes
+// one partial per CTA; the last CTA to finish (atomic ticket, no waiting)
+// sums the partials in CTA order, so results are deterministic.  Iterations
+// run in chunks replayed from a captured CUDA graph; the host reads the
+// scalars once per chunk.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "nir_internal.h"
+#include "nir_solve.h"
+
+namespace {
+
+struct CGScal {
+    double rz, pAp, alpha, beta, rr, thresh;
+    int done, bad, iters, pad;
+};
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(float v) { return (double)v; }
+__device__ __forceinline__ double to_d(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+__device__ __forceinline__ void st_v(double *p, double v) { *p = v; }
+__device__ __forceinline__ void st_v(float *p, double v) { *p = (float)v; }
+__device__ __forceinline__ void st_v(__nv_bfloat16 *p, double v) { *p = __float2bfloat16_rn((float)v); }
+
+// Block-wide sum of NV doubles; the result is valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV])
+{
+    __shared__ double sh[NV][kThreads / 32];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k][wid] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) s += sh[k][w];
+            v[k] = s;
+        }
+    __syncthreads();
+}
+
+// Publish this CTA's partials; returns true in thread 0 of the last CTA,
+// with the totals (summed in CTA order) in tot.
+template <int NV>
+__device__ __forceinline__ bool finish_reduce(double (&v)[NV], double *part, unsigned *ticket, double (&tot)[NV])
+{
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[k * gridDim.x + blockIdx.x] = v[k];
+        __threadfence();
+        last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return false;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile double *)part)[k * gridDim.x + b];
+        tot[k] = s;
+    }
+    *ticket = 0u;
+    return true;
+}
+
+// pAp = p . Ap ; alpha = rz / pAp
+template <class V, class T>
+__global__ void __launch_bounds__(kThreads) k_alpha(const V *p, const T *Ap, long long n, double *part,
+                                                    unsigned *ticket, CGScal *s)
+{
+    if (s->done) return;
+    double v[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
+        v[0] += to_d(p[i]) * to_d(Ap[i]);
+    block_sum(v);
+    double t[1];
+    if (finish_reduce(v, part, ticket, t)) {
+        s->pAp = t[0];
+        if (!isfinite(t[0])) { s->bad = 2; s->done = 1; }
+        else if (!(t[0] > 0.0)) { s->bad = 1; s->done = 1; }
+        else s->alpha = s->rz / t[0];
+    }
+}
+
+// x += alpha p; r -= alpha Ap; z = dinv r; rz' = r.z; rr = r.r; beta = rz'/rz
+template <class V, class T>
+__global__ void __launch_bounds__(kThreads) k_update(V *x, V *r, V *z, const V *p, const T *Ap, const V *dinv,
+                                                     long long n, double *part, unsigned *ticket, CGScal *s)
+{
+    if (s->done) return;
+    const double a = s->alpha;
+    double v[2] = {0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+        st_v(x + i, to_d(x[i]) + a * to_d(p[i]));
+        const double ri = to_d(r[i]) - a * to_d(Ap[i]);
+        st_v(r + i, ri);
+        const double rv = to_d(r[i]);  // the stored (rounded) residual
+        double zi = rv;
+        if (dinv) {
+            zi = to_d(dinv[i]) * rv;
+            st_v(z + i, zi);
+            zi = to_d(z[i]);
+        }
+        v[0] += rv * zi;
+        v[1] += rv * rv;
+    }
+    block_sum(v);
+    double t[2];
+    if (finish_reduce(v, part, ticket, t)) {
+        s->beta = t[0] / s->rz;
+        s->rz = t[0];
+        s->rr = t[1];
+        s->iters += 1;
+        if (!isfinite(t[0]) || !isfinite(t[1])) { s->bad = 2; s->done = 1; }
+        else if (t[1] <= s->thresh) s->done = 1;
+    }
+}
+
+// p = z + beta p ; pT = p in the operator's storage type
+template <class V, class T>
+__global__ void __launch_bounds__(kThreads) k_pupdate(V *p, const V *z, T *pT, long long n, const CGScal *s)
+{
+    if (s->done) return;
+    const double b = s->beta;
+    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+        const double pi = to_d(z[i]) + b * to_d(p[i]);
+        st_v(p + i, pi);
+        if (pT) st_v(pT + i, to_d(p[i]));
+    }
+}
+
+// start of a CG run: r given; z = dinv r; p = z; rz, rr
+template <class V, class T>
+__global__ void __launch_bounds__(kThreads) k_start(const V *r, V *z, V *p, T *pT, const V *dinv, long long n,
+                                                    double *part, unsigned *ticket, CGScal *s, double thresh)
+{
+    double v[2] = {0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+        const double rv = to_d(r[i]);
+        double zi = rv;
+        if (dinv) {
+            st_v(z + i, to_d(dinv[i]) * rv);
+            zi = to_d(z[i]);
+        }
+        st_v(p + i, zi);
+        if (pT) st_v(pT + i, to_d(p[i]));
+        v[0] += rv * zi;
+        v[1] += rv * rv;
+    }
+    block_sum(v);
+    double t[2];
+    if (finish_reduce(v, part, ticket, t)) {
+        s->rz = t[0];
+        s->rr = t[1];
+        s->thresh = thresh;
+        s->iters = 0;
+        s->bad = (isfinite(t[0]) && isfinite(t[1])) ? 0 : 2;
+        s->done = (s->bad || t[1] <= thresh) ? 1 : 0;
+    }
+}
+
+// out[0] = a . b (FP64)
+template <class V>
+__global__ void __launch_bounds__(kThreads) k_dot(const V *a, const V *b, long long n, double *part, unsigned *ticket,
+                                                  double *out)
+{
+    double v[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
+        v[0] += to_d(a[i]) * to_d(b[i]);
+    block_sum(v);
+    double t[1];
+    if (finish_reduce(v, part, ticket, t)) *out = t[0];
+}
+
+// r = b - Ax (FP64)
+__global__ void k_residual(double *r, const double *b, const double *Ax, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        r[i] = b[i] - Ax[i];
+}
+
+// lo = scale * r (rounded to FP32)
+__global__ void k_scale_to_f32(float *lo, const double *r, double scale, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        lo[i] = (float)(scale * r[i]);
+}
+
+// x += scale * d
+__global__ void k_correct(double *x, const float *d, double scale, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] += scale * (double)d[i];
+}
+
+template <class V>
+__global__ void k_fill(V *x, double v, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        st_v(x + i, v);
+}
+
+// Probing: vector with 1 at mode m of every element of every block.
+struct ProbeBlk {
+    long long off, nelem;
+    int M, pad;
+};
+
+template <class T>
+__global__ void k_probe_fill(T *x, const ProbeBlk *pb, int nb, int m, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int b = 0;
+        while (b + 1 < nb && pb[b + 1].off <= i) ++b;
+        const long long j = (i - pb[b].off) % pb[b].M;
+        st_v(x + i, j == m ? 1.0 : 0.0);
+    }
+}
+
+template <class T>
+__global__ void k_probe_gather(double *diag, const T *y, const ProbeBlk *pb, int nb, int m, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int b = 0;
+        while (b + 1 < nb && pb[b + 1].off <= i) ++b;
+        const long long j = (i - pb[b].off) % pb[b].M;
+        if (j == m) diag[i] = to_d(y[i]);
+    }
+}
+
+__global__ void k_invert(double *d64, float *d32, long long n, int *bad)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double d = d64[i];
+        if (!(d > 0.0) || !isfinite(d)) atomicExch(bad, 1);
+        const double inv = (d > 0.0) ? 1.0 / d : 1.0;
+        d64[i] = inv;
+        d32[i] = (float)inv;
+    }
+}
+
+}  // namespace
+
+struct CGWork {
+    long long n = 0;
+    int grid = 0;                 // CTAs of the vector kernels
+    double *x64 = nullptr, *r64 = nullptr, *z64 = nullptr, *p64 = nullptr, *Ap64 = nullptr;
+    float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *d32 = nullptr;
+    __nv_bfloat16 *pb16 = nullptr, *Apb16 = nullptr;
+    double *dinv64 = nullptr;
+    float *dinv32 = nullptr;
+    double *part = nullptr;       // 2 * grid partials
+    unsigned *ticket = nullptr;
+    CGScal *scal = nullptr;
+    double *dots = nullptr;       // scratch scalars
+    int *flag = nullptr;
+    bool diag_ready = false;
+    double diag_lambda = 0.0;
+    // chunk graphs per inner precision (0: FP64 plain, 1: FP32, 2: BF16)
+    cudaGraphExec_t chunk[3] = {nullptr, nullptr, nullptr};
+    double chunk_lambda[3] = {0, 0, 0};
+    nirk::MeshBlk *chunk_blk[3] = {nullptr, nullptr, nullptr};
+    nirk::MeshBlk *res_blk = nullptr;   // FP64 residual apply x64 -> Ap64
+    double res_lambda = 0.0;
+    int chunk_len = 25;
+};
+
+void nir_cg_invalidate(nir_mesh *m)
+{
+    CGWork *w = m->cg;
+    if (!w) return;
+    for (int i = 0; i < 3; ++i) {
+        if (w->chunk[i]) cudaGraphExecDestroy(w->chunk[i]);
+        if (w->chunk_blk[i]) cudaFree(w->chunk_blk[i]);
+        w->chunk[i] = nullptr;
+        w->chunk_blk[i] = nullptr;
+    }
+    w->diag_ready = false;
+}
+
+void nir_cg_free(nir_mesh *m)
+{
+    CGWork *w = m->cg;
+    if (!w) return;
+    for (int i = 0; i < 3; ++i) {
+        if (w->chunk[i]) cudaGraphExecDestroy(w->chunk[i]);
+        if (w->chunk_blk[i]) cudaFree(w->chunk_blk[i]);
+    }
+    void *ptrs[] = {w->x64, w->r64, w->z64, w->p64, w->Ap64, w->r32, w->z32, w->p32, w->Ap32, w->d32, w->pb16,
+                    w->Apb16, w->dinv64, w->dinv32, w->part, w->ticket, w->scal, w->dots, w->flag, w->res_blk};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete w;
+    m->cg = nullptr;
+}
+
+namespace {
+
+int cg_alloc(nir_mesh *m)
+{
+    if (m->cg) return NIR_OK;
+    CGWork *w = new (std::nothrow) CGWork();
+    if (!w) return NIR_ERR_NO_MEMORY;
+    m->cg = w;
+    const long long n = m->ndof;
+    w->n = n;
+    w->grid = m->ctx->num_sms * 4;
+    const size_t d = sizeof(double) * n, f = sizeof(float) * n, h = sizeof(__nv_bfloat16) * n;
+    bool ok = cudaMalloc(&w->x64, d) == cudaSuccess && cudaMalloc(&w->r64, d) == cudaSuccess &&
+              cudaMalloc(&w->z64, d) == cudaSuccess &&
+              cudaMalloc(&w->p64, d) == cudaSuccess && cudaMalloc(&w->Ap64, d) == cudaSuccess &&
+              cudaMalloc(&w->r32, f) == cudaSuccess && cudaMalloc(&w->z32, f) == cudaSuccess &&
+              cudaMalloc(&w->p32, f) == cudaSuccess && cudaMalloc(&w->Ap32, f) == cudaSuccess &&
+              cudaMalloc(&w->d32, f) == cudaSuccess && cudaMalloc(&w->pb16, h) == cudaSuccess &&
+              cudaMalloc(&w->Apb16, h) == cudaSuccess && cudaMalloc(&w->dinv64, d) == cudaSuccess &&
+              cudaMalloc(&w->dinv32, f) == cudaSuccess &&
+              cudaMalloc(&w->part, sizeof(double) * 2 * w->grid) == cudaSuccess &&
+              cudaMalloc(&w->ticket, sizeof(unsigned) * 4) == cudaSuccess &&
+              cudaMalloc(&w->scal, sizeof(CGScal)) == cudaSuccess &&
+              cudaMalloc(&w->dots, sizeof(double) * 4) == cudaSuccess && cudaMalloc(&w->flag, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        nir_cg_free(m);
+        return NIR_ERR_NO_MEMORY;
+    }
+    cudaMemset(w->ticket, 0, sizeof(unsigned) * 4);
+    return NIR_OK;
+}
+
+int vgrid(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 16); }
+
+// Jacobi diagonal by probing with the FP32 operator.
+int cg_diagonal(nir_mesh *m, double lambda, cudaStream_t st)
+{
+    CGWork *w = m->cg;
+    if (w->diag_ready && w->diag_lambda == lambda) return NIR_OK;
+    std::vector<ProbeBlk> hb(m->blocks.size());
+    int Mmax = 0;
+    for (size_t i = 0; i < m->blocks.size(); ++i) {
+        hb[i].off = m->off[i];
+        hb[i].nelem = m->blocks[i]->d.nelem;
+        hb[i].M = m->blocks[i]->M;
+        hb[i].pad = 0;
+        Mmax = std::max(Mmax, hb[i].M);
+    }
+    ProbeBlk *db = nullptr;
+    NIR_CUDA_TRY(cudaMalloc(&db, sizeof(ProbeBlk) * hb.size()));
+    int rc = NIR_OK;
+    if (cudaMemcpyAsync(db, hb.data(), sizeof(ProbeBlk) * hb.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = NIR_ERR_CUDA;
+    const long long n = w->n;
+    const int nb = (int)hb.size();
+    for (int mm = 0; mm < Mmax && !rc; ++mm) {
+        k_probe_fill<float><<<vgrid(n), 256, 0, st>>>(w->p32, db, nb, mm, n);
+        rc = nir_mesh_apply(m, NIR_F32, lambda, w->p32, w->Ap32, st);
+        if (!rc) k_probe_gather<float><<<vgrid(n), 256, 0, st>>>(w->dinv64, w->Ap32, db, nb, mm, n);
+    }
+    int bad = 0;
+    if (!rc) {
+        cudaMemsetAsync(w->flag, 0, sizeof(int), st);
+        k_invert<<<vgrid(n), 256, 0, st>>>(w->dinv64, w->dinv32, n, w->flag);
+        if (cudaMemcpyAsync(&bad, w->flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = NIR_ERR_CUDA;
+    }
+    cudaFree(db);
+    if (rc) return rc;
+    if (bad) return NIR_ERR_NONFINITE;  // a non-positive diagonal: the operator is not SPD
+    w->diag_ready = true;
+    w->diag_lambda = lambda;
+    return NIR_OK;
+}
+
+// Capture `len` CG iterations for the given inner precision into a graph.
+template <class V, class T>
+int capture_chunk(nir_mesh *m, int mode, int prec, double lambda, V *x, V *r, V *z, V *p, T *pT, T *Ap,
+                  const V *dinv)
+{
+    CGWork *w = m->cg;
+    if (w->chunk[mode] && w->chunk_lambda[mode] == lambda) return NIR_OK;
+    if (w->chunk[mode]) { cudaGraphExecDestroy(w->chunk[mode]); w->chunk[mode] = nullptr; }
+    if (w->chunk_blk[mode]) { cudaFree(w->chunk_blk[mode]); w->chunk_blk[mode] = nullptr; }
+    const void *apply_in = pT ? (const void *)pT : (const void *)p;
+    int rc = nir_mesh_block_table(m, prec, lambda, apply_in, Ap, &w->chunk_blk[mode]);
+    if (rc) return rc;
+    cudaStream_t cs = m->cap_stream;
+    cudaGraph_t g;
+    NIR_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const long long n = w->n;
+    for (int it = 0; it < w->chunk_len && !rc; ++it) {
+        rc = nir_mesh_launch_raw(m, prec, w->chunk_blk[mode], cs);
+        k_alpha<V, T><<<w->grid, kThreads, 0, cs>>>(p, Ap, n, w->part, w->ticket, w->scal);
+        k_update<V, T><<<w->grid, kThreads, 0, cs>>>(x, r, z, p, Ap, dinv, n, w->part, w->ticket + 1, w->scal);
+        k_pupdate<V, T><<<w->grid, kThreads, 0, cs>>>(p, dinv ? z : r, (pT == (T *)p) ? nullptr : pT, n, w->scal);
+    }
+    cudaError_t ec = cudaStreamEndCapture(cs, &g);
+    if (rc) return rc;
+    if (ec != cudaSuccess) return NIR_ERR_CUDA;
+    ec = cudaGraphInstantiate(&w->chunk[mode], g, 0);
+    cudaGraphDestroy(g);
+    if (ec != cudaSuccess) return NIR_ERR_CUDA;
+    w->chunk_lambda[mode] = lambda;
+    return NIR_OK;
+}
+
+// FP64 true residual r64 = b - H x; returns |r|^2 and |b|^2 on the host.
+int residual64(nir_mesh *m, double lambda, const double *b, const double *x, double *rr, double *bb, cudaStream_t st)
+{
+    CGWork *w = m->cg;
+    const long long n = w->n;
+    int rc = nir_mesh_apply(m, NIR_F64, lambda, x, w->Ap64, st);
+    if (rc) return rc;
+    k_residual<<<vgrid(n), 256, 0, st>>>(w->r64, b, w->Ap64, n);
+    k_dot<double><<<w->grid, kThreads, 0, st>>>(w->r64, w->r64, n, w->part, w->ticket + 2, w->dots);
+    if (bb) k_dot<double><<<w->grid, kThreads, 0, st>>>(b, b, n, w->part, w->ticket + 2, w->dots + 1);
+    double h[2] = {0, 0};
+    NIR_CUDA_TRY(cudaMemcpyAsync(h, w->dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+    NIR_CUDA_TRY(cudaStreamSynchronize(st));
+    *rr = h[0];
+    if (bb) *bb = h[1];
+    return NIR_OK;
+}
+
+// Run PCG chunks until done or max_iter; returns iterations and final rr.
+template <class V, class T>
+int run_pcg(nir_mesh *m, int mode, int prec, double lambda, V *x, V *r, V *z, V *p, T *pT, T *Ap, const V *dinv,
+            double thresh, int max_iter, int *iters, double *rr_out, int *bad_out, cudaStream_t st)
+{
+    CGWork *w = m->cg;
+    const long long n = w->n;
+    k_start<V, T><<<w->grid, kThreads, 0, st>>>(r, z, p, (pT == (T *)p) ? nullptr : pT, dinv, n, w->part,
+                                                w->ticket + 3, w->scal, thresh);
+    int rc = capture_chunk<V, T>(m, mode, prec, lambda, x, r, z, p, pT, Ap, dinv);
+    if (rc) return rc;
+    CGScal hs;
+    NIR_CUDA_TRY(cudaMemcpyAsync(&hs, w->scal, sizeof(CGScal), cudaMemcpyDeviceToHost, st));
+    NIR_CUDA_TRY(cudaStreamSynchronize(st));
+    while (!hs.done && hs.iters < max_iter) {
+        NIR_CUDA_TRY(cudaGraphLaunch(w->chunk[mode], st));
+        NIR_CUDA_TRY(cudaMemcpyAsync(&hs, w->scal, sizeof(CGScal), cudaMemcpyDeviceToHost, st));
+        NIR_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    *iters = hs.iters;
+    *rr_out = hs.rr;
+    *bad_out = hs.bad;
+    return NIR_OK;
+}
+
+}  // namespace
+
+extern "C" int nir_cg_solve(nir_mesh *m, double lambda, const double *b, double *x, const nir_cg_opts *o,
+                            nir_cg_stats *stats)
+{
+    if (!m || !b || !x || !o || (const void *)b == (const void *)x) return NIR_ERR_INVALID_ARG;
+    if (!(o->tol > 0.0) || o->max_inner < 1 || !std::isfinite(lambda) || !(lambda > 0.0)) return NIR_ERR_INVALID_ARG;
+    if (o->inner_prec != NIR_F64 && o->inner_prec != NIR_F32 && o->inner_prec != NIR_BF16) return NIR_ERR_INVALID_ARG;
+    if (o->inner_prec != NIR_F64 && (o->max_outer < 1 || !(o->inner_tol > 0.0) || !(o->inner_tol < 1.0)))
+        return NIR_ERR_INVALID_ARG;
+    NIR_CUDA_TRY(cudaSetDevice(m->ctx->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc = cg_alloc(m);
+    if (rc) return rc;
+    CGWork *w = m->cg;
+    cudaStream_t st = m->ctx->stream;
+    const long long n = w->n;
+    if (o->jacobi) {
+        rc = cg_diagonal(m, lambda, st);
+        if (rc) return rc;
+    }
+    double rr = 0.0, bb = 0.0;
+    rc = residual64(m, lambda, b, x, &rr, &bb, st);
+    if (rc) return rc;
+    if (!std::isfinite(rr) || !std::isfinite(bb)) return NIR_ERR_NONFINITE;
+    nir_cg_stats s{0, 0, 0.0, 0.0};
+    const double bn = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
+    int status = NIR_OK;
+    if (o->inner_prec == NIR_F64) {
+        // plain preconditioned CG, FP64 throughout, on an internal copy of x (the
+        // captured iteration graph holds fixed vector addresses).  The recursive
+        // residual drifts from the true one, so CG restarts from b - H x until
+        // the true residual meets the tolerance or the iteration cap is hit.
+        NIR_CUDA_TRY(cudaMemcpyAsync(w->x64, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        for (int restart = 0; restart < 50; ++restart) {
+            int iters = 0, bad = 0;
+            double rr_it = 0.0;
+            rc = run_pcg<double, double>(m, 0, NIR_F64, lambda, w->x64, w->r64, w->z64, w->p64, w->p64, w->Ap64,
+                                         o->jacobi ? w->dinv64 : nullptr, o->tol * o->tol * bb,
+                                         o->max_inner - s.inner_total, &iters, &rr_it, &bad, st);
+            if (rc) return rc;
+            s.inner_total += iters;
+            s.outer += 1;
+            const double prev = rr;
+            rc = residual64(m, lambda, b, w->x64, &rr, nullptr, st);  // also refreshes r64 for a restart
+            if (rc) return rc;
+            if (bad == 2 || !std::isfinite(rr)) { status = NIR_ERR_NONFINITE; break; }
+            if (bad == 1) { status = NIR_ERR_NOT_CONVERGED; break; }
+            if (std::sqrt(rr) / bn <= o->tol) break;
+            if (s.inner_total >= o->max_inner || rr >= prev) { status = NIR_ERR_NOT_CONVERGED; break; }
+        }
+        NIR_CUDA_TRY(cudaMemcpyAsync(x, w->x64, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    } else {
+        const int mode = o->inner_prec == NIR_F32 ? 1 : 2;
+        while (std::sqrt(rr) / bn > o->tol && s.outer < o->max_outer) {
+            const double rn = std::sqrt(rr);
+            k_scale_to_f32<<<vgrid(n), 256, 0, st>>>(w->r32, w->r64, 1.0 / rn, n);
+            k_fill<float><<<vgrid(n), 256, 0, st>>>(w->d32, 0.0, n);
+            int iters = 0, bad = 0;
+            double rr_in = 0.0;
+            const double th = o->inner_tol * o->inner_tol;
+            if (mode == 1)
+                rc = run_pcg<float, float>(m, 1, NIR_F32, lambda, w->d32, w->r32, w->z32, w->p32, w->p32, w->Ap32,
+                                           o->jacobi ? w->dinv32 : nullptr, th, o->max_inner, &iters, &rr_in, &bad, st);
+            else
+                rc = run_pcg<float, __nv_bfloat16>(m, 2, NIR_BF16, lambda, w->d32, w->r32, w->z32, w->p32, w->pb16,
+                                                   w->Apb16, o->jacobi ? w->dinv32 : nullptr, th, o->max_inner,
+                                                   &iters, &rr_in, &bad, st);
+            if (rc) return rc;
+            s.inner_total += iters;
+            s.outer += 1;
+            if (bad == 2) { status = NIR_ERR_NONFINITE; break; }
+            k_correct<<<vgrid(n), 256, 0, st>>>(x, w->d32, rn, n);
+            const double prev = rr;
+            rc = residual64(m, lambda, b, x, &rr, nullptr, st);
+            if (rc) return rc;
+            if (!std::isfinite(rr)) { status = NIR_ERR_NONFINITE; break; }
+            if (rr >= prev) { status = NIR_ERR_NOT_CONVERGED; break; }  // refinement stalled
+        }
+        if (!status && std::sqrt(rr) / bn > o->tol) status = NIR_ERR_NOT_CONVERGED;
+    }
+    NIR_CUDA_TRY(cudaStreamSynchronize(st));
+    s.rel_residual = std::sqrt(rr) / bn;
+    s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = s;
+    return status;
+}

@@ -212,7 +212,7 @@ int nir_geom_launch(const nirk::GeoArgs &a, cudaStream_t st)
     long long blocks = (total + 255) / 256;
     if (blocks > 65535LL * 8) blocks = 65535LL * 8;
     nirk::k_geometry<<<(unsigned)blocks, 256, 0, st>>>(a);
-    return cudaGetLastError() == cudaSuccess ? NIR_OK : NIR_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? NIR_OK : (cudaGetLastError(), NIR_ERR_CUDA);
 }
 
 int nir_convert_launch(const double *src, float *d32, void *d16, long long n, cudaStream_t st)
@@ -221,11 +221,11 @@ int nir_convert_launch(const double *src, float *d32, void *d16, long long n, cu
     if (blocks > 65535LL * 8) blocks = 65535LL * 8;
     if (d32) nirk::k_to_f32<<<(unsigned)blocks, 256, 0, st>>>(src, d32, n);
     if (d16) nirk::k_to_bf16<<<(unsigned)blocks, 256, 0, st>>>(src, reinterpret_cast<__nv_bfloat16 *>(d16), n);
-    return cudaGetLastError() == cudaSuccess ? NIR_OK : NIR_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? NIR_OK : (cudaGetLastError(), NIR_ERR_CUDA);
 }
 
 int nir_probe_launch(double *sink, int grid, int iters, cudaStream_t st)
 {
     nirk::k_dfma_probe<<<grid, 256, 0, st>>>(sink, iters, 0.9999999, 1e-7);
-    return cudaGetLastError() == cudaSuccess ? NIR_OK : NIR_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? NIR_OK : (cudaGetLastError(), NIR_ERR_CUDA);
 }

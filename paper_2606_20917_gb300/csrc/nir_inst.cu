@@ -22,30 +22,47 @@ using TT = float;
 using TT = __nv_bfloat16;
 #endif
 
-template <int N, int OP>
-KInfo make()
+template <int N, int OP, int EPB>
+KInfo make1()
 {
-    using C = Config<NIR_SHAPE, N, N + 1, TT, OP>;
+    using C = Config<NIR_SHAPE, N, N + 1, TT, OP, EPB>;
     KInfo k;
-    k.fn = reinterpret_cast<const void *>(&k_elem<NIR_SHAPE, N, N + 1, TT, OP>);
+    k.fn = reinterpret_cast<const void *>(&k_elem<NIR_SHAPE, N, N + 1, TT, OP, EPB>);
     k.smem = C::SMEM;
     k.epb = C::EPB;
     k.nt = C::NT;
     return k;
 }
 
+// Variant 0: default elements per CTA; 1: half; 2: double (when it fits in
+// 227 KB of shared memory).  Only the Helmholtz operator has variants.
+template <int N, int OP>
+KInfo make(int variant)
+{
+    using C0 = Config<NIR_SHAPE, N, N + 1, TT, OP, 0>;
+    constexpr int e0 = C0::EPB;
+    constexpr int eh = e0 > 1 ? e0 / 2 : 1;
+    constexpr int ed = (C0::TABB + 2 * C0::BUFB <= 227 * 1024 && e0 < 64) ? 2 * e0 : e0;
+    if constexpr (OP == OP_HELM) {
+        if (variant == 1) return make1<N, OP, eh>();
+        if (variant == 2) return make1<N, OP, ed>();
+    }
+    if (variant != 0) return KInfo{};
+    return make1<N, OP, 0>();
+}
+
 template <int OP>
-KInfo by_n(int N)
+KInfo by_n(int N, int v)
 {
     switch (N) {
-    case 2: return make<2, OP>();
-    case 3: return make<3, OP>();
-    case 4: return make<4, OP>();
-    case 5: return make<5, OP>();
-    case 6: return make<6, OP>();
-    case 7: return make<7, OP>();
-    case 8: return make<8, OP>();
-    case 9: return make<9, OP>();
+    case 2: return make<2, OP>(v);
+    case 3: return make<3, OP>(v);
+    case 4: return make<4, OP>(v);
+    case 5: return make<5, OP>(v);
+    case 6: return make<6, OP>(v);
+    case 7: return make<7, OP>(v);
+    case 8: return make<8, OP>(v);
+    case 9: return make<9, OP>(v);
     default: return KInfo{};
     }
 }
@@ -57,17 +74,17 @@ KInfo by_n(int N)
 #define NIR_CAT(a, b) NIR_CAT2(a, b, x)
 #define NIR_KINFO_FN NIR_CAT(NIR_SHAPE, NIR_PREC)
 
-KInfo NIR_KINFO_FN(int P, int op)
+KInfo NIR_KINFO_FN(int P, int op, int variant)
 {
     using namespace nirk;
     const int N = P + 1;
     switch (op) {
-    case OP_BWD: return by_n<OP_BWD>(N);
-    case OP_IPROD: return by_n<OP_IPROD>(N);
-    case OP_PHYSDERIV: return by_n<OP_PHYSDERIV>(N);
-    case OP_IPROD_DERIV: return by_n<OP_IPROD_DERIV>(N);
-    case OP_MASS: return by_n<OP_MASS>(N);
-    case OP_HELM: return by_n<OP_HELM>(N);
+    case OP_BWD: return by_n<OP_BWD>(N, variant);
+    case OP_IPROD: return by_n<OP_IPROD>(N, variant);
+    case OP_PHYSDERIV: return by_n<OP_PHYSDERIV>(N, variant);
+    case OP_IPROD_DERIV: return by_n<OP_IPROD_DERIV>(N, variant);
+    case OP_MASS: return by_n<OP_MASS>(N, variant);
+    case OP_HELM: return by_n<OP_HELM>(N, variant);
     default: return KInfo{};
     }
 }

@@ -24,7 +24,7 @@ struct KInfo {
 };
 
 // Provided by the instantiation units (one per shape x precision).
-KInfo nir_kinfo(int shape, int P, int prec, int op);
+KInfo nir_kinfo(int shape, int P, int prec, int op, int variant);
 
 struct nir_ctx {
     int device = 0;
@@ -44,7 +44,10 @@ struct nir_block {
     double *tab64 = nullptr;                  // table blob, device, FP64
     float *tab32 = nullptr;                   // table blob, device, FP32
     int geo_pp = 1;                           // per-point (1) or per-element (0) factors
+    int helm_variant[3] = {0, 0, 0};          // tuned elements-per-CTA variant per precision
+    int helm_grid[3] = {0, 0, 0};             // tuned grid size per precision (0: occupancy)
     bool geo_set = false;
+    unsigned geo_version = 0;                 // bumped by every nir_block_set_geometry
     double *G64 = nullptr, *L64 = nullptr;    // metric (ng) and d eta/d x + W (nl)
     float *G32 = nullptr, *L32 = nullptr;
     void *G16 = nullptr, *L16 = nullptr;      // bfloat16 copies
@@ -57,6 +60,8 @@ int nir_launch_op(nir_block *blk, int prec, int op, double lambda, const void *i
 const void *nir_geo_ptr(nir_block *blk, int prec, bool lam);
 const void *nir_tab_ptr(nir_block *blk, int prec);
 int nir_occupancy(nir_ctx *ctx, const KInfo &ki);
+// Derive the block's FP32/BF16 geometric factors if needed (allocates once).
+int nir_block_ensure_prec(nir_block *b, int prec);
 size_t nir_prec_size(int prec);
 
 #define NIR_CUDA_TRY(expr)                                   \

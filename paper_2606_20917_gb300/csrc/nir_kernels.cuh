@@ -79,16 +79,26 @@ constexpr int odd_stride(int n) { return (n % 2 == 0) ? n + 1 : n; }
 // One pencil stage over EPB * per_e work items.  out_o = sum_r T(o,r) x_r
 // (+ sum_r TX(r) xx_r when o == OEX).  `rot` rotates the thread->item map so
 // consecutive barrier-free stages spread their tails over different threads.
+// The table functors receive an offset z that is always 0 but is produced
+// inside the loop, so the compiler keeps the (warp-broadcast) table loads in
+// the loop instead of hoisting NIN x NOUT values into registers for threads
+// that only run one or two iterations.
 template <class A, int NIN, int NOUT, int NEX, int OEX, int EPB, int NT, class LD, class TB, class LDX,
           class TBX, class ST>
 __device__ __forceinline__ void pencils(int per_e, int &rot, LD ld, TB tb, LDX ldx, TBX tbx, ST st)
 {
-    const int total = per_e * EPB;
+    // The bound is hidden from the compiler: with few elements per CTA it can
+    // otherwise prove the loop runs at most once and straight-lines whole stages
+    // into code that needs several times the registers.
+    int total = per_e * EPB;
+    asm volatile("mov.u32 %0, %0;" : "+r"(total));
     int w = (int)threadIdx.x - (rot % NT);
     if (w < 0) w += NT;
     for (; w < total; w += NT) {
         const int e = w % EPB;
         const int s = w / EPB;
+        int z;
+        asm volatile("mov.u32 %0, 0;" : "=r"(z));
         A x[NIN];
         ld(e, s, x);
         A xx[NEX > 0 ? NEX : 1];
@@ -97,11 +107,11 @@ __device__ __forceinline__ void pencils(int per_e, int &rot, LD ld, TB tb, LDX l
         for (int o = 0; o < NOUT; ++o) {
             A acc = A(0);
 #pragma unroll
-            for (int r = 0; r < NIN; ++r) acc = fmaa(tb(s, o, r), x[r], acc);
+            for (int r = 0; r < NIN; ++r) acc = fmaa(tb(z, o, r), x[r], acc);
             if constexpr (NEX > 0) {
                 if (o == OEX) {
 #pragma unroll
-                    for (int r = 0; r < NEX; ++r) acc = fmaa(tbx(s, r), xx[r], acc);
+                    for (int r = 0; r < NEX; ++r) acc = fmaa(tbx(z, r), xx[r], acc);
                 }
             }
             st(e, s, o, acc);
@@ -137,7 +147,7 @@ struct Modal {
     {
         const A *Ba = tab + L.Ba;
         int rot = 0;
-        auto tBa = [=](int, int o, int r) { return Ba[o * N + r]; };
+        auto tBa = [=](int z, int o, int r) { return Ba[z + o * N + r]; };
         if constexpr (SH == QUAD || SH == TRI) {
             if constexpr (SH == QUAD) {
                 // t1[p][j] = sum_q u[p][q] psiA_q(z_j)
@@ -159,7 +169,7 @@ struct Modal {
 #pragma unroll
                             for (int r = 0; r < nc; ++r) x[r] = b[r];
                             if constexpr (p == 1) x[nc] = p0[e * S + 1]; },
-                        [=](int, int o, int r) { return (p == 1 && r == nc) ? B0[o * N + 1] : Bp[o * nc + r]; },
+                        [=](int z, int o, int r) { return (p == 1 && r == nc) ? B0[z + o * N + 1] : Bp[z + o * nc + r]; },
                         [=](int e, int, int o, A v) { p1[e * S + p * Q + o] = v; });
                 });
             }
@@ -192,7 +202,7 @@ struct Modal {
 #pragma unroll
                             for (int r = 0; r < nc; ++r) x[r] = b[r];
                             if constexpr (p == 1) x[nc] = p0[e * S + prism_m0(N, 0, q) + 1]; },
-                        [=](int, int o, int r) { return (p == 1 && r == nc) ? B0[o * N + 1] : Bp[o * nc + r]; },
+                        [=](int z, int o, int r) { return (p == 1 && r == nc) ? B0[z + o * N + 1] : Bp[z + o * nc + r]; },
                         [=](int e, int q, int o, A v) { p1[e * S + (p * N + q) * Q + o] = v; });
                 });
             } else {  // TET
@@ -209,7 +219,7 @@ struct Modal {
 #pragma unroll
                             for (int r = 0; r < nc; ++r) x[r] = b[r];
                             if constexpr (c == 1) x[nc] = p0[e * S + 1]; },
-                        [=](int, int o, int r) { return (c == 1 && r == nc) ? B0[o * N + 1] : Bc[o * nc + r]; },
+                        [=](int z, int o, int r) { return (c == 1 && r == nc) ? B0[z + o * N + 1] : Bc[z + o * nc + r]; },
                         [=](int e, int p, int o, A v) { p1[e * S + tet_pair(N, p, c - p) * Q + o] = v; });
                 });
             }
@@ -235,7 +245,7 @@ struct Modal {
 #pragma unroll
                             for (int r = 0; r < nc; ++r) x[r] = b[r * Q];
                             if constexpr (p == 1) x[nc] = p1[e * S + tet_pair(N, 0, 1) * Q + k]; },
-                        [=](int, int o, int r) { return (p == 1 && r == nc) ? B0[o * N + 1] : Bp[o * nc + r]; },
+                        [=](int z, int o, int r) { return (p == 1 && r == nc) ? B0[z + o * N + 1] : Bp[z + o * nc + r]; },
                         [=](int e, int k, int o, A v) { p2[e * S + (p * Q + o) * Q + k] = v; });
                 });
             }
@@ -256,7 +266,7 @@ struct Modal {
     {
         const A *Ba = tab + L.Ba;
         int rot = 0;
-        auto tBaT = [=](int, int o, int r) { return Ba[r * N + o]; };
+        auto tBaT = [=](int z, int o, int r) { return Ba[z + r * N + o]; };
         if constexpr (SH == QUAD || SH == TRI) {
             // t1[p][j] = sum_i psiA_p(z_i) f[i + Q j]
             pencils0<A, Q, N, EPB, NT>(Q, rot,
@@ -282,11 +292,11 @@ struct Modal {
                         [=](int e, int, A *x) { const A *b = p1 + e * S + p * Q;
 #pragma unroll
                             for (int r = 0; r < Q; ++r) x[r] = b[r]; },
-                        [=](int, int o, int r) { return Bp[r * nc + o]; },
+                        [=](int z, int o, int r) { return Bp[z + r * nc + o]; },
                         [=](int e, int, A *xx) { const A *b = p1 + e * S + 1 * Q;   // the (0,1) vertex: p = 1 line
 #pragma unroll
                             for (int r = 0; r < nex; ++r) xx[r] = b[r]; },
-                        [=](int, int r) { return B0[r * N + 1]; },
+                        [=](int z, int r) { return B0[z + r * N + 1]; },
                         [=](int e, int, int o, A v) { last[e * S + tri_m0(N, p) + o] = v; });
                 });
             }
@@ -320,11 +330,11 @@ struct Modal {
                         [=](int e, int k, A *x) { const A *b = p1 + e * S + p * QQ + k;
 #pragma unroll
                             for (int r = 0; r < Q; ++r) x[r] = b[r * Q]; },
-                        [=](int, int o, int r) { return Bp[r * nc + o]; },
+                        [=](int z, int o, int r) { return Bp[z + r * nc + o]; },
                         [=](int e, int k, A *xx) { const A *b = p1 + e * S + 1 * QQ + k;
 #pragma unroll
                             for (int r = 0; r < nex; ++r) xx[r] = b[r * Q]; },
-                        [=](int, int r) { return B0[r * N + 1]; },
+                        [=](int z, int r) { return B0[z + r * N + 1]; },
                         [=](int e, int k, int o, A v) { p2[e * S + (tet_pair(N, p, 0) + o) * Q + k] = v; });
                 });
             }
@@ -347,11 +357,11 @@ struct Modal {
                         [=](int e, int q, A *x) { const A *b = p2 + e * S + (p * N + q) * Q;
 #pragma unroll
                             for (int r = 0; r < Q; ++r) x[r] = b[r]; },
-                        [=](int, int o, int r) { return Bp[r * nc + o]; },
+                        [=](int z, int o, int r) { return Bp[z + r * nc + o]; },
                         [=](int e, int q, A *xx) { const A *b = p2 + e * S + (1 * N + q) * Q;
 #pragma unroll
                             for (int r = 0; r < nex; ++r) xx[r] = b[r]; },
-                        [=](int, int r) { return B0[r * N + 1]; },
+                        [=](int z, int r) { return B0[z + r * N + 1]; },
                         [=](int e, int q, int o, A v) { last[e * S + prism_m0(N, p, q) + o] = v; });
                 });
             } else {  // TET: the top vertex (0,0,1) collects pairs (0,1) and (1,0)
@@ -365,13 +375,13 @@ struct Modal {
                         [=](int e, int p, A *x) { const A *b = p2 + e * S + tet_pair(N, p, c - p) * Q;
 #pragma unroll
                             for (int r = 0; r < Q; ++r) x[r] = b[r]; },
-                        [=](int, int o, int r) { return Bc[r * nc + o]; },
+                        [=](int z, int o, int r) { return Bc[z + r * nc + o]; },
                         [=](int e, int, A *xx) {
                             const A *b1 = p2 + e * S + tet_pair(N, 0, 1) * Q;
                             const A *b2 = p2 + e * S + tet_pair(N, 1, 0) * Q;
 #pragma unroll
                             for (int r = 0; r < nex / 2; ++r) { xx[r] = b1[r]; xx[r + nex / 2] = b2[r]; } },
-                        [=](int, int r) { return B0[(r % Q) * N + 1]; },
+                        [=](int z, int r) { return B0[z + (r % Q) * N + 1]; },
                         [=](int e, int p, int o, A v) { last[e * S + tet_m0(N, p, c - p) + o] = v; });
                 });
             }
@@ -401,7 +411,10 @@ struct Geo {
     __device__ __forceinline__ A gscale(int n) const { return pp ? A(1) : wq[n]; }
 };
 
-template <int SH, int N, int Q, class T, int OP>
+// Default elements per CTA: fill about 110 KB (FP64) or 56 KB (FP32/BF16) of
+// shared memory with the operator's buffers.  EPB_ > 0 overrides it (the
+// autotuner picks among compiled alternatives).
+template <int SH, int N, int Q, class T, int OP, int EPB_ = 0>
 struct Config {
     using A = typename CT<T>::type;
     static constexpr int D = dim(SH);
@@ -411,14 +424,15 @@ struct Config {
     static constexpr int NBUF = (OP == OP_BWD || OP == OP_IPROD || OP == OP_MASS) ? 2 : D + 1;
     static constexpr int TABN = layout(SH, N, Q).total;
     static constexpr int TABB = ((TABN * (int)sizeof(A) + 15) / 16) * 16;
-    // elements per CTA: fill about 110 KB (FP64) or 56 KB (FP32) of shared memory
     static constexpr int budget = sizeof(A) == 8 ? 110 * 1024 : 56 * 1024;
     static constexpr int per_elem = NBUF * S * (int)sizeof(A);
     static constexpr int raw = (budget - TABB) / per_elem;
-    static constexpr int EPB = raw >= 64 ? 64 : raw >= 32 ? 32 : raw >= 16 ? 16 : raw >= 8 ? 8 : raw >= 4 ? 4
-                             : raw >= 2 ? 2 : 1;
+    static constexpr int EPB_DEF = raw >= 64 ? 64 : raw >= 32 ? 32 : raw >= 16 ? 16 : raw >= 8 ? 8 : raw >= 4 ? 4
+                                 : raw >= 2 ? 2 : 1;
+    static constexpr int EPB = EPB_ > 0 ? EPB_ : EPB_DEF;
     static constexpr int NT = 256;
-    static constexpr int SMEM = TABB + NBUF * EPB * S * (int)sizeof(A);
+    static constexpr int BUFB = NBUF * EPB * S * (int)sizeof(A);
+    static constexpr int SMEM = TABB + BUFB;
 };
 
 template <class T, class A, int LEN, int S, int NT>
@@ -489,175 +503,200 @@ __device__ __forceinline__ A dcolT(const A *V0, const A *V1, const A *V2, const 
     return acc;
 }
 
-template <int SH, int N, int Q, class T, int OP>
-__global__ void __launch_bounds__(256) k_elem(KArgs a)
+// Helmholtz metric stage: v_i = sum_j G_ij du_j at every point of the group.
+// PP: factors stored per point (true) or per element times the reference
+// weight (false), resolved at compile time so no scale is applied per point.
+template <bool PP, int D, int Q, int NQ, int NG, int EPB, int NT, class T, class A>
+__device__ __forceinline__ void helm_metric(const Geo<T, A, NQ, NG> &geo, long long e0, const A *D0, const A *D1,
+                                            const A *D2, int S, A *B0, A *B1, A *B2, A *B3)
 {
-    using C = Config<SH, N, Q, T, OP>;
+    for (int w = threadIdx.x; w < EPB * NQ; w += NT) {
+        const int e = w % EPB, n = w / EPB;
+        const int i = n % Q, j = (n / Q) % Q, k = n / (Q * Q);
+        const A *Ue = B0 + e * S;
+        const long long eg = e0 + e;
+        A u0 = dcol<A, Q, D>(Ue, D0, 0, i, j, k);
+        A u1 = dcol<A, Q, D>(Ue, D1, 1, i, j, k);
+        A u2 = A(0);
+        if constexpr (D == 3) u2 = dcol<A, Q, D>(Ue, D2, 2, i, j, k);
+        if constexpr (!PP) {
+            const A sc = geo.wq[n];
+            u0 *= sc;
+            u1 *= sc;
+            if constexpr (D == 3) u2 *= sc;
+        }
+        if constexpr (D == 2) {
+            const A g00 = geo.get(eg, n, 0), g01 = geo.get(eg, n, 1), g11 = geo.get(eg, n, 2);
+            B1[e * S + n] = fmaa(g00, u0, g01 * u1);
+            B2[e * S + n] = fmaa(g01, u0, g11 * u1);
+        } else {
+            const A g00 = geo.get(eg, n, 0), g01 = geo.get(eg, n, 1), g02 = geo.get(eg, n, 2);
+            const A g11 = geo.get(eg, n, 3), g12 = geo.get(eg, n, 4), g22 = geo.get(eg, n, 5);
+            B1[e * S + n] = fmaa(g00, u0, fmaa(g01, u1, g02 * u2));
+            B2[e * S + n] = fmaa(g01, u0, fmaa(g11, u1, g12 * u2));
+            B3[e * S + n] = fmaa(g02, u0, fmaa(g12, u1, g22 * u2));
+        }
+    }
+}
+
+// One group of ne (<= EPB) elements starting at e0: the whole operator.
+// tab: the block's tables in shared memory; buf: NBUF * EPB * S values.
+template <int SH, int N, int Q, class T, int OP, int EPB_>
+__device__ __forceinline__ void run_group(const KArgs &a, const typename CT<T>::type *tab,
+                                          typename CT<T>::type *buf, long long e0, int ne)
+{
+    using C = Config<SH, N, Q, T, OP, EPB_>;
     using A = typename C::A;
     constexpr int D = C::D, NQ = C::NQ, M = C::M, S = C::S, EPB = C::EPB, NT = C::NT;
     constexpr TabLayout L = layout(SH, N, Q);
     constexpr int NG = (OP == OP_PHYSDERIV || OP == OP_IPROD_DERIV) ? nlam(SH) : ngeo(SH);
     using MD = Modal<SH, N, Q, A, EPB, NT, S>;
+    A *B0 = buf, *B1 = buf + EPB * S, *B2 = buf + 2 * EPB * S, *B3 = buf + 3 * EPB * S;
+    const A *D0 = tab + L.D1, *D1 = tab + L.D2, *D2 = tab + L.D3;
+    const Geo<T, A, NQ, NG> geo{reinterpret_cast<const T *>(a.geo), tab + L.wq, a.geo_pp};
 
+    if constexpr (OP == OP_BWD) {
+        gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
+        __syncthreads();
+        if constexpr (D == 2) {
+            MD::bwd(tab, B0, B1, B0, nullptr);
+            gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B0);
+        } else {
+            MD::bwd(tab, B0, B1, B0, B1);
+            gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
+        }
+    } else if constexpr (OP == OP_IPROD || OP == OP_MASS) {
+        A *P = B0;
+        if constexpr (OP == OP_IPROD) {
+            gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
+            __syncthreads();
+        } else {
+            gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
+            __syncthreads();
+            if constexpr (D == 2) MD::bwd(tab, B0, B1, B0, nullptr);
+            else { MD::bwd(tab, B0, B1, B0, B1); P = B1; }
+        }
+        for (int w = threadIdx.x; w < EPB * NQ; w += NT) {
+            const int e = w % EPB, n = w / EPB;
+            P[e * S + n] *= geo.get(e0 + e, n, NG - 1);
+        }
+        __syncthreads();
+        A *O = (P == B0) ? B1 : B0;
+        if constexpr (D == 2) {
+            MD::iprod(tab, P, O, nullptr, P);
+            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, P);
+        } else {
+            MD::iprod(tab, P, O, P, O);
+            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, O);
+        }
+    } else if constexpr (OP == OP_PHYSDERIV) {
+        gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
+        __syncthreads();
+        A *Vs[3] = {B1, B2, B3};
+        for (int w = threadIdx.x; w < EPB * NQ; w += NT) {
+            const int e = w % EPB, n = w / EPB;
+            const int i = n % Q, j = (n / Q) % Q, k = n / (Q * Q);
+            const A *Ue = B0 + e * S;
+            A du[3];
+            du[0] = dcol<A, Q, D>(Ue, D0, 0, i, j, k);
+            du[1] = dcol<A, Q, D>(Ue, D1, 1, i, j, k);
+            if constexpr (D == 3) du[2] = dcol<A, Q, D>(Ue, D2, 2, i, j, k);
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                A s = A(0);
+#pragma unroll
+                for (int jj = 0; jj < D; ++jj) s = fmaa(geo.get(e0 + e, n, jj * D + l), du[jj], s);
+                Vs[l][e * S + n] = s;
+            }
+        }
+        __syncthreads();
+        gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
+        gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out1), e0, ne, B2);
+        if constexpr (D == 3) gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out2), e0, ne, B3);
+    } else if constexpr (OP == OP_IPROD_DERIV) {
+        gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B1);
+        gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in1), e0, ne, B2);
+        if constexpr (D == 3) gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in2), e0, ne, B3);
+        __syncthreads();
+        A *Vs[3] = {B1, B2, B3};
+        // g_j = W sum_l (d eta_j / d x_l) f_l, in place
+        for (int w = threadIdx.x; w < EPB * NQ; w += NT) {
+            const int e = w % EPB, n = w / EPB;
+            A f[3];
+#pragma unroll
+            for (int l = 0; l < D; ++l) f[l] = Vs[l][e * S + n];
+            const A Wn = geo.get(e0 + e, n, NG - 1);
+#pragma unroll
+            for (int jj = 0; jj < D; ++jj) {
+                A s = A(0);
+#pragma unroll
+                for (int l = 0; l < D; ++l) s = fmaa(geo.get(e0 + e, n, jj * D + l), f[l], s);
+                Vs[jj][e * S + n] = Wn * s;
+            }
+        }
+        __syncthreads();
+        for (int w = threadIdx.x; w < EPB * NQ; w += NT) {
+            const int e = w % EPB, n = w / EPB;
+            const int i = n % Q, j = (n / Q) % Q, k = n / (Q * Q);
+            B0[e * S + n] = dcolT<A, Q, D>(B1 + e * S, B2 + e * S, B3 + e * S, D0, D1, D2, i, j, k);
+        }
+        __syncthreads();
+        if constexpr (D == 2) {
+            MD::iprod(tab, B0, B1, nullptr, B2);
+            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B2);
+        } else {
+            MD::iprod(tab, B0, B1, B2, B1);
+            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
+        }
+    } else {  // OP_HELM
+        gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B1);
+        __syncthreads();
+        if constexpr (D == 2) MD::bwd(tab, B1, B2, B0, nullptr);
+        else MD::bwd(tab, B1, B2, B1, B0);
+        // v_i = sum_j G_ij du_j  (G includes W and the chain rule)
+        if (a.geo_pp) helm_metric<true, D, Q, NQ, NG, EPB, NT>(geo, e0, D0, D1, D2, S, B0, B1, B2, B3);
+        else helm_metric<false, D, Q, NQ, NG, EPB, NT>(geo, e0, D0, D1, D2, S, B0, B1, B2, B3);
+        __syncthreads();
+        // y = sum_i D_i^T v_i + lambda W u, in place over u
+        const A lam = A(a.lambda);
+        for (int w = threadIdx.x; w < EPB * NQ; w += NT) {
+            const int e = w % EPB, n = w / EPB;
+            const int i = n % Q, j = (n / Q) % Q, k = n / (Q * Q);
+            const A acc = dcolT<A, Q, D>(B1 + e * S, B2 + e * S, B3 + e * S, D0, D1, D2, i, j, k);
+            B0[e * S + n] = fmaa(lam * geo.get(e0 + e, n, NG - 1), B0[e * S + n], acc);
+        }
+        __syncthreads();
+        if constexpr (D == 2) {
+            MD::iprod(tab, B0, B1, nullptr, B2);
+            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B2);
+        } else {
+            MD::iprod(tab, B0, B1, B2, B1);
+            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
+        }
+    }
+    __syncthreads();
+}
+
+// Persistent single-block kernel: CTAs stride over the element groups.
+template <int SH, int N, int Q, class T, int OP, int EPB_ = 0>
+__global__ void __launch_bounds__(256) k_elem(KArgs a)
+{
+    using C = Config<SH, N, Q, T, OP, EPB_>;
+    using A = typename C::A;
+    constexpr int EPB = C::EPB, NT = C::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A *tab = reinterpret_cast<A *>(smem_raw);
     A *buf = reinterpret_cast<A *>(smem_raw + C::TABB);
-    A *B0 = buf, *B1 = buf + EPB * S, *B2 = buf + 2 * EPB * S, *B3 = buf + 3 * EPB * S;
-
     {
         const A *gt = reinterpret_cast<const A *>(a.tab);
         for (int i = threadIdx.x; i < C::TABN; i += NT) tab[i] = gt[i];
     }
-    const A *D0 = tab + L.D1, *D1 = tab + L.D2, *D2 = tab + L.D3;
-    const Geo<T, A, NQ, NG> geo{reinterpret_cast<const T *>(a.geo), tab + L.wq, a.geo_pp};
-    const A lam = A(a.lambda);
-    const long long ngroups = (a.nelem + EPB - 1) / EPB;
     __syncthreads();
-
+    const long long ngroups = (a.nelem + EPB - 1) / EPB;
     for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
         const long long e0 = g * EPB;
         const int ne = (int)((a.nelem - e0) < EPB ? (a.nelem - e0) : EPB);
-
-        if constexpr (OP == OP_BWD) {
-            gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
-            __syncthreads();
-            if constexpr (D == 2) {
-                MD::bwd(tab, B0, B1, B0, nullptr);
-                gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B0);
-            } else {
-                MD::bwd(tab, B0, B1, B0, B1);
-                gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
-            }
-        } else if constexpr (OP == OP_IPROD || OP == OP_MASS) {
-            A *P = B0;
-            if constexpr (OP == OP_IPROD) {
-                gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
-                __syncthreads();
-            } else {
-                gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
-                __syncthreads();
-                if constexpr (D == 2) MD::bwd(tab, B0, B1, B0, nullptr);
-                else { MD::bwd(tab, B0, B1, B0, B1); P = B1; }
-            }
-            for (int w = threadIdx.x; w < EPB * NQ; w += NT) {
-                const int e = w % EPB, n = w / EPB;
-                P[e * S + n] *= geo.get(e0 + e, n, NG - 1);
-            }
-            __syncthreads();
-            A *O = (P == B0) ? B1 : B0;
-            if constexpr (D == 2) {
-                MD::iprod(tab, P, O, nullptr, P);
-                gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, P);
-            } else {
-                MD::iprod(tab, P, O, P, O);
-                gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, O);
-            }
-        } else if constexpr (OP == OP_PHYSDERIV) {
-            gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
-            __syncthreads();
-            A *Vs[3] = {B1, B2, B3};
-            for (int w = threadIdx.x; w < EPB * NQ; w += NT) {
-                const int e = w % EPB, n = w / EPB;
-                const int i = n % Q, j = (n / Q) % Q, k = n / (Q * Q);
-                const A *Ue = B0 + e * S;
-                A du[3];
-                du[0] = dcol<A, Q, D>(Ue, D0, 0, i, j, k);
-                du[1] = dcol<A, Q, D>(Ue, D1, 1, i, j, k);
-                if constexpr (D == 3) du[2] = dcol<A, Q, D>(Ue, D2, 2, i, j, k);
-#pragma unroll
-                for (int l = 0; l < D; ++l) {
-                    A s = A(0);
-#pragma unroll
-                    for (int jj = 0; jj < D; ++jj) s = fmaa(geo.get(e0 + e, n, jj * D + l), du[jj], s);
-                    Vs[l][e * S + n] = s;
-                }
-            }
-            __syncthreads();
-            gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
-            gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out1), e0, ne, B2);
-            if constexpr (D == 3) gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out2), e0, ne, B3);
-        } else if constexpr (OP == OP_IPROD_DERIV) {
-            gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B1);
-            gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in1), e0, ne, B2);
-            if constexpr (D == 3) gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in2), e0, ne, B3);
-            __syncthreads();
-            A *Vs[3] = {B1, B2, B3};
-            // g_j = W sum_l (d eta_j / d x_l) f_l, in place
-            for (int w = threadIdx.x; w < EPB * NQ; w += NT) {
-                const int e = w % EPB, n = w / EPB;
-                A f[3];
-#pragma unroll
-                for (int l = 0; l < D; ++l) f[l] = Vs[l][e * S + n];
-                const A Wn = geo.get(e0 + e, n, NG - 1);
-#pragma unroll
-                for (int jj = 0; jj < D; ++jj) {
-                    A s = A(0);
-#pragma unroll
-                    for (int l = 0; l < D; ++l) s = fmaa(geo.get(e0 + e, n, jj * D + l), f[l], s);
-                    Vs[jj][e * S + n] = Wn * s;
-                }
-            }
-            __syncthreads();
-            for (int w = threadIdx.x; w < EPB * NQ; w += NT) {
-                const int e = w % EPB, n = w / EPB;
-                const int i = n % Q, j = (n / Q) % Q, k = n / (Q * Q);
-                B0[e * S + n] = dcolT<A, Q, D>(B1 + e * S, B2 + e * S, B3 + e * S, D0, D1, D2, i, j, k);
-            }
-            __syncthreads();
-            if constexpr (D == 2) {
-                MD::iprod(tab, B0, B1, nullptr, B2);
-                gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B2);
-            } else {
-                MD::iprod(tab, B0, B1, B2, B1);
-                gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
-            }
-        } else {  // OP_HELM
-            gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B1);
-            __syncthreads();
-            if constexpr (D == 2) MD::bwd(tab, B1, B2, B0, nullptr);
-            else MD::bwd(tab, B1, B2, B1, B0);
-            // v_i = sum_j G_ij du_j  (G includes W and the chain rule)
-            for (int w = threadIdx.x; w < EPB * NQ; w += NT) {
-                const int e = w % EPB, n = w / EPB;
-                const int i = n % Q, j = (n / Q) % Q, k = n / (Q * Q);
-                const A *Ue = B0 + e * S;
-                const long long eg = e0 + e;
-                const A sc = geo.gscale(n);
-                if constexpr (D == 2) {
-                    const A u0 = dcol<A, Q, D>(Ue, D0, 0, i, j, k) * sc;
-                    const A u1 = dcol<A, Q, D>(Ue, D1, 1, i, j, k) * sc;
-                    const A g00 = geo.get(eg, n, 0), g01 = geo.get(eg, n, 1), g11 = geo.get(eg, n, 2);
-                    B1[e * S + n] = fmaa(g00, u0, g01 * u1);
-                    B2[e * S + n] = fmaa(g01, u0, g11 * u1);
-                } else {
-                    const A u0 = dcol<A, Q, D>(Ue, D0, 0, i, j, k) * sc;
-                    const A u1 = dcol<A, Q, D>(Ue, D1, 1, i, j, k) * sc;
-                    const A u2 = dcol<A, Q, D>(Ue, D2, 2, i, j, k) * sc;
-                    const A g00 = geo.get(eg, n, 0), g01 = geo.get(eg, n, 1), g02 = geo.get(eg, n, 2);
-                    const A g11 = geo.get(eg, n, 3), g12 = geo.get(eg, n, 4), g22 = geo.get(eg, n, 5);
-                    B1[e * S + n] = fmaa(g00, u0, fmaa(g01, u1, g02 * u2));
-                    B2[e * S + n] = fmaa(g01, u0, fmaa(g11, u1, g12 * u2));
-                    B3[e * S + n] = fmaa(g02, u0, fmaa(g12, u1, g22 * u2));
-                }
-            }
-            __syncthreads();
-            // y = lambda W u + sum_i D_i^T v_i, in place over u
-            for (int w = threadIdx.x; w < EPB * NQ; w += NT) {
-                const int e = w % EPB, n = w / EPB;
-                const int i = n % Q, j = (n / Q) % Q, k = n / (Q * Q);
-                const A m = lam * geo.get(e0 + e, n, NG - 1) * B0[e * S + n];
-                B0[e * S + n] = m + dcolT<A, Q, D>(B1 + e * S, B2 + e * S, B3 + e * S, D0, D1, D2, i, j, k);
-            }
-            __syncthreads();
-            if constexpr (D == 2) {
-                MD::iprod(tab, B0, B1, nullptr, B2);
-                gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B2);
-            } else {
-                MD::iprod(tab, B0, B1, B2, B1);
-                gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
-            }
-        }
-        __syncthreads();
+        run_group<SH, N, Q, T, OP, EPB_>(a, tab, buf, e0, ne);
     }
 }
 

@@ -1,21 +1,462 @@
-// nir_solve.cu -- hybrid mesh, persistent launch, CUDA graph, autotuner and
-// the mixed-precision conjugate-gradient solve (filled in below).
+// nir_solve.cu -- hybrid meshes: the persistent single-launch Helmholtz apply
+// over blocks of different shapes and orders, its CUDA-graph cache and the
+// autotuner (elements-per-CTA variants and grid sizes, JSON cache file).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
+
 #include "nir_internal.h"
+#include "nir_mesh.h"
+#include "nir_solve.h"
 
-struct nir_mesh {
-    nir_ctx *ctx = nullptr;
-};
+#define NIR_MDECL(d, p) MeshKInfo nir_mesh_kinfo_d##d##_p##p(int shape, int P);
+NIR_MDECL(2, 0) NIR_MDECL(2, 1) NIR_MDECL(2, 2)
+NIR_MDECL(3, 0) NIR_MDECL(3, 1) NIR_MDECL(3, 2)
+#undef NIR_MDECL
 
-extern "C" int nir_mesh_create(nir_ctx *, nir_block *const *, int, nir_mesh **out)
+MeshKInfo nir_mesh_kinfo(int dim, int prec, int shape, int P)
 {
-    if (out) *out = nullptr;
-    return NIR_ERR_UNSUPPORTED;
+    typedef MeshKInfo (*F)(int, int);
+    static const F tab[2][3] = {{nir_mesh_kinfo_d2_p0, nir_mesh_kinfo_d2_p1, nir_mesh_kinfo_d2_p2},
+                                {nir_mesh_kinfo_d3_p0, nir_mesh_kinfo_d3_p1, nir_mesh_kinfo_d3_p2}};
+    if ((dim != 2 && dim != 3) || prec < 0 || prec > 2) return MeshKInfo{};
+    return tab[dim - 2][prec](shape, P);
 }
-extern "C" void nir_mesh_destroy(nir_mesh *m) { delete m; }
-extern "C" int nir_mesh_num_dofs(const nir_mesh *, int64_t *) { return NIR_ERR_UNSUPPORTED; }
-extern "C" int nir_mesh_helmholtz(nir_mesh *, int, double, const void *, void *) { return NIR_ERR_UNSUPPORTED; }
-extern "C" int nir_tune(nir_mesh *, const char *) { return NIR_ERR_UNSUPPORTED; }
-extern "C" int nir_cg_solve(nir_mesh *, double, const double *, double *, const nir_cg_opts *, nir_cg_stats *)
+
+namespace {
+
+// Relative cost of one element's Helmholtz apply (sum-factorised flop count),
+// used to order the work list longest first.
+double elem_cost(int shape, int P)
 {
-    return NIR_ERR_UNSUPPORTED;
+    const double N = P + 1, Q = P + 2;
+    if (shape == NIR_QUAD || shape == NIR_TRI) return 4 * N * (N * Q + Q * Q) + 8 * Q * Q * Q + 10 * Q * Q;
+    return 4 * N * (N * N * Q + N * Q * Q + Q * Q * Q) + 12 * Q * Q * Q * Q + 20 * Q * Q * Q;
+}
+
+bool valid_prec(int p) { return p == NIR_F64 || p == NIR_F32 || p == NIR_BF16; }
+
+}  // namespace
+
+int nir_mesh_build_items(nir_mesh *m, int prec, int gran)
+{
+    MeshPrec &ps = m->ps[prec];
+    std::vector<std::pair<double, nirk::MeshItem>> items;
+    ps.smem = 0;
+    ps.fn = nullptr;
+    for (size_t bi = 0; bi < m->blocks.size(); ++bi) {
+        nir_block *b = m->blocks[bi];
+        MeshKInfo k = nir_mesh_kinfo(m->dim, prec, b->d.shape, b->d.P);
+        if (!k.fn) return NIR_ERR_UNSUPPORTED;
+        ps.fn = k.fn;
+        ps.smem = std::max(ps.smem, k.smem);
+        ps.vid[bi] = k.vid;
+        const long long ngroups = (b->d.nelem + k.epb - 1) / k.epb;
+        for (long long g = 0; g < ngroups; g += gran) {
+            nirk::MeshItem it;
+            it.block = (int)bi;
+            it.g0 = (int)g;
+            it.ng = (int)std::min<long long>(gran, ngroups - g);
+            it.pad = 0;
+            const long long nel = std::min<long long>((long long)it.ng * k.epb, b->d.nelem - g * k.epb);
+            items.push_back({nel * elem_cost(b->d.shape, b->d.P), it});
+        }
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<double, nirk::MeshItem> &a, const std::pair<double, nirk::MeshItem> &b) {
+                         return a.first > b.first;
+                     });
+    std::vector<nirk::MeshItem> h(items.size());
+    for (size_t i = 0; i < items.size(); ++i) h[i] = items[i].second;
+    if (ps.ditems) cudaFree(ps.ditems);
+    ps.ditems = nullptr;
+    NIR_CUDA_TRY(cudaMalloc(&ps.ditems, sizeof(nirk::MeshItem) * std::max<size_t>(1, h.size())));
+    NIR_CUDA_TRY(cudaMemcpy(ps.ditems, h.data(), sizeof(nirk::MeshItem) * h.size(), cudaMemcpyHostToDevice));
+    ps.nitems = (int)h.size();
+    ps.gran = gran;
+    if (ps.smem > 48 * 1024)
+        NIR_CUDA_TRY(cudaFuncSetAttribute(ps.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ps.smem));
+    int occ = 0;
+    NIR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ps.fn, 256, ps.smem));
+    ps.occ = std::max(1, occ);
+    if (ps.grid <= 0 || ps.grid > ps.occ * m->ctx->num_sms) ps.grid = ps.occ * m->ctx->num_sms;
+    ps.ready = true;
+    // captured graphs embed the old work list
+    for (auto &g : m->graphs)
+        if (g.prec == prec) g.stale = true;
+    nir_cg_invalidate(m);
+    return NIR_OK;
+}
+
+// Launch the persistent kernel for (prec, in, out, lambda) on `st` using a
+// device block table `dblk` (already uploaded).
+int nir_mesh_launch_raw(nir_mesh *m, int prec, const nirk::MeshBlk *dblk, cudaStream_t st)
+{
+    MeshPrec &ps = m->ps[prec];
+    if (!ps.ready || !ps.fn) return NIR_ERR_STATE;
+    NIR_CUDA_TRY(cudaMemsetAsync(m->counter + prec, 0, sizeof(int), st));
+    int *ctr = m->counter + prec;
+    int nitems = ps.nitems;
+    const nirk::MeshItem *items = ps.ditems;
+    void *args[] = {(void *)&dblk, (void *)&items, (void *)&nitems, (void *)&ctr};
+    if (cudaLaunchKernel(ps.fn, dim3(ps.grid), dim3(256), args, (size_t)ps.smem, st) != cudaSuccess) {
+        (void)cudaGetLastError();  // consume the launch error so it does not surface in a later call
+        return NIR_ERR_CUDA;
+    }
+    return NIR_OK;
+}
+
+int nir_mesh_prepare(nir_mesh *m, int prec)
+{
+    // a block whose geometry was set again has new factor arrays: every
+    // captured graph and block table of the mesh is out of date
+    bool changed = m->geo_seen.size() != m->blocks.size();
+    for (size_t i = 0; !changed && i < m->blocks.size(); ++i) changed = m->geo_seen[i] != m->blocks[i]->geo_version;
+    if (changed) {
+        for (auto &g : m->graphs) g.stale = true;
+        nir_cg_invalidate(m);
+        m->geo_seen.resize(m->blocks.size());
+        for (size_t i = 0; i < m->blocks.size(); ++i) m->geo_seen[i] = m->blocks[i]->geo_version;
+        for (size_t i = 0; i < m->blocks.size(); ++i)
+            if (!m->blocks[i]->geo_set) return NIR_ERR_STATE;
+    }
+    if (m->ps[prec].ready) return NIR_OK;
+    return nir_mesh_build_items(m, prec, m->ps[prec].gran > 0 ? m->ps[prec].gran : 1);
+}
+
+int nir_mesh_block_table(nir_mesh *m, int prec, double lambda, const void *in, void *out, nirk::MeshBlk **dout)
+{
+    int rc0 = nir_mesh_prepare(m, prec);
+    if (rc0) return rc0;
+    const size_t es = nir_prec_size(prec);
+    std::vector<nirk::MeshBlk> h(m->blocks.size());
+    for (size_t bi = 0; bi < m->blocks.size(); ++bi) {
+        nir_block *b = m->blocks[bi];
+        int rc = nir_block_ensure_prec(b, prec);
+        if (rc) return rc;
+        nirk::KArgs &a = h[bi].a;
+        std::memset(&a, 0, sizeof(a));
+        a.in0 = (const char *)in + (size_t)m->off[bi] * es;
+        a.out0 = (char *)out + (size_t)m->off[bi] * es;
+        a.geo = nir_geo_ptr(b, prec, false);
+        a.tab = nir_tab_ptr(b, prec);
+        a.nelem = b->d.nelem;
+        a.lambda = lambda;
+        a.geo_pp = b->geo_pp;
+        h[bi].vid = m->ps[prec].vid[bi];
+    }
+    nirk::MeshBlk *d = nullptr;
+    NIR_CUDA_TRY(cudaMalloc(&d, sizeof(nirk::MeshBlk) * h.size()));
+    if (cudaMemcpy(d, h.data(), sizeof(nirk::MeshBlk) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return NIR_ERR_CUDA;
+    }
+    *dout = d;
+    return NIR_OK;
+}
+
+// Apply through a cached CUDA graph (captured on first use per key).
+int nir_mesh_apply(nir_mesh *m, int prec, double lambda, const void *in, void *out, cudaStream_t st)
+{
+    {
+        int rc = nir_mesh_prepare(m, prec);
+        if (rc) return rc;
+    }
+    MeshGraph *hit = nullptr;
+    for (auto &g : m->graphs)
+        if (g.prec == prec && g.in == in && g.out == out && g.lambda == lambda) hit = &g;
+    if (hit && hit->stale) {
+        cudaGraphExecDestroy(hit->exec);
+        cudaFree(hit->dblk);
+        *hit = m->graphs.back();
+        m->graphs.pop_back();
+        hit = nullptr;
+    }
+    if (!hit) {
+        if (m->graphs.size() >= 32) {  // bounded cache: drop the oldest entry
+            cudaGraphExecDestroy(m->graphs.front().exec);
+            cudaFree(m->graphs.front().dblk);
+            m->graphs.erase(m->graphs.begin());
+        }
+        MeshGraph g;
+        g.prec = prec;
+        g.in = in;
+        g.out = out;
+        g.lambda = lambda;
+        int rc = nir_mesh_block_table(m, prec, lambda, in, out, &g.dblk);
+        if (rc) return rc;
+        cudaGraph_t graph;
+        if (cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaFree(g.dblk);
+            return NIR_ERR_CUDA;
+        }
+        rc = nir_mesh_launch_raw(m, prec, g.dblk, m->cap_stream);
+        cudaError_t ec = cudaStreamEndCapture(m->cap_stream, &graph);
+        if (rc || ec != cudaSuccess) {
+            cudaFree(g.dblk);
+            return rc ? rc : NIR_ERR_CUDA;
+        }
+        ec = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ec != cudaSuccess) {
+            cudaFree(g.dblk);
+            return NIR_ERR_CUDA;
+        }
+        m->graphs.push_back(g);
+        hit = &m->graphs.back();
+    }
+    NIR_CUDA_TRY(cudaGraphLaunch(hit->exec, st));
+    return NIR_OK;
+}
+
+// --------------------------------------------------------------------------- C ABI
+extern "C" int nir_mesh_create(nir_ctx *ctx, nir_block *const *blocks, int nblocks, nir_mesh **out)
+{
+    if (!out) return NIR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!ctx || !blocks || nblocks < 1) return NIR_ERR_INVALID_ARG;
+    const int dim = blocks[0] ? blocks[0]->dim : 0;
+    for (int i = 0; i < nblocks; ++i) {
+        if (!blocks[i] || blocks[i]->ctx != ctx || blocks[i]->dim != dim) return NIR_ERR_INVALID_ARG;
+        if (!blocks[i]->geo_set) return NIR_ERR_STATE;
+        for (int j = 0; j < i; ++j)
+            if (blocks[j] == blocks[i]) return NIR_ERR_INVALID_ARG;
+    }
+    NIR_CUDA_TRY(cudaSetDevice(ctx->device));
+    nir_mesh *m = new (std::nothrow) nir_mesh();
+    if (!m) return NIR_ERR_NO_MEMORY;
+    m->ctx = ctx;
+    m->dim = dim;
+    long long o = 0;
+    for (int i = 0; i < nblocks; ++i) {
+        m->blocks.push_back(blocks[i]);
+        m->off.push_back(o);
+        o += blocks[i]->d.nelem * blocks[i]->M;
+    }
+    m->ndof = o;
+    for (int p = 0; p < 3; ++p) m->ps[p].vid.assign(nblocks, -1);
+    if (cudaMalloc(&m->counter, sizeof(int) * 4) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        nir_mesh_destroy(m);
+        return NIR_ERR_CUDA;
+    }
+    *out = m;
+    return NIR_OK;
+}
+
+extern "C" void nir_mesh_destroy(nir_mesh *m)
+{
+    if (!m) return;
+    for (auto &g : m->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        cudaFree(g.dblk);
+    }
+    for (int p = 0; p < 3; ++p)
+        if (m->ps[p].ditems) cudaFree(m->ps[p].ditems);
+    if (m->counter) cudaFree(m->counter);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    nir_cg_free(m);
+    delete m;
+}
+
+extern "C" int nir_mesh_num_dofs(const nir_mesh *m, int64_t *ndof)
+{
+    if (!m || !ndof) return NIR_ERR_INVALID_ARG;
+    *ndof = m->ndof;
+    return NIR_OK;
+}
+
+extern "C" int nir_mesh_helmholtz(nir_mesh *m, int prec, double lambda, const void *in, void *out)
+{
+    if (!m || !valid_prec(prec) || !in || !out || in == out || !std::isfinite(lambda)) return NIR_ERR_INVALID_ARG;
+    NIR_CUDA_TRY(cudaSetDevice(m->ctx->device));
+    return nir_mesh_apply(m, prec, lambda, in, out, m->ctx->stream);
+}
+
+// --------------------------------------------------------------------------- autotuner
+namespace {
+
+std::string gpu_name(int dev)
+{
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+    std::string s = p.name;
+    for (auto &c : s)
+        if (c == '"' || c == '|') c = '_';
+    return s;
+}
+
+std::map<std::string, std::string> read_cache(const char *path)
+{
+    std::map<std::string, std::string> kv;
+    if (!path) return kv;
+    std::ifstream f(path);
+    if (!f) return kv;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    const std::string s = ss.str();
+    // flat JSON object of string keys to string values
+    size_t i = 0;
+    while (true) {
+        size_t k0 = s.find('"', i);
+        if (k0 == std::string::npos) break;
+        size_t k1 = s.find('"', k0 + 1);
+        size_t v0 = s.find('"', k1 + 1);
+        size_t v1 = v0 == std::string::npos ? v0 : s.find('"', v0 + 1);
+        if (k1 == std::string::npos || v1 == std::string::npos) break;
+        kv[s.substr(k0 + 1, k1 - k0 - 1)] = s.substr(v0 + 1, v1 - v0 - 1);
+        i = v1 + 1;
+    }
+    return kv;
+}
+
+bool write_cache(const char *path, const std::map<std::string, std::string> &kv)
+{
+    if (!path) return true;
+    std::string tmp = std::string(path) + ".tmp";
+    {
+        std::ofstream f(tmp);
+        if (!f) return false;
+        f << "{\n";
+        size_t n = 0;
+        for (auto &e : kv) f << "  \"" << e.first << "\": \"" << e.second << "\"" << (++n < kv.size() ? ",\n" : "\n");
+        f << "}\n";
+    }
+    return std::rename(tmp.c_str(), path) == 0;
+}
+
+// Median time (ms) of `reps` launches of f on stream st.
+template <class F>
+float time_ms(cudaStream_t st, int reps, F f)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    std::vector<float> t;
+    f();
+    f();
+    for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(a, st);
+        f();
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        t.push_back(ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    std::sort(t.begin(), t.end());
+    return t[t.size() / 2];
+}
+
+}  // namespace
+
+extern "C" int nir_tune(nir_mesh *m, const char *cache_path)
+{
+    if (!m) return NIR_ERR_INVALID_ARG;
+    nir_ctx *ctx = m->ctx;
+    NIR_CUDA_TRY(cudaSetDevice(ctx->device));
+    const std::string gpu = gpu_name(ctx->device);
+    auto kv = read_cache(cache_path);
+    cudaStream_t st = ctx->stream;
+    const char *pname[3] = {"f64", "f32", "bf16"};
+    // scratch vectors for timing (largest block / whole mesh)
+    size_t maxb = 0;
+    for (auto *b : m->blocks) maxb = std::max(maxb, (size_t)b->d.nelem * b->M);
+    void *x = nullptr, *y = nullptr;
+    if (cudaMalloc(&x, std::max(maxb, (size_t)m->ndof) * 8) != cudaSuccess ||
+        cudaMalloc(&y, std::max(maxb, (size_t)m->ndof) * 8) != cudaSuccess) {
+        if (x) cudaFree(x);
+        return NIR_ERR_NO_MEMORY;
+    }
+    cudaMemsetAsync(x, 0, std::max(maxb, (size_t)m->ndof) * 8, st);
+    int rc = NIR_OK;
+    for (int prec = 0; prec < 2 && !rc; ++prec) {
+        // per-block elements-per-CTA variant and grid size
+        for (auto *b : m->blocks) {
+            char key[160];
+            std::snprintf(key, sizeof key, "%s|block|%d|%d|%d|%s", gpu.c_str(), b->d.shape, b->d.P, b->d.Q,
+                          pname[prec]);
+            auto it = kv.find(key);
+            if (it != kv.end()) {
+                std::sscanf(it->second.c_str(), "%d,%d", &b->helm_variant[prec], &b->helm_grid[prec]);
+                continue;
+            }
+            float best = 1e30f;
+            int bv = 0, bg = 0;
+            for (int v = 0; v < 3 && !rc; ++v) {
+                KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, 5, v);
+                if (!ki.fn || (v > 0 && ki.epb == nir_kinfo(b->d.shape, b->d.P, prec, 5, 0).epb)) continue;
+                int occ = nir_occupancy(ctx, ki);
+                for (int c = 1; c <= std::max(1, occ) && !rc; ++c) {
+                    b->helm_variant[prec] = v;
+                    b->helm_grid[prec] = c * ctx->num_sms;
+                    float t = time_ms(st, 5, [&] {
+                        if (!rc) rc = nir_launch_op(b, prec, 5, 1.0, x, nullptr, nullptr, y, nullptr, nullptr, st, 0);
+                    });
+                    if (t < best) { best = t; bv = v; bg = c * ctx->num_sms; }
+                }
+            }
+            b->helm_variant[prec] = bv;
+            b->helm_grid[prec] = bg;
+            char val[64];
+            std::snprintf(val, sizeof val, "%d,%d", bv, bg);
+            kv[key] = val;
+        }
+        if (rc) break;
+        // persistent mesh kernel: work-item granularity and grid size
+        std::string sig;
+        for (auto *b : m->blocks) sig += std::to_string(b->d.shape) + "." + std::to_string(b->d.P) + "." +
+                                         std::to_string(b->d.nelem) + ";";
+        std::string key = gpu + "|mesh|" + std::to_string(std::hash<std::string>{}(sig)) + "|" + pname[prec];
+        auto it = kv.find(key);
+        int gran = 1, grid = 0;
+        if (it != kv.end()) {
+            std::sscanf(it->second.c_str(), "%d,%d", &gran, &grid);
+            m->ps[prec].grid = grid;
+            rc = nir_mesh_build_items(m, prec, gran);
+            continue;
+        }
+        float best = 1e30f;
+        for (int gr : {1, 2, 4, 8}) {
+            m->ps[prec].grid = 0;
+            rc = nir_mesh_build_items(m, prec, gr);
+            if (rc) break;
+            const int occ = m->ps[prec].occ;
+            for (int c = 1; c <= occ && !rc; ++c) {
+                m->ps[prec].grid = c * ctx->num_sms;
+                nirk::MeshBlk *dblk = nullptr;
+                rc = nir_mesh_block_table(m, prec, 1.0, x, y, &dblk);
+                if (rc) break;
+                float t = time_ms(st, 5, [&] {
+                    if (!rc) rc = nir_mesh_launch_raw(m, prec, dblk, st);
+                });
+                cudaStreamSynchronize(st);
+                cudaFree(dblk);
+                if (t < best) { best = t; gran = gr; grid = c * ctx->num_sms; }
+            }
+        }
+        if (rc) break;
+        m->ps[prec].grid = grid;
+        rc = nir_mesh_build_items(m, prec, gran);
+        char val[64];
+        std::snprintf(val, sizeof val, "%d,%d", gran, grid);
+        kv[key] = val;
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(x);
+    cudaFree(y);
+    if (rc) return rc;
+    if (!write_cache(cache_path, kv)) return NIR_ERR_INVALID_ARG;
+    return NIR_OK;
 }

@@ -1,0 +1,198 @@
+"""GPU tests of the hybrid mesh (one persistent launch, CUDA graphs,
+autotuner) and of the conjugate-gradient Helmholtz solve with FP64 iterative
+refinement, against the FP64 oracle (per-element operator and dense Cholesky)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nir():
+    import paper_2606_20917_gb300 as nir
+    return nir
+
+
+@pytest.fixture(scope="module")
+def ctx(nir):
+    torch.cuda.set_device(0)
+    return nir.Context(0)
+
+
+def build_mesh(nir, ctx, parts):
+    blocks = []
+    for p in parts:
+        b = nir.Block(ctx, p["shape"], p["nodes"].shape[0], p["P"], deformed=p["deformed"])
+        b.set_geometry(p["gorder"], torch.from_numpy(np.ascontiguousarray(p["nodes"])).cuda())
+        blocks.append(b)
+    return nir.Mesh(ctx, blocks), blocks
+
+
+def small_hybrid():
+    return W.hybrid_mesh(seed=0, scale=20)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_mesh_apply_matches_blocks_and_oracle(nir, ctx, prec, tol):
+    parts = small_hybrid()
+    mesh, blocks = build_mesh(nir, ctx, parts)
+    x64 = W.coefficients(1, mesh.ndof, seed=4)[0]
+    x = torch.from_numpy(x64).cuda().to(nir.DTYPE[prec])
+    y = mesh.helmholtz(x, lam=1.0, prec=prec).double().cpu().numpy()
+    for b, o, p in zip(blocks, mesh.offsets, parts):
+        n = b.nelem * b.M
+        xb = x[o:o + n].view(b.nelem, b.M).contiguous()
+        yb = b.helmholtz(xb, lam=1.0, prec=prec).double().cpu().numpy().ravel()
+        # the persistent kernel runs the same element-group code as the block kernel
+        assert np.array_equal(y[o:o + n], yb), (p["shape"], p["P"])
+        ids = W.sample_elements(b.nelem, 8, seed=p["P"])
+        ref = oracle.helmholtz(p["shape"], p["P"], p["Q"], p["gorder"], p["nodes"][ids], 1.0,
+                               x64[o:o + n].reshape(b.nelem, b.M)[ids])
+        assert rel(y[o:o + n].reshape(b.nelem, b.M)[ids], ref) <= tol, (p["shape"], p["P"])
+
+
+def test_mesh_graph_replay_and_buffers(nir, ctx):
+    parts = small_hybrid()
+    mesh, blocks = build_mesh(nir, ctx, parts)
+    out = torch.empty(mesh.ndof, dtype=torch.float64, device="cuda")
+    xa = torch.from_numpy(W.coefficients(1, mesh.ndof, seed=1)[0]).cuda()
+    xb = torch.from_numpy(W.coefficients(1, mesh.ndof, seed=2)[0]).cuda()
+    ya = mesh.helmholtz(xa, out=out).clone()
+    xa.copy_(xb)  # same buffer, new data: the replayed graph must read it
+    yb = mesh.helmholtz(xa, out=out).clone()
+    yc = mesh.helmholtz(xb)  # different buffers: another graph
+    assert not torch.equal(ya, yb)
+    assert torch.equal(yb, yc)
+
+
+def test_tune_and_cache(nir, ctx, tmp_path):
+    parts = small_hybrid()
+    mesh, blocks = build_mesh(nir, ctx, parts)
+    x = torch.from_numpy(W.coefficients(1, mesh.ndof, seed=3)[0]).cuda()
+    before = mesh.helmholtz(x).clone()
+    cache = str(tmp_path / "tune.json")
+    mesh.tune(cache)
+    after = mesh.helmholtz(x)
+    assert torch.equal(before, after)
+    kv = json.load(open(cache))
+    assert any("|mesh|" in k for k in kv) and any("|block|" in k for k in kv)
+    mesh.tune(cache)  # second call reads the cache
+    assert torch.equal(mesh.helmholtz(x), before)
+
+
+def hex_problem(nir, ctx, n=4, P=3, amp=0.05):
+    nodes = W.hex_grid(n, 2, amp=amp)
+    parts = [dict(shape="hex", P=P, Q=P + 2, gorder=2, nodes=nodes, deformed=True)]
+    mesh, blocks = build_mesh(nir, ctx, parts)
+    b = W.coefficients(nodes.shape[0], blocks[0].M, seed=7)
+    x_ref = oracle.helmholtz_solve("hex", P, P + 2, 2, nodes, 1.0, b)
+    return mesh, nodes, b, x_ref
+
+
+def kappa(nodes, P):
+    """Condition number of the block-diagonal operator (all element matrices)."""
+    H = oracle.helmholtz_matrix("hex", P, P + 2, 2, nodes, 1.0)
+    ev = np.concatenate([np.linalg.eigvalsh(h) for h in H])
+    return ev.max() / ev.min()
+
+
+@pytest.mark.parametrize("jacobi", [True, False])
+def test_fp64_cg_matches_dense_cholesky(nir, ctx, jacobi):
+    mesh, nodes, b, x_ref = hex_problem(nir, ctx)
+    bt = torch.from_numpy(b.ravel()).cuda()
+    x = torch.zeros_like(bt)
+    rc, st = mesh.cg_solve(bt, x, inner_prec="f64", tol=1e-12, max_inner=20000, jacobi=jacobi)
+    assert rc == 0, st
+    assert st["rel_residual"] <= 1e-12
+    # forward error is bounded by kappa times the relative residual
+    assert rel(x.cpu().numpy(), x_ref.ravel()) <= 2 * kappa(nodes, 3) * st["rel_residual"] + 1e-14
+
+
+@pytest.mark.parametrize("inner", ["f32", "bf16"])
+def test_mixed_refinement_reaches_fp64_accuracy(nir, ctx, inner):
+    mesh, nodes, b, x_ref = hex_problem(nir, ctx)
+    bt = torch.from_numpy(b.ravel()).cuda()
+    x = torch.zeros_like(bt)
+    rc, st = mesh.cg_solve(bt, x, inner_prec=inner, tol=1e-10, max_outer=60, max_inner=5000, inner_tol=1e-3)
+    if inner == "f32":
+        assert rc == 0, st
+    if rc == 0:
+        assert st["rel_residual"] <= 1e-10
+        xf = torch.zeros_like(bt)
+        rc64, st64 = mesh.cg_solve(bt, xf, inner_prec="f64", tol=1e-10, max_inner=20000)
+        assert rc64 == 0
+        e_mixed = rel(x.cpu().numpy(), x_ref.ravel())
+        e_fp64 = rel(xf.cpu().numpy(), x_ref.ravel())
+        bound = 2 * kappa(nodes, 3) * 1e-10
+        assert e_mixed <= bound and e_fp64 <= bound, (e_mixed, e_fp64, bound)
+    else:
+        assert rc == -4, (rc, st)   # refinement stalls: reported, not hidden
+
+
+def test_cg_on_hybrid_mesh(nir, ctx):
+    parts = small_hybrid()
+    mesh, blocks = build_mesh(nir, ctx, parts)
+    b = torch.from_numpy(W.coefficients(1, mesh.ndof, seed=9)[0]).cuda()
+    x = torch.zeros_like(b)
+    rc, st = mesh.cg_solve(b, x, inner_prec="f32", tol=1e-10, max_outer=60, max_inner=5000, inner_tol=1e-3)
+    assert rc == 0 and st["rel_residual"] <= 1e-10, st
+    # check against the per-element dense solve on a few elements of every block
+    xh = x.cpu().numpy()
+    bh = b.cpu().numpy()
+    for blk, o, p in zip(blocks, mesh.offsets, parts):
+        ids = W.sample_elements(blk.nelem, 3, seed=1)
+        n = blk.nelem * blk.M
+        xr = oracle.helmholtz_solve(p["shape"], p["P"], p["Q"], p["gorder"], p["nodes"][ids], 1.0,
+                                    bh[o:o + n].reshape(blk.nelem, blk.M)[ids])
+        assert rel(xh[o:o + n].reshape(blk.nelem, blk.M)[ids], xr) <= 1e-5
+
+
+def test_cg_failure_reporting(nir, ctx):
+    mesh, nodes, b, x_ref = hex_problem(nir, ctx, n=2, P=2)
+    bt = torch.from_numpy(b.ravel()).cuda()
+    x = torch.zeros_like(bt)
+    rc, st = mesh.cg_solve(bt, x, inner_prec="f64", tol=1e-12, max_inner=3)
+    assert rc == -4 and st["inner_total"] <= 25  # iteration cap -> NOT_CONVERGED
+    bad = bt.clone()
+    bad[5] = float("nan")
+    rc, st = mesh.cg_solve(bad, torch.zeros_like(bt), inner_prec="f32")
+    assert rc == -5  # NaN input -> NONFINITE
+    with pytest.raises(ValueError):
+        mesh.cg_solve(bt.float(), x)
+    rc, _ = mesh.cg_solve(bt, x, lam=-1.0)
+    assert rc == -1
+
+
+def test_graphs_follow_retuning_and_new_geometry(nir, ctx):
+    """Captured graphs (mesh applies and CG chunks) are rebuilt when the work
+    list is re-tuned or a block's geometry is set again."""
+    mesh, nodes, b, x_ref = hex_problem(nir, ctx, n=3, P=2)
+    bt = torch.from_numpy(b.ravel()).cuda()
+    x1 = torch.zeros_like(bt)
+    rc, _ = mesh.cg_solve(bt, x1, inner_prec="f32", tol=1e-10, max_outer=60, max_inner=5000)
+    assert rc == 0
+    mesh.tune(None)
+    x2 = torch.zeros_like(bt)
+    rc, _ = mesh.cg_solve(bt, x2, inner_prec="f32", tol=1e-10, max_outer=60, max_inner=5000)
+    assert rc == 0
+    assert rel(x2.cpu().numpy(), x1.cpu().numpy()) <= 1e-8
+    # move the geometry: the next apply must use the new factors
+    blk = mesh.blocks[0]
+    y_old = mesh.helmholtz(bt).cpu().numpy()
+    moved = W.hex_grid(3, 2, amp=0.02)
+    blk.set_geometry(2, torch.from_numpy(moved).cuda())
+    y_new = mesh.helmholtz(bt).cpu().numpy()
+    ref = oracle.helmholtz("hex", 2, 4, 2, moved, 1.0, b)
+    assert rel(y_new, ref.ravel()) <= 1e-12
+    assert rel(y_old, ref.ravel()) > 1e-6
