@@ -92,6 +92,11 @@ int nir_ctx_create(nir_ctx **out, int device, void *cuda_stream);
 /* Re-target subsequent calls of all blocks of this context to another stream. */
 int nir_ctx_set_stream(nir_ctx *ctx, void *cuda_stream);
 void nir_ctx_destroy(nir_ctx *ctx);
+/* Synchronise the context stream and report device-side failures of earlier
+ * asynchronous calls: kernels never hang on an asynchronous copy; a bounded
+ * wait that runs out sets a device error word and the kernel returns.
+ * Returns NIR_ERR_CUDA (and clears the word) if one was set. */
+int nir_ctx_check(nir_ctx *ctx);
 
 /* Create a block; builds the FP64 basis/quadrature tables (Eqs. basis matrix,
  * bwdsumfachex, bwdsumfactet, stdderiv) and uploads them.  Errors:

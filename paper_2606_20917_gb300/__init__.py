@@ -50,6 +50,7 @@ class CGStats(C.Structure):
 _SIGS = {
     "nir_ctx_create": [C.POINTER(_vp), _i, _vp],
     "nir_ctx_set_stream": [_vp, _vp],
+    "nir_ctx_check": [_vp],
     "nir_block_create": [_vp, C.POINTER(BlockDesc), C.POINTER(_vp)],
     "nir_block_num_modes": [_vp, C.POINTER(_i64)],
     "nir_block_num_points": [_vp, C.POINTER(_i64)],
@@ -122,6 +123,10 @@ class Context:
 
     def set_stream(self, stream: torch.cuda.Stream):
         _chk(_lib.nir_ctx_set_stream(self.h, _stream_handle(stream)), "nir_ctx_set_stream")
+
+    def check(self):
+        """Synchronise and raise if a kernel reported a device-side failure."""
+        _chk(_lib.nir_ctx_check(self.h), "nir_ctx_check")
 
     def probe_fp64_peak(self) -> float:
         v = _d()

@@ -121,8 +121,13 @@ int nir_launch_op(nir_block *b, int prec, int op, double lambda, const void *in0
     a.nelem = b->d.nelem;
     a.lambda = lambda;
     a.geo_pp = b->geo_pp;
-    a.pad = 0;
-    void *args[] = {&a};
+    a.pf = (op == nirk::OP_HELM && prec >= 0 && prec < 3) ? b->helm_pf[prec] : 0;
+    a.err = b->ctx->derr;
+    // the kernel's second parameter is the table blob in its compute type
+    const void *tabp = (prec == NIR_F64) ? (const void *)b->tab_h.data() : (const void *)b->tab32_h.data();
+    if ((size_t)ki.tabp_bytes != (prec == NIR_F64 ? b->tab_h.size() * 8 : b->tab32_h.size() * 4))
+        return NIR_ERR_UNSUPPORTED;
+    void *args[] = {&a, const_cast<void *>(tabp)};
     if (cudaLaunchKernel(ki.fn, dim3((unsigned)grid), dim3(ki.nt), args, (size_t)ki.smem, stream) != cudaSuccess) {
         (void)cudaGetLastError();  // consume the launch error so it does not surface in a later call
         return NIR_ERR_CUDA;
@@ -142,7 +147,9 @@ extern "C" int nir_ctx_create(nir_ctx **out, int device, void *stream)
     if (!c) return NIR_ERR_NO_MEMORY;
     c->device = device;
     c->stream = (cudaStream_t)stream;
-    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMalloc(&c->derr, sizeof(int)) != cudaSuccess || cudaMemset(c->derr, 0, sizeof(int)) != cudaSuccess) {
+        if (c->derr) cudaFree(c->derr);
         delete c;
         return NIR_ERR_CUDA;
     }
@@ -157,7 +164,26 @@ extern "C" int nir_ctx_set_stream(nir_ctx *ctx, void *stream)
     return NIR_OK;
 }
 
-extern "C" void nir_ctx_destroy(nir_ctx *ctx) { delete ctx; }
+extern "C" void nir_ctx_destroy(nir_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->derr) cudaFree(ctx->derr);
+    delete ctx;
+}
+
+extern "C" int nir_ctx_check(nir_ctx *ctx)
+{
+    if (!ctx) return NIR_ERR_INVALID_ARG;
+    NIR_CUDA_TRY(cudaSetDevice(ctx->device));
+    int h = 0;
+    NIR_CUDA_TRY(cudaMemcpyAsync(&h, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    NIR_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (h) {
+        NIR_CUDA_TRY(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->stream));
+        return NIR_ERR_CUDA;
+    }
+    return NIR_OK;
+}
 
 // --------------------------------------------------------------------------- blocks
 extern "C" int nir_block_create(nir_ctx *ctx, const nir_block_desc *d, nir_block **out)
@@ -184,8 +210,9 @@ extern "C" int nir_block_create(nir_ctx *ctx, const nir_block_desc *d, nir_block
         delete b;
         return NIR_ERR_CUDA;
     }
-    std::vector<float> t32(ntab);
-    for (int i = 0; i < ntab; ++i) t32[i] = (float)b->tab_h[i];
+    b->tab32_h.resize(ntab);
+    for (int i = 0; i < ntab; ++i) b->tab32_h[i] = (float)b->tab_h[i];
+    const std::vector<float> &t32 = b->tab32_h;
     if (cudaSetDevice(ctx->device) != cudaSuccess || cudaMalloc(&b->tab64, ntab * 8) != cudaSuccess ||
         cudaMalloc(&b->tab32, ntab * 4) != cudaSuccess) {
         nir_block_destroy(b);

@@ -27,10 +27,17 @@ KInfo make1()
 {
     using C = Config<NIR_SHAPE, N, N + 1, TT, OP, EPB>;
     KInfo k;
-    k.fn = reinterpret_cast<const void *>(&k_elem<NIR_SHAPE, N, N + 1, TT, OP, EPB>);
-    k.smem = C::SMEM;
+    if constexpr (C::FUSED) {  // FP32/BF16 Helmholtz: bulk-copy staged kernel
+        constexpr int stg = ((C::EPB * C::M * (int)sizeof(TT) + 15) / 16) * 16;
+        k.fn = reinterpret_cast<const void *>(&k_helm_tma<NIR_SHAPE, N, N + 1, TT, EPB>);
+        k.smem = C::SMEM + stg;
+    } else {
+        k.fn = reinterpret_cast<const void *>(&k_elem<NIR_SHAPE, N, N + 1, TT, OP, EPB>);
+        k.smem = C::SMEM;
+    }
     k.epb = C::EPB;
     k.nt = C::NT;
+    k.tabp_bytes = C::TABN * (int)sizeof(typename C::A);
     return k;
 }
 
@@ -42,7 +49,8 @@ KInfo make(int variant)
     using C0 = Config<NIR_SHAPE, N, N + 1, TT, OP, 0>;
     constexpr int e0 = C0::EPB;
     constexpr int eh = e0 > 1 ? e0 / 2 : 1;
-    constexpr int ed = (C0::TABB + 2 * C0::BUFB <= 227 * 1024 && e0 < 64) ? 2 * e0 : e0;
+    constexpr int stg2 = C0::FUSED ? ((2 * e0 * C0::M * (int)sizeof(TT) + 15) / 16) * 16 : 0;
+    constexpr int ed = (C0::TABB + 2 * C0::BUFB + stg2 <= 227 * 1024 && e0 < 64) ? 2 * e0 : e0;
     if constexpr (OP == OP_HELM) {
         if (variant == 1) return make1<N, OP, eh>();
         if (variant == 2) return make1<N, OP, ed>();

@@ -21,6 +21,7 @@ struct KInfo {
     int smem = 0;              // dynamic shared memory bytes
     int epb = 0;               // elements per CTA group
     int nt = 0;                // threads per CTA
+    int tabp_bytes = 0;        // size of the table parameter (compute type)
 };
 
 // Provided by the instantiation units (one per shape x precision).
@@ -30,6 +31,7 @@ struct nir_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
+    int *derr = nullptr;                    // device error word of bounded in-kernel waits
     std::mutex mu;
     std::map<const void *, int> occupancy;  // CTAs per SM per kernel
     std::map<std::string, int> tuned_grid;  // autotuner overrides (key: shape/P/prec/op)
@@ -41,11 +43,13 @@ struct nir_block {
     int dim = 0, N = 0, M = 0, NQ = 0, ng = 0, nl = 0;
     long long epad = 0;                       // element count padded to 64
     std::vector<double> tab_h;                // FP64 table blob (host)
+    std::vector<float> tab32_h;               // the same tables rounded to FP32 (host)
     double *tab64 = nullptr;                  // table blob, device, FP64
     float *tab32 = nullptr;                   // table blob, device, FP32
     int geo_pp = 1;                           // per-point (1) or per-element (0) factors
     int helm_variant[3] = {0, 0, 0};          // tuned elements-per-CTA variant per precision
     int helm_grid[3] = {0, 0, 0};             // tuned grid size per precision (0: occupancy)
+    int helm_pf[3] = {0, 0, 0};               // tuned L2 metric-prefetch policy per precision
     bool geo_set = false;
     unsigned geo_version = 0;                 // bumped by every nir_block_set_geometry
     double *G64 = nullptr, *L64 = nullptr;    // metric (ng) and d eta/d x + W (nl)

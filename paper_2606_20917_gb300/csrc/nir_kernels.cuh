@@ -50,7 +50,8 @@ struct KArgs {
     long long nelem;
     double lambda;
     int geo_pp;                   // 1: per point, 32-element interleaved; 0: per element
-    int pad;
+    int pf;                       // FP32/BF16 Helmholtz: 1 = bulk-prefetch the group's metric into L2
+    int *err;                     // device error word (bounded waits that gave up set it)
 };
 
 template <class T> struct CT { using type = float; };
@@ -120,6 +121,24 @@ __device__ __forceinline__ void pencils(int per_e, int &rot, LD ld, TB tb, LDX l
     rot += total;
 }
 
+// Work-item loop shared by the fused stages: items are (element e, index s)
+// with e fastest across lanes; the loop bound is hidden from the compiler and
+// z is a loop-local zero for shared-memory table offsets (see pencils()).
+template <int EPB, int NT, class F>
+__device__ __forceinline__ void for_items(int per_e, int &rot, F f)
+{
+    int total = per_e * EPB;
+    asm volatile("mov.u32 %0, %0;" : "+r"(total));
+    int w = (int)threadIdx.x - (rot % NT);
+    if (w < 0) w += NT;
+    for (; w < total; w += NT) {
+        int z;
+        asm volatile("mov.u32 %0, 0;" : "=r"(z));
+        f(w % EPB, w / EPB, z);
+    }
+    rot += total;
+}
+
 struct NoX {
     template <class A> __device__ void operator()(int, int, A *) const {}
 };
@@ -133,6 +152,32 @@ __device__ __forceinline__ void pencils0(int per_e, int &rot, LD ld, TB tb, ST s
     pencils<A, NIN, NOUT, 0, 0, EPB, NT>(per_e, rot, ld, tb, NoX{}, [](int, int) { return A(0); }, st);
 }
 
+// Table accessors.  Tables live either in shared memory (the persistent mesh
+// kernel, whose blocks have different tables) or in the kernel-parameter
+// constant bank (single-block kernels, passed as a __grid_constant__ struct):
+// there, fully unrolled contractions read table entries as constant operands
+// with no load instruction.  z is the loop-local zero of pencils() (only the
+// shared-memory accessor uses it).
+template <class A>
+struct STab {
+    const A *p;
+    __device__ __forceinline__ STab operator+(int o) const { return STab{p + o}; }
+    __device__ __forceinline__ A operator()(int z, int i) const { return p[z + i]; }
+};
+
+template <class A, int NTAB>
+struct TabP {
+    A v[NTAB];
+};
+
+template <class A, int NTAB>
+struct PTab {
+    const TabP<A, NTAB> *t;
+    int base;
+    __device__ __forceinline__ PTab operator+(int o) const { return PTab{t, base + o}; }
+    __device__ __forceinline__ A operator()(int, int i) const { return t->v[base + i]; }
+};
+
 // ---------------------------------------------------------------------------
 // Modal <-> quadrature stages per shape.  Buffers: element e, index i at
 // buf[e*S + i].  bwd: p0 (modes) -> p1 -> p2 (-> p3) (points);
@@ -143,11 +188,13 @@ struct Modal {
     static constexpr TabLayout L = layout(SH, N, Q);
     static constexpr int QQ = Q * Q;
 
-    static __device__ __forceinline__ void bwd(const A *tab, A *p0, A *p1, A *p2, A *p3)
+    // All BwdTrans stages but the last: 2-D p0 -> p1; 3-D p0 -> p1 -> p2.
+    template <class TP>
+    static __device__ __forceinline__ void front(TP tab, A *p0, A *p1, A *p2)
     {
-        const A *Ba = tab + L.Ba;
+        const TP Ba = tab + L.Ba;
         int rot = 0;
-        auto tBa = [=](int z, int o, int r) { return Ba[z + o * N + r]; };
+        auto tBa = [=](int z, int o, int r) { return Ba(z, o * N + r); };
         if constexpr (SH == QUAD || SH == TRI) {
             if constexpr (SH == QUAD) {
                 // t1[p][j] = sum_q u[p][q] psiA_q(z_j)
@@ -162,24 +209,17 @@ struct Modal {
                     constexpr int p = decltype(cc)::value;
                     constexpr int nc = N - p;
                     constexpr int nin = nc + (p == 1 ? 1 : 0);
-                    const A *Bp = tab + L.Bb + cls_off(N, Q, p);
-                    const A *B0 = tab + L.Bb;
+                    const TP Bp = tab + L.Bb + cls_off(N, Q, p);
+                    const TP B0 = tab + L.Bb;
                     pencils0<A, nin, Q, EPB, NT>(1, rot,
                         [=](int e, int, A *x) { const A *b = p0 + e * S + tri_m0(N, p);
 #pragma unroll
                             for (int r = 0; r < nc; ++r) x[r] = b[r];
                             if constexpr (p == 1) x[nc] = p0[e * S + 1]; },
-                        [=](int z, int o, int r) { return (p == 1 && r == nc) ? B0[z + o * N + 1] : Bp[z + o * nc + r]; },
+                        [=](int z, int o, int r) { return (p == 1 && r == nc) ? B0(z, o * N + 1) : Bp(z, o * nc + r); },
                         [=](int e, int, int o, A v) { p1[e * S + p * Q + o] = v; });
                 });
             }
-            __syncthreads();
-            // u[i + Q j] = sum_p psiA_p(z_i) t1[p][j]
-            pencils0<A, N, Q, EPB, NT>(Q, rot,
-                [=](int e, int s, A *x) { const A *b = p1 + e * S + s;
-#pragma unroll
-                    for (int r = 0; r < N; ++r) x[r] = b[r * Q]; },
-                tBa, [=](int e, int s, int o, A v) { p2[e * S + o + Q * s] = v; });
             __syncthreads();
         } else {
             // ---- stage 1: contract the third mode index r -> k
@@ -195,14 +235,14 @@ struct Modal {
                     constexpr int p = decltype(cc)::value;
                     constexpr int nc = N - p;
                     constexpr int nin = nc + (p == 1 ? 1 : 0);
-                    const A *Bp = tab + L.Bb + cls_off(N, Q, p);
-                    const A *B0 = tab + L.Bb;
+                    const TP Bp = tab + L.Bb + cls_off(N, Q, p);
+                    const TP B0 = tab + L.Bb;
                     pencils0<A, nin, Q, EPB, NT>(N, rot,
                         [=](int e, int q, A *x) { const A *b = p0 + e * S + prism_m0(N, p, q);
 #pragma unroll
                             for (int r = 0; r < nc; ++r) x[r] = b[r];
                             if constexpr (p == 1) x[nc] = p0[e * S + prism_m0(N, 0, q) + 1]; },
-                        [=](int z, int o, int r) { return (p == 1 && r == nc) ? B0[z + o * N + 1] : Bp[z + o * nc + r]; },
+                        [=](int z, int o, int r) { return (p == 1 && r == nc) ? B0(z, o * N + 1) : Bp(z, o * nc + r); },
                         [=](int e, int q, int o, A v) { p1[e * S + (p * N + q) * Q + o] = v; });
                 });
             } else {  // TET
@@ -212,14 +252,14 @@ struct Modal {
                     constexpr int c = decltype(cc)::value;
                     constexpr int nc = N - c;
                     constexpr int nin = nc + (c == 1 ? 1 : 0);
-                    const A *Bc = tab + L.Bc + cls_off(N, Q, c);
-                    const A *B0 = tab + L.Bc;
+                    const TP Bc = tab + L.Bc + cls_off(N, Q, c);
+                    const TP B0 = tab + L.Bc;
                     pencils0<A, nin, Q, EPB, NT>(c + 1, rot,
                         [=](int e, int p, A *x) { const A *b = p0 + e * S + tet_m0(N, p, c - p);
 #pragma unroll
                             for (int r = 0; r < nc; ++r) x[r] = b[r];
                             if constexpr (c == 1) x[nc] = p0[e * S + 1]; },
-                        [=](int z, int o, int r) { return (c == 1 && r == nc) ? B0[z + o * N + 1] : Bc[z + o * nc + r]; },
+                        [=](int z, int o, int r) { return (c == 1 && r == nc) ? B0(z, o * N + 1) : Bc(z, o * nc + r); },
                         [=](int e, int p, int o, A v) { p1[e * S + tet_pair(N, p, c - p) * Q + o] = v; });
                 });
             }
@@ -238,78 +278,56 @@ struct Modal {
                     constexpr int p = decltype(cc)::value;
                     constexpr int nc = N - p;
                     constexpr int nin = nc + (p == 1 ? 1 : 0);
-                    const A *Bp = tab + L.Bb + cls_off(N, Q, p);
-                    const A *B0 = tab + L.Bb;
+                    const TP Bp = tab + L.Bb + cls_off(N, Q, p);
+                    const TP B0 = tab + L.Bb;
                     pencils0<A, nin, Q, EPB, NT>(Q, rot,
                         [=](int e, int k, A *x) { const A *b = p1 + e * S + tet_pair(N, p, 0) * Q + k;
 #pragma unroll
                             for (int r = 0; r < nc; ++r) x[r] = b[r * Q];
                             if constexpr (p == 1) x[nc] = p1[e * S + tet_pair(N, 0, 1) * Q + k]; },
-                        [=](int z, int o, int r) { return (p == 1 && r == nc) ? B0[z + o * N + 1] : Bp[z + o * nc + r]; },
+                        [=](int z, int o, int r) { return (p == 1 && r == nc) ? B0(z, o * N + 1) : Bp(z, o * nc + r); },
                         [=](int e, int k, int o, A v) { p2[e * S + (p * Q + o) * Q + k] = v; });
                 });
             }
             __syncthreads();
-            // ---- stage 3: contract p -> i; u[i + Q j + Q^2 k]
-            pencils0<A, N, Q, EPB, NT>(QQ, rot,
-                [=](int e, int s, A *x) { const int k = s / Q, j = s - k * Q;
-                    const A *b = p2 + e * S + j * Q + k;
-#pragma unroll
-                    for (int r = 0; r < N; ++r) x[r] = b[r * QQ]; },
-                tBa, [=](int e, int s, int o, A v) { p3[e * S + o + Q * s] = v; });
-            __syncthreads();
         }
     }
 
-    // Transposed stages: p0 (points, weights already applied) -> modes in `last`.
-    static __device__ __forceinline__ void iprod(const A *tab, A *p0, A *p1, A *p2, A *last)
+    // All transposed stages but the first: 2-D p1 -> last; 3-D p1 -> p2 -> last.
+    template <class TP>
+    static __device__ __forceinline__ void back(TP tab, A *p1, A *p2, A *outm)
     {
-        const A *Ba = tab + L.Ba;
+        const TP Ba = tab + L.Ba;
         int rot = 0;
-        auto tBaT = [=](int z, int o, int r) { return Ba[z + r * N + o]; };
+        auto tBaT = [=](int z, int o, int r) { return Ba(z, r * N + o); };
         if constexpr (SH == QUAD || SH == TRI) {
-            // t1[p][j] = sum_i psiA_p(z_i) f[i + Q j]
-            pencils0<A, Q, N, EPB, NT>(Q, rot,
-                [=](int e, int s, A *x) { const A *b = p0 + e * S + Q * s;
-#pragma unroll
-                    for (int r = 0; r < Q; ++r) x[r] = b[r]; },
-                tBaT, [=](int e, int s, int o, A v) { p1[e * S + o * Q + s] = v; });
-            __syncthreads();
             if constexpr (SH == QUAD) {
                 pencils0<A, Q, N, EPB, NT>(N, rot,
                     [=](int e, int s, A *x) { const A *b = p1 + e * S + s * Q;
 #pragma unroll
                         for (int r = 0; r < Q; ++r) x[r] = b[r]; },
-                    tBaT, [=](int e, int s, int o, A v) { last[e * S + s * N + o] = v; });
+                    tBaT, [=](int e, int s, int o, A v) { outm[e * S + s * N + o] = v; });
             } else {
                 sfor<0, N>([&](auto cc) {
                     constexpr int p = decltype(cc)::value;
                     constexpr int nc = N - p;
                     constexpr int nex = (p == 0 && N > 1) ? Q : 0;
-                    const A *Bp = tab + L.Bb + cls_off(N, Q, p);
-                    const A *B0 = tab + L.Bb;
+                    const TP Bp = tab + L.Bb + cls_off(N, Q, p);
+                    const TP B0 = tab + L.Bb;
                     pencils<A, Q, nc, nex, 1, EPB, NT>(1, rot,
                         [=](int e, int, A *x) { const A *b = p1 + e * S + p * Q;
 #pragma unroll
                             for (int r = 0; r < Q; ++r) x[r] = b[r]; },
-                        [=](int z, int o, int r) { return Bp[z + r * nc + o]; },
+                        [=](int z, int o, int r) { return Bp(z, r * nc + o); },
                         [=](int e, int, A *xx) { const A *b = p1 + e * S + 1 * Q;   // the (0,1) vertex: p = 1 line
 #pragma unroll
                             for (int r = 0; r < nex; ++r) xx[r] = b[r]; },
-                        [=](int z, int r) { return B0[z + r * N + 1]; },
-                        [=](int e, int, int o, A v) { last[e * S + tri_m0(N, p) + o] = v; });
+                        [=](int z, int r) { return B0(z, r * N + 1); },
+                        [=](int e, int, int o, A v) { outm[e * S + tri_m0(N, p) + o] = v; });
                 });
             }
             __syncthreads();
         } else {
-            // ---- transpose of stage 3: t2[p][j][k] = sum_i psiA_p(z_i) f[i + Q j + Q^2 k]
-            pencils0<A, Q, N, EPB, NT>(QQ, rot,
-                [=](int e, int s, A *x) { const A *b = p0 + e * S + Q * s;
-#pragma unroll
-                    for (int r = 0; r < Q; ++r) x[r] = b[r]; },
-                tBaT, [=](int e, int s, int o, A v) { const int k = s / Q, j = s - k * Q;
-                    p1[e * S + o * QQ + j * Q + k] = v; });
-            __syncthreads();
             // ---- transpose of stage 2
             if constexpr (SH == HEX || SH == PRISM) {
                 pencils0<A, Q, N, EPB, NT>(N * Q, rot,
@@ -324,17 +342,17 @@ struct Modal {
                     constexpr int p = decltype(cc)::value;
                     constexpr int nc = N - p;
                     constexpr int nex = (p == 0 && N > 1) ? Q : 0;
-                    const A *Bp = tab + L.Bb + cls_off(N, Q, p);
-                    const A *B0 = tab + L.Bb;
+                    const TP Bp = tab + L.Bb + cls_off(N, Q, p);
+                    const TP B0 = tab + L.Bb;
                     pencils<A, Q, nc, nex, 1, EPB, NT>(Q, rot,
                         [=](int e, int k, A *x) { const A *b = p1 + e * S + p * QQ + k;
 #pragma unroll
                             for (int r = 0; r < Q; ++r) x[r] = b[r * Q]; },
-                        [=](int z, int o, int r) { return Bp[z + r * nc + o]; },
+                        [=](int z, int o, int r) { return Bp(z, r * nc + o); },
                         [=](int e, int k, A *xx) { const A *b = p1 + e * S + 1 * QQ + k;
 #pragma unroll
                             for (int r = 0; r < nex; ++r) xx[r] = b[r * Q]; },
-                        [=](int z, int r) { return B0[z + r * N + 1]; },
+                        [=](int z, int r) { return B0(z, r * N + 1); },
                         [=](int e, int k, int o, A v) { p2[e * S + (tet_pair(N, p, 0) + o) * Q + k] = v; });
                 });
             }
@@ -345,50 +363,116 @@ struct Modal {
                     [=](int e, int s, A *x) { const A *b = p2 + e * S + s * Q;
 #pragma unroll
                         for (int r = 0; r < Q; ++r) x[r] = b[r]; },
-                    tBaT, [=](int e, int s, int o, A v) { last[e * S + s * N + o] = v; });
+                    tBaT, [=](int e, int s, int o, A v) { outm[e * S + s * N + o] = v; });
             } else if constexpr (SH == PRISM) {
                 sfor<0, N>([&](auto cc) {
                     constexpr int p = decltype(cc)::value;
                     constexpr int nc = N - p;
                     constexpr int nex = (p == 0 && N > 1) ? Q : 0;
-                    const A *Bp = tab + L.Bb + cls_off(N, Q, p);
-                    const A *B0 = tab + L.Bb;
+                    const TP Bp = tab + L.Bb + cls_off(N, Q, p);
+                    const TP B0 = tab + L.Bb;
                     pencils<A, Q, nc, nex, 1, EPB, NT>(N, rot,
                         [=](int e, int q, A *x) { const A *b = p2 + e * S + (p * N + q) * Q;
 #pragma unroll
                             for (int r = 0; r < Q; ++r) x[r] = b[r]; },
-                        [=](int z, int o, int r) { return Bp[z + r * nc + o]; },
+                        [=](int z, int o, int r) { return Bp(z, r * nc + o); },
                         [=](int e, int q, A *xx) { const A *b = p2 + e * S + (1 * N + q) * Q;
 #pragma unroll
                             for (int r = 0; r < nex; ++r) xx[r] = b[r]; },
-                        [=](int z, int r) { return B0[z + r * N + 1]; },
-                        [=](int e, int q, int o, A v) { last[e * S + prism_m0(N, p, q) + o] = v; });
+                        [=](int z, int r) { return B0(z, r * N + 1); },
+                        [=](int e, int q, int o, A v) { outm[e * S + prism_m0(N, p, q) + o] = v; });
                 });
             } else {  // TET: the top vertex (0,0,1) collects pairs (0,1) and (1,0)
                 sfor<0, N>([&](auto cc) {
                     constexpr int c = decltype(cc)::value;
                     constexpr int nc = N - c;
                     constexpr int nex = (c == 0 && N > 1) ? 2 * Q : 0;
-                    const A *Bc = tab + L.Bc + cls_off(N, Q, c);
-                    const A *B0 = tab + L.Bc;
+                    const TP Bc = tab + L.Bc + cls_off(N, Q, c);
+                    const TP B0 = tab + L.Bc;
                     pencils<A, Q, nc, nex, 1, EPB, NT>(c + 1, rot,
                         [=](int e, int p, A *x) { const A *b = p2 + e * S + tet_pair(N, p, c - p) * Q;
 #pragma unroll
                             for (int r = 0; r < Q; ++r) x[r] = b[r]; },
-                        [=](int z, int o, int r) { return Bc[z + r * nc + o]; },
+                        [=](int z, int o, int r) { return Bc(z, r * nc + o); },
                         [=](int e, int, A *xx) {
                             const A *b1 = p2 + e * S + tet_pair(N, 0, 1) * Q;
                             const A *b2 = p2 + e * S + tet_pair(N, 1, 0) * Q;
 #pragma unroll
                             for (int r = 0; r < nex / 2; ++r) { xx[r] = b1[r]; xx[r + nex / 2] = b2[r]; } },
-                        [=](int z, int r) { return B0[z + (r % Q) * N + 1]; },
-                        [=](int e, int p, int o, A v) { last[e * S + tet_m0(N, p, c - p) + o] = v; });
+                        [=](int z, int r) { return B0(z, (r % Q) * N + 1); },
+                        [=](int e, int p, int o, A v) { outm[e * S + tet_m0(N, p, c - p) + o] = v; });
                 });
             }
             __syncthreads();
         }
     }
+    // Last BwdTrans stage (common to all shapes of a dimension):
+    // 2-D u[i + Q j] = sum_p psiA_p(z_i) t1[p][j]; 3-D u[i + Q j + Q^2 k] = sum_p psiA_p(z_i) t2[p][j][k].
+    template <class TP>
+    static __device__ __forceinline__ void last(TP tab, A *in, A *out)
+    {
+        const TP Ba = tab + L.Ba;
+        int rot = 0;
+        auto tBa = [=](int z, int o, int r) { return Ba(z, o * N + r); };
+        if constexpr (SH == QUAD || SH == TRI) {
+            pencils0<A, N, Q, EPB, NT>(Q, rot,
+                [=](int e, int s, A *x) { const A *b = in + e * S + s;
+#pragma unroll
+                    for (int r = 0; r < N; ++r) x[r] = b[r * Q]; },
+                tBa, [=](int e, int s, int o, A v) { out[e * S + o + Q * s] = v; });
+        } else {
+            pencils0<A, N, Q, EPB, NT>(QQ, rot,
+                [=](int e, int s, A *x) { const int k = s / Q, j = s - k * Q;
+                    const A *b = in + e * S + j * Q + k;
+#pragma unroll
+                    for (int r = 0; r < N; ++r) x[r] = b[r * QQ]; },
+                tBa, [=](int e, int s, int o, A v) { out[e * S + o + Q * s] = v; });
+        }
+        __syncthreads();
+    }
+
+    // First transposed stage (common): t[p][j](k) = sum_i psiA_p(z_i) f[i + Q j (+ Q^2 k)].
+    template <class TP>
+    static __device__ __forceinline__ void first(TP tab, A *in, A *out)
+    {
+        const TP Ba = tab + L.Ba;
+        int rot = 0;
+        auto tBaT = [=](int z, int o, int r) { return Ba(z, r * N + o); };
+        if constexpr (SH == QUAD || SH == TRI) {
+            pencils0<A, Q, N, EPB, NT>(Q, rot,
+                [=](int e, int s, A *x) { const A *b = in + e * S + Q * s;
+#pragma unroll
+                    for (int r = 0; r < Q; ++r) x[r] = b[r]; },
+                tBaT, [=](int e, int s, int o, A v) { out[e * S + o * Q + s] = v; });
+        } else {
+            pencils0<A, Q, N, EPB, NT>(QQ, rot,
+                [=](int e, int s, A *x) { const A *b = in + e * S + Q * s;
+#pragma unroll
+                    for (int r = 0; r < Q; ++r) x[r] = b[r]; },
+                tBaT, [=](int e, int s, int o, A v) { const int k = s / Q, j = s - k * Q;
+                    out[e * S + o * QQ + j * Q + k] = v; });
+        }
+        __syncthreads();
+    }
+
+    // BwdTrans: p0 (modes) -> 2-D: p1 -> p2 (points); 3-D: p1 -> p2 -> p3 (points).
+    template <class TP>
+    static __device__ __forceinline__ void bwd(TP tab, A *p0, A *p1, A *p2, A *p3)
+    {
+        front(tab, p0, p1, p2);
+        if constexpr (SH == QUAD || SH == TRI) last(tab, p1, p2);
+        else last(tab, p2, p3);
+    }
+
+    // Transposed: p0 (points, weights applied) -> p1 (-> p2) -> modes in `lastbuf`.
+    template <class TP>
+    static __device__ __forceinline__ void iprod(TP tab, A *p0, A *p1, A *p2, A *lastbuf)
+    {
+        first(tab, p0, p1);
+        back(tab, p1, p2, lastbuf);
+    }
 };
+
 
 // ---------------------------------------------------------------------------
 // Geometry access.  Per-point arrays are interleaved by 32 elements:
@@ -421,16 +505,20 @@ struct Config {
     static constexpr int NQ = npts(SH, Q);
     static constexpr int M = nmodes(SH, N);
     static constexpr int S = odd_stride(NQ);
-    static constexpr int NBUF = (OP == OP_BWD || OP == OP_IPROD || OP == OP_MASS) ? 2 : D + 1;
+    // the fused FP32/BF16 Helmholtz recomputes du/d eta3 in registers: 3 buffers
+    static constexpr bool FUSED = (OP == OP_HELM && sizeof(A) == 4);
+    static constexpr int NBUF = (OP == OP_BWD || OP == OP_IPROD || OP == OP_MASS) ? 2 : FUSED ? 3 : D + 1;
     static constexpr int TABN = layout(SH, N, Q).total;
     static constexpr int TABB = ((TABN * (int)sizeof(A) + 15) / 16) * 16;
-    static constexpr int budget = sizeof(A) == 8 ? 110 * 1024 : 56 * 1024;
+    // FP32/BF16 aim at >= 32 elements so a warp covers one structural index of
+    // 32 elements (conflict-free with the odd stride); FP64 keeps ~110 KB.
+    static constexpr int budget = sizeof(A) == 8 ? 110 * 1024 : 100 * 1024;
     static constexpr int per_elem = NBUF * S * (int)sizeof(A);
     static constexpr int raw = (budget - TABB) / per_elem;
     static constexpr int EPB_DEF = raw >= 64 ? 64 : raw >= 32 ? 32 : raw >= 16 ? 16 : raw >= 8 ? 8 : raw >= 4 ? 4
                                  : raw >= 2 ? 2 : 1;
     static constexpr int EPB = EPB_ > 0 ? EPB_ : EPB_DEF;
-    static constexpr int NT = 256;
+    static constexpr int NT = FUSED ? 512 : 256;
     static constexpr int BUFB = NBUF * EPB * S * (int)sizeof(A);
     static constexpr int SMEM = TABB + BUFB;
 };
@@ -503,7 +591,222 @@ __device__ __forceinline__ A dcolT(const A *V0, const A *V1, const A *V2, const 
     return acc;
 }
 
-// Helmholtz metric stage: v_i = sum_j G_ij du_j at every point of the group.
+// ---------------------------------------------------------------------------
+// Fused Helmholtz stages (register-blocked pencils).  3-D buffers:
+//   in (t2) -> U = u, V1 = du/d eta1      last BwdTrans stage + D1
+//   U -> V2 = du/d eta2                  middle gradient direction
+//   pencils along k: du/d eta3 = D3 u in registers, per point v = G du and
+//   m = lambda W u, then U = m + D3^T v3
+//   U += D2^T v2 (pencils along j)
+//   y = U + D1^T v1, t2 = B1^T y (pencils along i) -> first IProduct stage
+// 2-D drops the middle direction.  Every pencil loads its line once and
+// produces a whole output line from registers.
+// ---------------------------------------------------------------------------
+template <int SH, int N, int Q, class A, int EPB, int NT, int S>
+struct HelmStages {
+    static constexpr TabLayout L = layout(SH, N, Q);
+    static constexpr int D = dim(SH);
+    static constexpr int QQ = Q * Q;
+    static constexpr int PER = D == 3 ? QQ : Q;  // pencils per direction per element
+
+    template <class TP>
+    static __device__ __forceinline__ void last_grad1(TP tab, const A *in, A *U, A *V1)
+    {
+        const TP Ba = tab + L.Ba, D1 = tab + L.D1;
+        int rot = 0;
+        for_items<EPB, NT>(PER, rot, [&](int e, int s, int z) {
+            A x[N];
+            if constexpr (D == 3) {
+                const int k = s / Q, j = s - k * Q;
+                const A *b = in + e * S + j * Q + k;
+#pragma unroll
+                for (int r = 0; r < N; ++r) x[r] = b[r * QQ];
+            } else {
+                const A *b = in + e * S + s;
+#pragma unroll
+                for (int r = 0; r < N; ++r) x[r] = b[r * Q];
+            }
+            A u[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                A acc = A(0);
+#pragma unroll
+                for (int r = 0; r < N; ++r) acc = fmaa(Ba(z, i * N + r), x[r], acc);
+                u[i] = acc;
+                U[e * S + i + Q * s] = acc;
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                A acc = A(0);
+#pragma unroll
+                for (int r = 0; r < Q; ++r) acc = fmaa(D1(z, i * Q + r), u[r], acc);
+                V1[e * S + i + Q * s] = acc;
+            }
+        });
+        __syncthreads();
+    }
+
+    // d/d eta2 (3-D: pencils along j; 2-D: pencils along j of the 2-D grid).
+    // The 3-D d/d eta3 is formed in registers by metric_tlast.
+    template <class TP>
+    static __device__ __forceinline__ void grad_rest(TP tab, const A *U, A *V2)
+    {
+        const TP D2 = tab + L.D2;
+        int rot = 0;
+        if constexpr (D == 3) {
+            for_items<EPB, NT>(QQ, rot, [&](int e, int s, int z) {  // along j: s = i + Q k
+                const int k = s / Q, i = s - k * Q;
+                const A *b = U + e * S + i + QQ * k;
+                A x[Q];
+#pragma unroll
+                for (int r = 0; r < Q; ++r) x[r] = b[r * Q];
+#pragma unroll
+                for (int o = 0; o < Q; ++o) {
+                    A acc = A(0);
+#pragma unroll
+                    for (int r = 0; r < Q; ++r) acc = fmaa(D2(z, o * Q + r), x[r], acc);
+                    V2[e * S + i + Q * o + QQ * k] = acc;
+                }
+            });
+        } else {
+            for_items<EPB, NT>(Q, rot, [&](int e, int s, int z) {  // along j: s = i
+                const A *b = U + e * S + s;
+                A x[Q];
+#pragma unroll
+                for (int r = 0; r < Q; ++r) x[r] = b[r * Q];
+#pragma unroll
+                for (int o = 0; o < Q; ++o) {
+                    A acc = A(0);
+#pragma unroll
+                    for (int r = 0; r < Q; ++r) acc = fmaa(D2(z, o * Q + r), x[r], acc);
+                    V2[e * S + s + Q * o] = acc;
+                }
+            });
+        }
+        __syncthreads();
+    }
+
+    // Per point v = G du (G holds W and the chain rule; per-element factors
+    // are scaled by the reference weight) and m = lambda W u; the pencil along
+    // the last direction then writes U = m + D_last^T v_last.
+    template <bool PP, class TP, class GEO>
+    static __device__ __forceinline__ void metric_tlast(TP tab, const GEO &geo, long long e0, A lam, A *U, A *V1,
+                                                        A *V2)
+    {
+        constexpr int ST = D == 3 ? QQ : Q;
+        constexpr int NG = D == 3 ? 7 : 4;
+        const TP DL = tab + (D == 3 ? L.D3 : L.D2);
+        int rot = 0;
+        for_items<EPB, NT>(PER, rot, [&](int e, int s, int z) {
+            const long long eg = e0 + e;
+            A vl[Q], m[Q], d3[Q];
+            if constexpr (D == 3) {  // du/d eta3 along this pencil, from u
+                A u[Q];
+#pragma unroll
+                for (int k = 0; k < Q; ++k) u[k] = U[e * S + s + ST * k];
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    A acc = A(0);
+#pragma unroll
+                    for (int r = 0; r < Q; ++r) acc = fmaa(DL(z, k * Q + r), u[r], acc);
+                    d3[k] = acc;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const int n = s + ST * k;
+                A d0 = V1[e * S + n], d1 = V2[e * S + n], d2 = A(0);
+                if constexpr (D == 3) d2 = d3[k];
+                if constexpr (!PP) {
+                    const A sc = geo.wq[n];
+                    d0 *= sc;
+                    d1 *= sc;
+                    d2 *= sc;
+                }
+                if constexpr (D == 3) {
+                    const A g00 = geo.get(eg, n, 0), g01 = geo.get(eg, n, 1), g02 = geo.get(eg, n, 2);
+                    const A g11 = geo.get(eg, n, 3), g12 = geo.get(eg, n, 4), g22 = geo.get(eg, n, 5);
+                    V1[e * S + n] = fmaa(g00, d0, fmaa(g01, d1, g02 * d2));
+                    V2[e * S + n] = fmaa(g01, d0, fmaa(g11, d1, g12 * d2));
+                    vl[k] = fmaa(g02, d0, fmaa(g12, d1, g22 * d2));
+                } else {
+                    const A g00 = geo.get(eg, n, 0), g01 = geo.get(eg, n, 1), g11 = geo.get(eg, n, 2);
+                    V1[e * S + n] = fmaa(g00, d0, g01 * d1);
+                    vl[k] = fmaa(g01, d0, g11 * d1);
+                }
+                m[k] = lam * geo.get(eg, n, NG - 1) * U[e * S + n];
+            }
+#pragma unroll
+            for (int o = 0; o < Q; ++o) {
+                A acc = m[o];
+#pragma unroll
+                for (int r = 0; r < Q; ++r) acc = fmaa(DL(z, r * Q + o), vl[r], acc);
+                U[e * S + s + ST * o] = acc;
+            }
+        });
+        __syncthreads();
+    }
+
+    template <class TP>
+    static __device__ __forceinline__ void tmid(TP tab, A *U, const A *V2)
+    {
+        const TP D2 = tab + L.D2;
+        int rot = 0;
+        for_items<EPB, NT>(QQ, rot, [&](int e, int s, int z) {  // along j: s = i + Q k
+            const int k = s / Q, i = s - k * Q;
+            const A *b = V2 + e * S + i + QQ * k;
+            A x[Q];
+#pragma unroll
+            for (int r = 0; r < Q; ++r) x[r] = b[r * Q];
+#pragma unroll
+            for (int o = 0; o < Q; ++o) {
+                A *y = U + e * S + i + Q * o + QQ * k;
+                A acc = *y;
+#pragma unroll
+                for (int r = 0; r < Q; ++r) acc = fmaa(D2(z, r * Q + o), x[r], acc);
+                *y = acc;
+            }
+        });
+        __syncthreads();
+    }
+
+    template <class TP>
+    static __device__ __forceinline__ void t1_first(TP tab, const A *U, const A *V1, A *out)
+    {
+        const TP Ba = tab + L.Ba, D1 = tab + L.D1;
+        int rot = 0;
+        for_items<EPB, NT>(PER, rot, [&](int e, int s, int z) {
+            const A *bv = V1 + e * S + Q * s;
+            const A *bu = U + e * S + Q * s;
+            A v[Q], y[Q];
+#pragma unroll
+            for (int r = 0; r < Q; ++r) v[r] = bv[r];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                A acc = bu[i];
+#pragma unroll
+                for (int r = 0; r < Q; ++r) acc = fmaa(D1(z, r * Q + i), v[r], acc);
+                y[i] = acc;
+            }
+#pragma unroll
+            for (int p = 0; p < N; ++p) {
+                A acc = A(0);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) acc = fmaa(Ba(z, i * N + p), y[i], acc);
+                if constexpr (D == 3) {
+                    const int k = s / Q, j = s - k * Q;
+                    out[e * S + p * QQ + j * Q + k] = acc;
+                } else {
+                    out[e * S + p * Q + s] = acc;
+                }
+            }
+        });
+        __syncthreads();
+    }
+};
+
+// Point-wise Helmholtz metric stage (FP64 path): v_i = sum_j G_ij du_j at
+// every point of the group, du by collocation gathers.
 // PP: factors stored per point (true) or per element times the reference
 // weight (false), resolved at compile time so no scale is applied per point.
 template <bool PP, int D, int Q, int NQ, int NG, int EPB, int NT, class T, class A>
@@ -541,9 +844,12 @@ __device__ __forceinline__ void helm_metric(const Geo<T, A, NQ, NG> &geo, long l
 
 // One group of ne (<= EPB) elements starting at e0: the whole operator.
 // tab: the block's tables in shared memory; buf: NBUF * EPB * S values.
-template <int SH, int N, int Q, class T, int OP, int EPB_>
-__device__ __forceinline__ void run_group(const KArgs &a, const typename CT<T>::type *tab,
-                                          typename CT<T>::type *buf, long long e0, int ne)
+// TP: table accessor for the contractions (STab or PTab); tab: the same
+// tables in shared memory (collocation gathers of PhysDeriv and
+// IProductWRTDerivBase, reference weights).
+template <int SH, int N, int Q, class T, int OP, int EPB_, class TP>
+__device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename CT<T>::type *tab,
+                                          typename CT<T>::type *buf, long long e0, int ne, bool staged = false)
 {
     using C = Config<SH, N, Q, T, OP, EPB_>;
     using A = typename C::A;
@@ -551,6 +857,7 @@ __device__ __forceinline__ void run_group(const KArgs &a, const typename CT<T>::
     constexpr TabLayout L = layout(SH, N, Q);
     constexpr int NG = (OP == OP_PHYSDERIV || OP == OP_IPROD_DERIV) ? nlam(SH) : ngeo(SH);
     using MD = Modal<SH, N, Q, A, EPB, NT, S>;
+    using HS = HelmStages<SH, N, Q, A, EPB, NT, S>;
     A *B0 = buf, *B1 = buf + EPB * S, *B2 = buf + 2 * EPB * S, *B3 = buf + 3 * EPB * S;
     const A *D0 = tab + L.D1, *D1 = tab + L.D2, *D2 = tab + L.D3;
     const Geo<T, A, NQ, NG> geo{reinterpret_cast<const T *>(a.geo), tab + L.wq, a.geo_pp};
@@ -559,10 +866,10 @@ __device__ __forceinline__ void run_group(const KArgs &a, const typename CT<T>::
         gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
         __syncthreads();
         if constexpr (D == 2) {
-            MD::bwd(tab, B0, B1, B0, nullptr);
+            MD::bwd(tp, B0, B1, B0, nullptr);
             gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B0);
         } else {
-            MD::bwd(tab, B0, B1, B0, B1);
+            MD::bwd(tp, B0, B1, B0, B1);
             gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
         }
     } else if constexpr (OP == OP_IPROD || OP == OP_MASS) {
@@ -573,8 +880,8 @@ __device__ __forceinline__ void run_group(const KArgs &a, const typename CT<T>::
         } else {
             gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
             __syncthreads();
-            if constexpr (D == 2) MD::bwd(tab, B0, B1, B0, nullptr);
-            else { MD::bwd(tab, B0, B1, B0, B1); P = B1; }
+            if constexpr (D == 2) MD::bwd(tp, B0, B1, B0, nullptr);
+            else { MD::bwd(tp, B0, B1, B0, B1); P = B1; }
         }
         for (int w = threadIdx.x; w < EPB * NQ; w += NT) {
             const int e = w % EPB, n = w / EPB;
@@ -583,10 +890,10 @@ __device__ __forceinline__ void run_group(const KArgs &a, const typename CT<T>::
         __syncthreads();
         A *O = (P == B0) ? B1 : B0;
         if constexpr (D == 2) {
-            MD::iprod(tab, P, O, nullptr, P);
+            MD::iprod(tp, P, O, nullptr, P);
             gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, P);
         } else {
-            MD::iprod(tab, P, O, P, O);
+            MD::iprod(tp, P, O, P, O);
             gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, O);
         }
     } else if constexpr (OP == OP_PHYSDERIV) {
@@ -642,17 +949,19 @@ __device__ __forceinline__ void run_group(const KArgs &a, const typename CT<T>::
         }
         __syncthreads();
         if constexpr (D == 2) {
-            MD::iprod(tab, B0, B1, nullptr, B2);
+            MD::iprod(tp, B0, B1, nullptr, B2);
             gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B2);
         } else {
-            MD::iprod(tab, B0, B1, B2, B1);
+            MD::iprod(tp, B0, B1, B2, B1);
             gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
         }
-    } else {  // OP_HELM
+    } else if constexpr (sizeof(A) == 8) {  // OP_HELM, FP64: point-wise gradient flow
+        // (the FP64 pipe is the bound; fine-grained point work items keep it
+        // busy across barriers better than whole pencils)
         gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B1);
         __syncthreads();
-        if constexpr (D == 2) MD::bwd(tab, B1, B2, B0, nullptr);
-        else MD::bwd(tab, B1, B2, B1, B0);
+        if constexpr (D == 2) MD::bwd(tp, B1, B2, B0, nullptr);
+        else MD::bwd(tp, B1, B2, B1, B0);
         // v_i = sum_j G_ij du_j  (G includes W and the chain rule)
         if (a.geo_pp) helm_metric<true, D, Q, NQ, NG, EPB, NT>(geo, e0, D0, D1, D2, S, B0, B1, B2, B3);
         else helm_metric<false, D, Q, NQ, NG, EPB, NT>(geo, e0, D0, D1, D2, S, B0, B1, B2, B3);
@@ -667,19 +976,177 @@ __device__ __forceinline__ void run_group(const KArgs &a, const typename CT<T>::
         }
         __syncthreads();
         if constexpr (D == 2) {
-            MD::iprod(tab, B0, B1, nullptr, B2);
+            MD::iprod(tp, B0, B1, nullptr, B2);
             gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B2);
         } else {
-            MD::iprod(tab, B0, B1, B2, B1);
+            MD::iprod(tp, B0, B1, B2, B1);
             gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
         }
+    } else {  // OP_HELM, FP32 / BF16: fused register-blocked pencils
+        const A lam = A(a.lambda);
+        if (!staged) {  // otherwise the caller has already put the coefficients in B1
+            gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B1);
+            __syncthreads();
+        }
+        if constexpr (D == 2) {
+            // B1 modes -> B2 t1 -> U = B0, V1 = B1, V2 = B2
+            MD::front(tp, B1, B2, nullptr);
+            HS::last_grad1(tp, B2, B0, B1);
+            HS::grad_rest(tp, B0, B2);
+            if (a.geo_pp) HS::template metric_tlast<true>(tp, geo, e0, lam, B0, B1, B2);
+            else HS::template metric_tlast<false>(tp, geo, e0, lam, B0, B1, B2);
+            HS::t1_first(tp, B0, B1, B2);
+            MD::back(tp, B2, nullptr, B0);
+        } else {
+            // B1 modes -> B2 t1 -> B1 t2 -> U = B0, V1 = B2, V2 = B1
+            MD::front(tp, B1, B2, B1);
+            HS::last_grad1(tp, B1, B0, B2);
+            HS::grad_rest(tp, B0, B1);
+            if (a.geo_pp) HS::template metric_tlast<true>(tp, geo, e0, lam, B0, B2, B1);
+            else HS::template metric_tlast<false>(tp, geo, e0, lam, B0, B2, B1);
+            HS::tmid(tp, B0, B1);
+            HS::t1_first(tp, B0, B2, B1);
+            MD::back(tp, B1, B2, B0);
+        }
+        gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B0);
     }
     __syncthreads();
 }
 
-// Persistent single-block kernel: CTAs stride over the element groups.
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, non-tensor form) and mbarriers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Copy `bytes` (multiple of 16, both addresses 16-byte aligned) from global
+// to shared memory, completing on `bar`; the caller arrives with expect_tx.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bring `bytes` (multiple of 16, 16-byte aligned) of global memory into L2.
+__device__ __forceinline__ void l2_prefetch(const void *src, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// Wait for phase `parity` of `bar` for at most ~2^31 clock cycles (about a
+// second).  Returns false on timeout after setting the device error word.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *err)
+{
+    const long long t0 = clock64();
+    unsigned done = 0;
+    while (true) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (1LL << 31)) {
+            if (err) atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+
+// Single-block FP32/BF16 Helmholtz with the next group's coefficients staged
+// by a bulk copy while the current group computes (a group's inputs are
+// [EPB][M] contiguous values).  With a.pf = 1 the group's per-point metric
+// (for EPB a multiple of 32: whole 32-element chunks of the interleaved
+// layout) is bulk-prefetched into L2 when the group starts, so the metric
+// stage finds it there; the autotuner decides whether that pays.  Groups whose
+// copy would not be 16-byte aligned, and the ragged last group, are loaded
+// with plain coalesced loads.
+template <int SH, int N, int Q, class T, int EPB_ = 0>
+__global__ void __launch_bounds__(512)
+    k_helm_tma(KArgs a, const __grid_constant__ TabP<typename CT<T>::type, layout(SH, N, Q).total> tp)
+{
+    using C = Config<SH, N, Q, T, OP_HELM, EPB_>;
+    using A = typename C::A;
+    static_assert(C::FUSED, "FP32/BF16 Helmholtz only");
+    constexpr int EPB = C::EPB, NT = C::NT, M = C::M, S = C::S, NQ = C::NQ, NG = ngeo(SH);
+    constexpr int STG = ((EPB * M * (int)sizeof(T) + 15) / 16) * 16;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    A *tab = reinterpret_cast<A *>(smem_raw);
+    T *stage = reinterpret_cast<T *>(smem_raw + C::TABB);
+    A *buf = reinterpret_cast<A *>(smem_raw + C::TABB + STG);
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int s_next, s_fail;
+    for (int i = threadIdx.x; i < C::TABN; i += NT) tab[i] = tp.v[i];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        s_fail = 0;
+    }
+    __syncthreads();
+    const PTab<A, C::TABN> ptab{&tp, 0};
+    const long long ngroups = (a.nelem + EPB - 1) / EPB;
+    const T *in = reinterpret_cast<const T *>(a.in0);
+    const T *G = reinterpret_cast<const T *>(a.geo);
+    // issue the copy of group g (thread 0); returns whether it was issued
+    auto prefetch_metric = [&](long long e0) {  // EPB / 32 whole chunks of the metric
+        if (a.pf && a.geo_pp && (EPB % 32) == 0) {
+            const char *gp = reinterpret_cast<const char *>(G + (((e0 >> 5) * NQ * NG) << 5));
+            const long long gbytes = (long long)NQ * NG * EPB * (long long)sizeof(T);
+            for (long long off = 0; off < gbytes; off += 32768)
+                l2_prefetch(gp + off, (unsigned)((gbytes - off) < 32768 ? (gbytes - off) : 32768));
+        }
+    };
+    auto issue = [&](long long g) -> int {
+        if (g >= ngroups) return 0;
+        const long long e0 = g * EPB;
+        if (e0 + EPB > a.nelem) return 0;
+        const T *src = in + e0 * M;
+        const unsigned bytes = (unsigned)(EPB * M * sizeof(T));
+        if ((reinterpret_cast<unsigned long long>(src) & 15) || (bytes & 15)) return 0;
+        tma_load_1d(stage, src, bytes, &bar);
+        return 1;
+    };
+    unsigned phase = 0;
+    if (threadIdx.x == 0) s_next = issue(blockIdx.x);
+    __syncthreads();
+    for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const long long e0 = g * EPB;
+        const int ne = (int)((a.nelem - e0) < EPB ? (a.nelem - e0) : EPB);
+        const bool staged = s_next != 0;
+        if (threadIdx.x == 0) prefetch_metric(e0);
+        if (staged) {
+            if (!mbar_wait(&bar, phase, a.err)) s_fail = 1;
+            phase ^= 1u;
+            __syncthreads();
+            if (s_fail) return;  // every thread leaves together; the error word is set
+            A *B1 = buf + EPB * S;
+            for (int i = threadIdx.x; i < EPB * M; i += NT) {
+                const int e = i / M, m = i - e * M;
+                B1[e * S + m] = to_a(stage[i], A());
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_next = issue(g + gridDim.x);  // stage is free again
+        run_group<SH, N, Q, T, OP_HELM, EPB_>(a, ptab, tab, buf, e0, ne, staged);
+    }
+}
+
+// Persistent single-block kernel: CTAs stride over the element groups.  The
+// tables arrive twice: as a __grid_constant__ parameter (constant bank, used
+// by the contractions) and copied once into shared memory (gathers, weights).
 template <int SH, int N, int Q, class T, int OP, int EPB_ = 0>
-__global__ void __launch_bounds__(256) k_elem(KArgs a)
+__global__ void __launch_bounds__(256)
+    k_elem(KArgs a, const __grid_constant__ TabP<typename CT<T>::type, layout(SH, N, Q).total> tp)
 {
     using C = Config<SH, N, Q, T, OP, EPB_>;
     using A = typename C::A;
@@ -687,16 +1154,26 @@ __global__ void __launch_bounds__(256) k_elem(KArgs a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A *tab = reinterpret_cast<A *>(smem_raw);
     A *buf = reinterpret_cast<A *>(smem_raw + C::TABB);
-    {
-        const A *gt = reinterpret_cast<const A *>(a.tab);
-        for (int i = threadIdx.x; i < C::TABN; i += NT) tab[i] = gt[i];
-    }
+    for (int i = threadIdx.x; i < C::TABN; i += NT) tab[i] = tp.v[i];
     __syncthreads();
     const long long ngroups = (a.nelem + EPB - 1) / EPB;
-    for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
-        const long long e0 = g * EPB;
-        const int ne = (int)((a.nelem - e0) < EPB ? (a.nelem - e0) : EPB);
-        run_group<SH, N, Q, T, OP, EPB_>(a, tab, buf, e0, ne);
+    // FP32 contractions take table entries as constant-bank operands; DFMA
+    // would first load them into register pairs (and the compiler hoists
+    // them), so FP64 reads its tables from shared memory instead.
+    if constexpr (sizeof(A) == 4) {
+        const PTab<A, C::TABN> ptab{&tp, 0};
+        for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
+            const long long e0 = g * EPB;
+            const int ne = (int)((a.nelem - e0) < EPB ? (a.nelem - e0) : EPB);
+            run_group<SH, N, Q, T, OP, EPB_>(a, ptab, tab, buf, e0, ne);
+        }
+    } else {
+        const STab<A> stab{tab};
+        for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
+            const long long e0 = g * EPB;
+            const int ne = (int)((a.nelem - e0) < EPB ? (a.nelem - e0) : EPB);
+            run_group<SH, N, Q, T, OP, EPB_>(a, stab, tab, buf, e0, ne);
+        }
     }
 }
 

@@ -54,7 +54,7 @@ __device__ __noinline__ void run_item(const MeshBlk &mb, const MeshItem &m, unsi
         const long long e0 = (long long)g * C::EPB;
         const long long left = mb.a.nelem - e0;
         const int ne = (int)(left < C::EPB ? left : C::EPB);
-        run_group<SH, N, N + 1, TT, OP_HELM, 0>(mb.a, tab, buf, e0, ne);
+        run_group<SH, N, N + 1, TT, OP_HELM, 0>(mb.a, STab<A>{tab}, tab, buf, e0, ne);
     }
 }
 
@@ -71,7 +71,9 @@ __device__ __forceinline__ void dispatch_one(int vid, const MeshBlk &mb, const M
     }
 }
 
-__global__ void __launch_bounds__(256) k_mesh(const MeshBlk *__restrict__ blks, const MeshItem *__restrict__ items,
+constexpr int kMeshNT = Config<HEX, 5, 6, TT, OP_HELM, 0>::NT;  // the same for every variant
+
+__global__ void __launch_bounds__(kMeshNT) k_mesh(const MeshBlk *__restrict__ blks, const MeshItem *__restrict__ items,
                                               int nitems, int *counter)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -127,6 +129,6 @@ MeshKInfo NIR_MCAT(NIR_MESH_DIM, NIR_PREC)(int shape, int P)
     k.fn = reinterpret_cast<const void *>(&k_mesh);
     k.smem = smem_of<0>(k.vid);
     k.epb = epb_of<0>(k.vid);
-    k.nt = 256;
+    k.nt = kMeshNT;
     return k;
 }

@@ -58,6 +58,7 @@ int nir_mesh_build_items(nir_mesh *m, int prec, int gran)
         MeshKInfo k = nir_mesh_kinfo(m->dim, prec, b->d.shape, b->d.P);
         if (!k.fn) return NIR_ERR_UNSUPPORTED;
         ps.fn = k.fn;
+        ps.nt = k.nt;
         ps.smem = std::max(ps.smem, k.smem);
         ps.vid[bi] = k.vid;
         const long long ngroups = (b->d.nelem + k.epb - 1) / k.epb;
@@ -86,7 +87,7 @@ int nir_mesh_build_items(nir_mesh *m, int prec, int gran)
     if (ps.smem > 48 * 1024)
         NIR_CUDA_TRY(cudaFuncSetAttribute(ps.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ps.smem));
     int occ = 0;
-    NIR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ps.fn, 256, ps.smem));
+    NIR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ps.fn, ps.nt, ps.smem));
     ps.occ = std::max(1, occ);
     if (ps.grid <= 0 || ps.grid > ps.occ * m->ctx->num_sms) ps.grid = ps.occ * m->ctx->num_sms;
     ps.ready = true;
@@ -108,7 +109,7 @@ int nir_mesh_launch_raw(nir_mesh *m, int prec, const nirk::MeshBlk *dblk, cudaSt
     int nitems = ps.nitems;
     const nirk::MeshItem *items = ps.ditems;
     void *args[] = {(void *)&dblk, (void *)&items, (void *)&nitems, (void *)&ctr};
-    if (cudaLaunchKernel(ps.fn, dim3(ps.grid), dim3(256), args, (size_t)ps.smem, st) != cudaSuccess) {
+    if (cudaLaunchKernel(ps.fn, dim3(ps.grid), dim3(ps.nt), args, (size_t)ps.smem, st) != cudaSuccess) {
         (void)cudaGetLastError();  // consume the launch error so it does not surface in a later call
         return NIR_ERR_CUDA;
     }
@@ -152,6 +153,7 @@ int nir_mesh_block_table(nir_mesh *m, int prec, double lambda, const void *in, v
         a.nelem = b->d.nelem;
         a.lambda = lambda;
         a.geo_pp = b->geo_pp;
+        a.err = m->ctx->derr;
         h[bi].vid = m->ps[prec].vid[bi];
     }
     nirk::MeshBlk *d = nullptr;
@@ -381,7 +383,7 @@ extern "C" int nir_tune(nir_mesh *m, const char *cache_path)
     }
     cudaMemsetAsync(x, 0, std::max(maxb, (size_t)m->ndof) * 8, st);
     int rc = NIR_OK;
-    for (int prec = 0; prec < 2 && !rc; ++prec) {
+    for (int prec = 0; prec < 3 && !rc; ++prec) {
         // per-block elements-per-CTA variant and grid size
         for (auto *b : m->blocks) {
             char key[160];
@@ -389,28 +391,35 @@ extern "C" int nir_tune(nir_mesh *m, const char *cache_path)
                           pname[prec]);
             auto it = kv.find(key);
             if (it != kv.end()) {
-                std::sscanf(it->second.c_str(), "%d,%d", &b->helm_variant[prec], &b->helm_grid[prec]);
+                b->helm_pf[prec] = 0;
+                std::sscanf(it->second.c_str(), "%d,%d,%d", &b->helm_variant[prec], &b->helm_grid[prec],
+                            &b->helm_pf[prec]);
                 continue;
             }
             float best = 1e30f;
-            int bv = 0, bg = 0;
+            int bv = 0, bg = 0, bp = 0;
             for (int v = 0; v < 3 && !rc; ++v) {
                 KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, 5, v);
                 if (!ki.fn || (v > 0 && ki.epb == nir_kinfo(b->d.shape, b->d.P, prec, 5, 0).epb)) continue;
                 int occ = nir_occupancy(ctx, ki);
-                for (int c = 1; c <= std::max(1, occ) && !rc; ++c) {
-                    b->helm_variant[prec] = v;
-                    b->helm_grid[prec] = c * ctx->num_sms;
-                    float t = time_ms(st, 5, [&] {
-                        if (!rc) rc = nir_launch_op(b, prec, 5, 1.0, x, nullptr, nullptr, y, nullptr, nullptr, st, 0);
-                    });
-                    if (t < best) { best = t; bv = v; bg = c * ctx->num_sms; }
-                }
+                const int npf = (prec != NIR_F64 && b->geo_pp && ki.epb % 32 == 0) ? 2 : 1;
+                for (int c = 1; c <= std::max(1, occ) && !rc; ++c)
+                    for (int pf = 0; pf < npf && !rc; ++pf) {
+                        b->helm_variant[prec] = v;
+                        b->helm_grid[prec] = c * ctx->num_sms;
+                        b->helm_pf[prec] = pf;
+                        float t = time_ms(st, 5, [&] {
+                            if (!rc)
+                                rc = nir_launch_op(b, prec, 5, 1.0, x, nullptr, nullptr, y, nullptr, nullptr, st, 0);
+                        });
+                        if (t < best) { best = t; bv = v; bg = c * ctx->num_sms; bp = pf; }
+                    }
             }
             b->helm_variant[prec] = bv;
             b->helm_grid[prec] = bg;
+            b->helm_pf[prec] = bp;
             char val[64];
-            std::snprintf(val, sizeof val, "%d,%d", bv, bg);
+            std::snprintf(val, sizeof val, "%d,%d,%d", bv, bg, bp);
             kv[key] = val;
         }
         if (rc) break;

@@ -13,6 +13,7 @@ struct MeshPrec {
     const void *fn = nullptr;        // persistent kernel of this precision
     int smem = 0;                    // dynamic shared memory (max over the mesh's variants)
     int occ = 1;                     // CTAs per SM at that shared memory
+    int nt = 256;                    // threads per CTA of the persistent kernel
     int grid = 0;                    // CTAs launched (tuned; 0: occ * SMs)
     int gran = 1;                    // element groups per work item (tuned)
     std::vector<int> vid;            // variant id per block
