@@ -49,6 +49,34 @@ def helm_bytes_per_elem(shape: str, N: int, Q: int, wb: int, deformed: bool) -> 
     return 2 * M * wb + geo * wb
 
 
+KERNEL_SOURCES = ("paper_2606_20917_gb300/csrc/nir_kernels.cuh", "paper_2606_20917_gb300/csrc/nir_inst.cu",
+                  "paper_2606_20917_gb300/csrc/nir_layout.h")
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch from the committed ncu summary profiles/<name>.md,
+    or None when the kernel sources changed since that capture."""
+    import re
+    path = os.path.join(ROOT, "profiles", name + ".md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", txt)
+    h = re.search(r"kernel_sources_sha256:\s*([0-9a-f]{64})", txt)
+    if not t or not h or h.group(1) != kernel_sources_sha256():
+        return None
+    return int(t.group(1))
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -213,8 +241,9 @@ def run_nir(args, ws, rank, local):
     blk.set_geometry(g, torch.from_numpy(wl["nodes"]).to(dev))
     if not args.no_tune:
         # set-up, untimed: the library's autotuner picks elements per CTA, grid
-        # size and metric-prefetch policy for this block on this GPU
-        nir.Mesh(ctx, [blk]).tune(None)
+        # size and metric-prefetch policy for this block on this GPU (a cache
+        # file, when given, is read back instead of re-timing)
+        nir.Mesh(ctx, [blk]).tune(args.tune_cache)
     M = blk.M
     dt_t = nir.DTYPE[args.prec]
     u = torch.from_numpy(W.coefficients(E, M, seed=0)).to(dev, dt_t)
@@ -269,7 +298,8 @@ def run_nir(args, ws, rank, local):
         if args.prec == "f64":
             fp64 = ctx.probe_fp64_peak()
             roof = {"bound": "alu", "achieved": flops / avg_launch_s / 1e12, "peak": fp64, "unit": "TFLOP/s",
-                    "frac": flops / avg_launch_s / 1e12 / fp64, "traffic": None,
+                    "frac": flops / avg_launch_s / 1e12 / fp64,
+                    "traffic": profiled_traffic(f"helm_{args.workload}_{args.prec}"),
                     "peak_source": "FP64 FMA throughput measured in this run by nir_probe_fp64_peak "
                                    "(register-resident DFMA chains); nominal GB300 FP64 is 1.25 TFLOP/s",
                     "flops_per_elem": flops // E,
@@ -278,7 +308,8 @@ def run_nir(args, ws, rank, local):
             gbs = work_bytes / avg_launch_s / 1e9
             peak = peaks.get("hbm_gbs", 6800.0)
             roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                    "traffic": None, "bytes_per_elem": work_bytes // E,
+                    "traffic": profiled_traffic(f"helm_{args.workload}_{args.prec}"),
+                    "bytes_per_elem": work_bytes // E,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "_fallback" not in peaks else "fallback 6.8 TB/s"}
     extras = {}
     if args.extras and ws == 1:
@@ -325,6 +356,8 @@ def run_solve(args, ws, rank, local):
     blk = nir.Block(ctx, wl["shape"], E, wl["P"], deformed=wl["deformed"])
     blk.set_geometry(wl["gorder"], torch.from_numpy(wl["nodes"]).to(dev))
     mesh = nir.Mesh(ctx, [blk])
+    if not args.no_tune:
+        mesh.tune(args.tune_cache)  # set-up, untimed
     # right-hand side b = B^T W f for f = (3 pi^2 + lambda) sin(pi x) sin(pi y) sin(pi z)
     eta, xi = blk.points()
     lam = 1.0
@@ -404,9 +437,8 @@ def run_hybrid(args, ws, rank, local):
         b.set_geometry(p["gorder"], torch.from_numpy(p["nodes"]).to(dev))
         blocks.append(b)
     mesh = nir.Mesh(ctx, blocks)
-    if args.tune:
-        mesh.tune(os.path.join(ROOT, "gpurun_out", "tune_cache.json") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else None)
+    if not args.no_tune:
+        mesh.tune(args.tune_cache)  # set-up, untimed
     res = {}
     nel = sum(b.nelem for b in blocks)
     for prec in ("f64", "f32"):
@@ -432,7 +464,7 @@ def run_hybrid(args, ws, rank, local):
             "ms_per_step": res["f64"]["ms_per_apply"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "hybrid mesh: 50000 curved hex + 25000 prism + 75000 tet, P ~ U{2..8}, Q = P+2",
-                       "nelem": nel, "ndof": mesh.ndof, "blocks": len(blocks), "tuned": bool(args.tune)},
+                       "nelem": nel, "ndof": mesh.ndof, "blocks": len(blocks), "tuned": not args.no_tune},
             "precisions": res, "gpu_launches": args.steps}
     print(json.dumps(line), flush=True)
 
@@ -453,8 +485,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--inner-tol", type=float, default=1e-3)
     ap.add_argument("--max-inner", type=int, default=20000)
-    ap.add_argument("--tune", action="store_true", help="hybrid mode: autotune the mesh first")
-    ap.add_argument("--no-tune", action="store_true", help="apply mode: skip the autotuner set-up")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner set-up")
+    ap.add_argument("--tune-cache", default=None, help="autotuner cache file (read if present, else written)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
