@@ -96,9 +96,14 @@ const void *nir_geo_ptr(nir_block *b, int prec, bool lam)
 
 const void *nir_tab_ptr(nir_block *b, int prec) { return prec == NIR_F64 ? (const void *)b->tab64 : (const void *)b->tab32; }
 
-int nir_launch_op(nir_block *b, int prec, int op, double lambda, const void *in0, const void *in1, const void *in2,
-                  void *out0, void *out1, void *out2, cudaStream_t stream, int grid_override)
+// Launch one operator over elements [e_begin, e_begin + e_count) of a block.
+// Pointers are the block's full arrays; e_begin must be a multiple of 64 so
+// the 32-element interleaved factors stay aligned.
+int nir_launch_op_range(nir_block *b, int prec, int op, double lambda, const void *in0, const void *in1,
+                        const void *in2, void *out0, void *out1, void *out2, long long e_begin, long long e_count,
+                        cudaStream_t stream, int grid_override)
 {
+    if (e_begin < 0 || e_count < 1 || e_begin + e_count > b->d.nelem || (e_begin & 63)) return NIR_ERR_INVALID_ARG;
     int variant = (op == nirk::OP_HELM && prec >= 0 && prec < 3) ? b->helm_variant[prec] : 0;
     KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, op, variant);
     if (!ki.fn) ki = nir_kinfo(b->d.shape, b->d.P, prec, op, 0);
@@ -107,18 +112,34 @@ int nir_launch_op(nir_block *b, int prec, int op, double lambda, const void *in0
     if (rc) return rc;
     int occ = nir_occupancy(b->ctx, ki);
     if (occ < 0) return NIR_ERR_CUDA;
-    const long long groups = (b->d.nelem + ki.epb - 1) / ki.epb;
+    const long long groups = (e_count + ki.epb - 1) / ki.epb;
     long long grid = (long long)occ * b->ctx->num_sms;
     if (grid_override <= 0 && op == nirk::OP_HELM && prec >= 0 && prec < 3) grid_override = b->helm_grid[prec];
     if (grid_override > 0) grid = grid_override;
     if (grid > groups) grid = groups;
-    nirk::KArgs a;
-    a.in0 = in0; a.in1 = in1; a.in2 = in2;
-    a.out0 = out0; a.out1 = out1; a.out2 = out2;
     const bool lam = (op == nirk::OP_PHYSDERIV || op == nirk::OP_IPROD_DERIV);
-    a.geo = nir_geo_ptr(b, prec, lam);
+    const bool modal_in = (op == nirk::OP_BWD || op == nirk::OP_MASS || op == nirk::OP_HELM);
+    const bool modal_out = (op == nirk::OP_IPROD || op == nirk::OP_IPROD_DERIV || op == nirk::OP_MASS ||
+                            op == nirk::OP_HELM);
+    const size_t es = nir_prec_size(prec);
+    const size_t in_stride = (size_t)(modal_in ? b->M : b->NQ) * es;
+    const size_t out_stride = (size_t)(modal_out ? b->M : b->NQ) * es;
+    auto shift = [&](const void *p, size_t stride) -> const void * {
+        return p ? (const void *)((const char *)p + (size_t)e_begin * stride) : nullptr;
+    };
+    nirk::KArgs a;
+    a.in0 = shift(in0, in_stride);
+    a.in1 = shift(in1, in_stride);
+    a.in2 = shift(in2, in_stride);
+    a.out0 = const_cast<void *>(shift(out0, out_stride));
+    a.out1 = const_cast<void *>(shift(out1, out_stride));
+    a.out2 = const_cast<void *>(shift(out2, out_stride));
+    const int nf = lam ? b->nl : b->ng;
+    const size_t geo_off = b->geo_pp ? (size_t)e_begin * b->NQ * nf : (size_t)e_begin * nf;
+    const void *g = nir_geo_ptr(b, prec, lam);
+    a.geo = g ? (const void *)((const char *)g + geo_off * es) : nullptr;
     a.tab = nir_tab_ptr(b, prec);
-    a.nelem = b->d.nelem;
+    a.nelem = e_count;
     a.lambda = lambda;
     a.geo_pp = b->geo_pp;
     a.pf = (op == nirk::OP_HELM && prec >= 0 && prec < 3) ? b->helm_pf[prec] : 0;
@@ -133,6 +154,13 @@ int nir_launch_op(nir_block *b, int prec, int op, double lambda, const void *in0
         return NIR_ERR_CUDA;
     }
     return NIR_OK;
+}
+
+int nir_launch_op(nir_block *b, int prec, int op, double lambda, const void *in0, const void *in1, const void *in2,
+                  void *out0, void *out1, void *out2, cudaStream_t stream, int grid_override)
+{
+    return nir_launch_op_range(b, prec, op, lambda, in0, in1, in2, out0, out1, out2, 0, b->d.nelem, stream,
+                               grid_override);
 }
 
 // --------------------------------------------------------------------------- context
@@ -236,6 +264,14 @@ extern "C" void nir_block_destroy(nir_block *b)
     if (b->L16) cudaFree(b->L16);
     if (b->stage_in) cudaFree(b->stage_in);
     if (b->stage_out) cudaFree(b->stage_out);
+    if (b->copy_in) {
+        cudaStreamDestroy(b->copy_in);
+        cudaStreamDestroy(b->copy_out);
+        for (int k = 0; k < NIR_HOST_CHUNKS; ++k) {
+            cudaEventDestroy(b->ev_in[k]);
+            cudaEventDestroy(b->ev_done[k]);
+        }
+    }
     delete b;
 }
 
@@ -440,12 +476,17 @@ extern "C" int nir_helmholtz(nir_block *b, int prec, double lambda, const void *
                          b->ctx->stream, 0);
 }
 
+// Host-buffer Helmholtz: the elements are split into chunks (multiples of 64
+// elements); chunk k's copy to the device, its apply and its copy back run on
+// three streams ordered by events, so the copies of one chunk overlap the
+// apply of its neighbours.
 extern "C" int nir_helmholtz_host(nir_block *b, int prec, double lambda, const void *h_in, void *h_out)
 {
     int rc = check_block(b, prec);
     if (rc) return rc;
     if (!h_in || !h_out || h_in == h_out || !std::isfinite(lambda)) return NIR_ERR_INVALID_ARG;
-    const size_t bytes = (size_t)b->d.nelem * b->M * nir_prec_size(prec);
+    const size_t es = nir_prec_size(prec);
+    const size_t bytes = (size_t)b->d.nelem * b->M * es;
     if (b->stage_bytes < bytes) {
         if (b->stage_in) cudaFree(b->stage_in);
         if (b->stage_out) cudaFree(b->stage_out);
@@ -455,12 +496,36 @@ extern "C" int nir_helmholtz_host(nir_block *b, int prec, double lambda, const v
             return NIR_ERR_NO_MEMORY;
         b->stage_bytes = bytes;
     }
+    if (!b->copy_in) {
+        NIR_CUDA_TRY(cudaStreamCreateWithFlags(&b->copy_in, cudaStreamNonBlocking));
+        NIR_CUDA_TRY(cudaStreamCreateWithFlags(&b->copy_out, cudaStreamNonBlocking));
+        for (int k = 0; k < NIR_HOST_CHUNKS; ++k) {
+            NIR_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_in[k], cudaEventDisableTiming));
+            NIR_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_done[k], cudaEventDisableTiming));
+        }
+    }
     cudaStream_t st = b->ctx->stream;
-    NIR_CUDA_TRY(cudaMemcpyAsync(b->stage_in, h_in, bytes, cudaMemcpyHostToDevice, st));
-    rc = nir_launch_op(b, prec, nirk::OP_HELM, lambda, b->stage_in, nullptr, nullptr, b->stage_out, nullptr,
-                       nullptr, st, 0);
-    if (rc) return rc;
-    NIR_CUDA_TRY(cudaMemcpyAsync(h_out, b->stage_out, bytes, cudaMemcpyDeviceToHost, st));
+    const long long E = b->d.nelem;
+    long long chunk = ((E + NIR_HOST_CHUNKS - 1) / NIR_HOST_CHUNKS + 63) / 64 * 64;
+    if (chunk < 256) chunk = E;  // small blocks: one chunk
+    const size_t row = (size_t)b->M * es;
+    int k = 0;
+    for (long long e0 = 0; e0 < E; e0 += chunk, ++k) {
+        const long long n = (E - e0) < chunk ? (E - e0) : chunk;
+        const size_t off = (size_t)e0 * row, nb = (size_t)n * row;
+        NIR_CUDA_TRY(cudaMemcpyAsync((char *)b->stage_in + off, (const char *)h_in + off, nb,
+                                     cudaMemcpyHostToDevice, b->copy_in));
+        NIR_CUDA_TRY(cudaEventRecord(b->ev_in[k], b->copy_in));
+        NIR_CUDA_TRY(cudaStreamWaitEvent(st, b->ev_in[k], 0));
+        rc = nir_launch_op_range(b, prec, nirk::OP_HELM, lambda, b->stage_in, nullptr, nullptr, b->stage_out,
+                                 nullptr, nullptr, e0, n, st, 0);
+        if (rc) return rc;
+        NIR_CUDA_TRY(cudaEventRecord(b->ev_done[k], st));
+        NIR_CUDA_TRY(cudaStreamWaitEvent(b->copy_out, b->ev_done[k], 0));
+        NIR_CUDA_TRY(cudaMemcpyAsync((char *)h_out + off, (const char *)b->stage_out + off, nb,
+                                     cudaMemcpyDeviceToHost, b->copy_out));
+    }
+    NIR_CUDA_TRY(cudaStreamSynchronize(b->copy_out));
     NIR_CUDA_TRY(cudaStreamSynchronize(st));
     return NIR_OK;
 }

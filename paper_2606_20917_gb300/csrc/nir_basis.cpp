@@ -275,6 +275,18 @@ bool nirb_build_tables(int shape, int P, int Q, double *blob)
     nirb_colloc(Q, z1, blob + L.D1);
     if (shape == TRI || shape == TET) nirb_colloc(Q, z2, blob + L.D2);
     if (shape == TET || shape == PRISM) nirb_colloc(Q, z3, blob + L.D3);
+    // even/odd form of Ba (the first-direction points are symmetric for every shape)
+    {
+        const int ne = sym_ne(N), no = sym_no(N), w = ne + no;
+        for (int i = 0; i < (Q + 1) / 2; ++i) {
+            const double *B = blob + L.Ba + i * N;
+            double *R = blob + L.Bs + i * w;
+            R[0] = 0.5 * (B[0] + B[1]);
+            for (int k = 1; k < ne; ++k) R[k] = B[2 * k];
+            R[ne] = 0.5 * (B[0] - B[1]);
+            for (int k = 1; k < no; ++k) R[ne + k] = B[2 * k + 1];
+        }
+    }
     const int d = dim(shape);
     for (int n = 0; n < npts(shape, Q); ++n) {
         int i = n % Q, j = (n / Q) % Q, k = n / (Q * Q);

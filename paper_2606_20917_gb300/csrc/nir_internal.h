@@ -15,6 +15,9 @@ namespace nirk {
 struct KArgs;
 }
 
+// Chunks of the pipelined host-buffer Helmholtz.
+#define NIR_HOST_CHUNKS 8
+
 // Kernel registry entry of one (shape, P, precision, operator) instantiation.
 struct KInfo {
     const void *fn = nullptr;  // __global__ function
@@ -57,10 +60,15 @@ struct nir_block {
     void *G16 = nullptr, *L16 = nullptr;      // bfloat16 copies
     void *stage_in = nullptr, *stage_out = nullptr;
     size_t stage_bytes = 0;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;   // host-buffer pipeline streams
+    cudaEvent_t ev_in[NIR_HOST_CHUNKS] = {}, ev_done[NIR_HOST_CHUNKS] = {};
 };
 
 int nir_launch_op(nir_block *blk, int prec, int op, double lambda, const void *in0, const void *in1,
                   const void *in2, void *out0, void *out1, void *out2, cudaStream_t stream, int grid_override);
+int nir_launch_op_range(nir_block *b, int prec, int op, double lambda, const void *in0, const void *in1,
+                        const void *in2, void *out0, void *out1, void *out2, long long e_begin, long long e_count,
+                        cudaStream_t stream, int grid_override);
 const void *nir_geo_ptr(nir_block *blk, int prec, bool lam);
 const void *nir_tab_ptr(nir_block *blk, int prec);
 int nir_occupancy(nir_ctx *ctx, const KInfo &ki);

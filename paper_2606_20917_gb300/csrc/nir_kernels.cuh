@@ -178,6 +178,87 @@ struct PTab {
     __device__ __forceinline__ A operator()(int, int i) const { return t->v[base + i]; }
 };
 
+// Even/odd (symmetric) forms of the psiA contractions.  The first-direction
+// points are symmetric (z_{Q-1-i} = -z_i: GLL, or Gauss-Legendre for the
+// collapsed shapes' eta1) and psiA_0(-z) = psiA_1(z), psiA_p(-z) = (-1)^p psiA_p(z),
+// so with s = x0 + x1, d = x0 - x1:
+//   u_i = E_i + O_i, u_{Q-1-i} = E_i - O_i, E_i = Bs_e(i) . (s, x2, x4, ...),
+//   O_i = Bs_o(i) . (d, x3, x5, ...),
+// and the transpose pairs f_i +- f_{Q-1-i} the same way.  At P = 4 a pencil
+// costs 23 instead of 30 multiply-add slots, at P = 6 38 instead of 56.
+template <class A, int N, int Q, int EPB, int NT, class TP, class LD, class ST>
+__device__ __forceinline__ void sym_bwd(int per_e, int &rot, TP Bs, LD ld, ST st)
+{
+    constexpr int QL = Q / 2, NE = sym_ne(N), NO = sym_no(N), W = NE + NO;
+    for_items<EPB, NT>(per_e, rot, [&](int e, int s, int z) {
+        A x[N];
+        ld(e, s, x);
+        A xe[NE], xo[NO];
+        xe[0] = x[0] + x[1];
+        xo[0] = x[0] - x[1];
+#pragma unroll
+        for (int k = 1; k < NE; ++k) xe[k] = x[2 * k];
+#pragma unroll
+        for (int k = 1; k < NO; ++k) xo[k] = x[2 * k + 1];
+#pragma unroll
+        for (int i = 0; i < QL; ++i) {
+            A E = A(0), O = A(0);
+#pragma unroll
+            for (int k = 0; k < NE; ++k) E = fmaa(Bs(z, i * W + k), xe[k], E);
+#pragma unroll
+            for (int k = 0; k < NO; ++k) O = fmaa(Bs(z, i * W + NE + k), xo[k], O);
+            st(e, s, i, E + O);
+            st(e, s, Q - 1 - i, E - O);
+        }
+        if constexpr (Q % 2 == 1) {
+            A E = A(0);
+#pragma unroll
+            for (int k = 0; k < NE; ++k) E = fmaa(Bs(z, QL * W + k), xe[k], E);
+            st(e, s, QL, E);
+        }
+    });
+}
+
+template <class A, int N, int Q, int EPB, int NT, class TP, class LD, class ST>
+__device__ __forceinline__ void sym_iprod(int per_e, int &rot, TP Bs, LD ld, ST st)
+{
+    constexpr int QL = Q / 2, QH = (Q + 1) / 2, NE = sym_ne(N), NO = sym_no(N), W = NE + NO;
+    for_items<EPB, NT>(per_e, rot, [&](int e, int s, int z) {
+        A f[Q];
+        ld(e, s, f);
+        A fe[QH], fo[QL > 0 ? QL : 1];
+#pragma unroll
+        for (int i = 0; i < QL; ++i) {
+            fe[i] = f[i] + f[Q - 1 - i];
+            fo[i] = f[i] - f[Q - 1 - i];
+        }
+        if constexpr (Q % 2 == 1) fe[QL] = f[QL];
+        {
+            A Se = A(0), So = A(0);
+#pragma unroll
+            for (int i = 0; i < QH; ++i) Se = fmaa(Bs(z, i * W), fe[i], Se);
+#pragma unroll
+            for (int i = 0; i < QL; ++i) So = fmaa(Bs(z, i * W + NE), fo[i], So);
+            st(e, s, 0, Se + So);
+            st(e, s, 1, Se - So);
+        }
+#pragma unroll
+        for (int k = 1; k < NE; ++k) {
+            A acc = A(0);
+#pragma unroll
+            for (int i = 0; i < QH; ++i) acc = fmaa(Bs(z, i * W + k), fe[i], acc);
+            st(e, s, 2 * k, acc);
+        }
+#pragma unroll
+        for (int k = 1; k < NO; ++k) {
+            A acc = A(0);
+#pragma unroll
+            for (int i = 0; i < QL; ++i) acc = fmaa(Bs(z, i * W + NE + k), fo[i], acc);
+            st(e, s, 2 * k + 1, acc);
+        }
+    });
+}
+
 // ---------------------------------------------------------------------------
 // Modal <-> quadrature stages per shape.  Buffers: element e, index i at
 // buf[e*S + i].  bwd: p0 (modes) -> p1 -> p2 (-> p3) (points);
@@ -192,17 +273,15 @@ struct Modal {
     template <class TP>
     static __device__ __forceinline__ void front(TP tab, A *p0, A *p1, A *p2)
     {
-        const TP Ba = tab + L.Ba;
         int rot = 0;
-        auto tBa = [=](int z, int o, int r) { return Ba(z, o * N + r); };
         if constexpr (SH == QUAD || SH == TRI) {
             if constexpr (SH == QUAD) {
                 // t1[p][j] = sum_q u[p][q] psiA_q(z_j)
-                pencils0<A, N, Q, EPB, NT>(N, rot,
+                sym_bwd<A, N, Q, EPB, NT>(N, rot, tab + L.Bs,
                     [=](int e, int s, A *x) { const A *b = p0 + e * S + s * N;
 #pragma unroll
                         for (int r = 0; r < N; ++r) x[r] = b[r]; },
-                    tBa, [=](int e, int s, int o, A v) { p1[e * S + s * Q + o] = v; });
+                    [=](int e, int s, int o, A v) { p1[e * S + s * Q + o] = v; });
             } else {
                 // t1[p][j] = sum_{q<N-p} u[m(p,q)] psiB_pq(z_j) (+ the collapsed vertex (0,1) for p = 1)
                 sfor<0, N>([&](auto cc) {
@@ -224,11 +303,11 @@ struct Modal {
         } else {
             // ---- stage 1: contract the third mode index r -> k
             if constexpr (SH == HEX) {
-                pencils0<A, N, Q, EPB, NT>(N * N, rot,
+                sym_bwd<A, N, Q, EPB, NT>(N * N, rot, tab + L.Bs,
                     [=](int e, int s, A *x) { const A *b = p0 + e * S + s * N;
 #pragma unroll
                         for (int r = 0; r < N; ++r) x[r] = b[r]; },
-                    tBa, [=](int e, int s, int o, A v) { p1[e * S + s * Q + o] = v; });
+                    [=](int e, int s, int o, A v) { p1[e * S + s * Q + o] = v; });
             } else if constexpr (SH == PRISM) {
                 // t1[p][q][k] = sum_{r<N-p} u[m(p,q,r)] psiB_pr(z3_k) (+ collapsed edge (0,q,1) for p = 1)
                 sfor<0, N>([&](auto cc) {
@@ -266,12 +345,12 @@ struct Modal {
             __syncthreads();
             // ---- stage 2: contract q -> j
             if constexpr (SH == HEX || SH == PRISM) {
-                pencils0<A, N, Q, EPB, NT>(N * Q, rot,
+                sym_bwd<A, N, Q, EPB, NT>(N * Q, rot, tab + L.Bs,
                     [=](int e, int s, A *x) { const int p = s / Q, k = s - p * Q;
                         const A *b = p1 + e * S + p * N * Q + k;
 #pragma unroll
                         for (int r = 0; r < N; ++r) x[r] = b[r * Q]; },
-                    tBa, [=](int e, int s, int o, A v) { const int p = s / Q, k = s - p * Q;
+                    [=](int e, int s, int o, A v) { const int p = s / Q, k = s - p * Q;
                         p2[e * S + (p * Q + o) * Q + k] = v; });
             } else {  // TET: t2[p][j][k] = sum_{q<N-p} psiB_pq(z2_j) t1[pair(p,q)][k] (+ edge (0,1,.) for p = 1)
                 sfor<0, N>([&](auto cc) {
@@ -297,16 +376,14 @@ struct Modal {
     template <class TP>
     static __device__ __forceinline__ void back(TP tab, A *p1, A *p2, A *outm)
     {
-        const TP Ba = tab + L.Ba;
         int rot = 0;
-        auto tBaT = [=](int z, int o, int r) { return Ba(z, r * N + o); };
         if constexpr (SH == QUAD || SH == TRI) {
             if constexpr (SH == QUAD) {
-                pencils0<A, Q, N, EPB, NT>(N, rot,
+                sym_iprod<A, N, Q, EPB, NT>(N, rot, tab + L.Bs,
                     [=](int e, int s, A *x) { const A *b = p1 + e * S + s * Q;
 #pragma unroll
                         for (int r = 0; r < Q; ++r) x[r] = b[r]; },
-                    tBaT, [=](int e, int s, int o, A v) { outm[e * S + s * N + o] = v; });
+                    [=](int e, int s, int o, A v) { outm[e * S + s * N + o] = v; });
             } else {
                 sfor<0, N>([&](auto cc) {
                     constexpr int p = decltype(cc)::value;
@@ -330,12 +407,12 @@ struct Modal {
         } else {
             // ---- transpose of stage 2
             if constexpr (SH == HEX || SH == PRISM) {
-                pencils0<A, Q, N, EPB, NT>(N * Q, rot,
+                sym_iprod<A, N, Q, EPB, NT>(N * Q, rot, tab + L.Bs,
                     [=](int e, int s, A *x) { const int p = s / Q, k = s - p * Q;
                         const A *b = p1 + e * S + p * QQ + k;
 #pragma unroll
                         for (int r = 0; r < Q; ++r) x[r] = b[r * Q]; },
-                    tBaT, [=](int e, int s, int o, A v) { const int p = s / Q, k = s - p * Q;
+                    [=](int e, int s, int o, A v) { const int p = s / Q, k = s - p * Q;
                         p2[e * S + (p * N + o) * Q + k] = v; });
             } else {  // TET: t1[pair(p,q)][k] = sum_j psiB_pq(z2_j) t2[p][j][k]; edge (0,1,.) also gets p = 1
                 sfor<0, N>([&](auto cc) {
@@ -359,11 +436,11 @@ struct Modal {
             __syncthreads();
             // ---- transpose of stage 1
             if constexpr (SH == HEX) {
-                pencils0<A, Q, N, EPB, NT>(N * N, rot,
+                sym_iprod<A, N, Q, EPB, NT>(N * N, rot, tab + L.Bs,
                     [=](int e, int s, A *x) { const A *b = p2 + e * S + s * Q;
 #pragma unroll
                         for (int r = 0; r < Q; ++r) x[r] = b[r]; },
-                    tBaT, [=](int e, int s, int o, A v) { outm[e * S + s * N + o] = v; });
+                    [=](int e, int s, int o, A v) { outm[e * S + s * N + o] = v; });
             } else if constexpr (SH == PRISM) {
                 sfor<0, N>([&](auto cc) {
                     constexpr int p = decltype(cc)::value;
@@ -411,22 +488,20 @@ struct Modal {
     template <class TP>
     static __device__ __forceinline__ void last(TP tab, A *in, A *out)
     {
-        const TP Ba = tab + L.Ba;
         int rot = 0;
-        auto tBa = [=](int z, int o, int r) { return Ba(z, o * N + r); };
         if constexpr (SH == QUAD || SH == TRI) {
-            pencils0<A, N, Q, EPB, NT>(Q, rot,
+            sym_bwd<A, N, Q, EPB, NT>(Q, rot, tab + L.Bs,
                 [=](int e, int s, A *x) { const A *b = in + e * S + s;
 #pragma unroll
                     for (int r = 0; r < N; ++r) x[r] = b[r * Q]; },
-                tBa, [=](int e, int s, int o, A v) { out[e * S + o + Q * s] = v; });
+                [=](int e, int s, int o, A v) { out[e * S + o + Q * s] = v; });
         } else {
-            pencils0<A, N, Q, EPB, NT>(QQ, rot,
+            sym_bwd<A, N, Q, EPB, NT>(QQ, rot, tab + L.Bs,
                 [=](int e, int s, A *x) { const int k = s / Q, j = s - k * Q;
                     const A *b = in + e * S + j * Q + k;
 #pragma unroll
                     for (int r = 0; r < N; ++r) x[r] = b[r * QQ]; },
-                tBa, [=](int e, int s, int o, A v) { out[e * S + o + Q * s] = v; });
+                [=](int e, int s, int o, A v) { out[e * S + o + Q * s] = v; });
         }
         __syncthreads();
     }
@@ -435,21 +510,19 @@ struct Modal {
     template <class TP>
     static __device__ __forceinline__ void first(TP tab, A *in, A *out)
     {
-        const TP Ba = tab + L.Ba;
         int rot = 0;
-        auto tBaT = [=](int z, int o, int r) { return Ba(z, r * N + o); };
         if constexpr (SH == QUAD || SH == TRI) {
-            pencils0<A, Q, N, EPB, NT>(Q, rot,
+            sym_iprod<A, N, Q, EPB, NT>(Q, rot, tab + L.Bs,
                 [=](int e, int s, A *x) { const A *b = in + e * S + Q * s;
 #pragma unroll
                     for (int r = 0; r < Q; ++r) x[r] = b[r]; },
-                tBaT, [=](int e, int s, int o, A v) { out[e * S + o * Q + s] = v; });
+                [=](int e, int s, int o, A v) { out[e * S + o * Q + s] = v; });
         } else {
-            pencils0<A, Q, N, EPB, NT>(QQ, rot,
+            sym_iprod<A, N, Q, EPB, NT>(QQ, rot, tab + L.Bs,
                 [=](int e, int s, A *x) { const A *b = in + e * S + Q * s;
 #pragma unroll
                     for (int r = 0; r < Q; ++r) x[r] = b[r]; },
-                tBaT, [=](int e, int s, int o, A v) { const int k = s / Q, j = s - k * Q;
+                [=](int e, int s, int o, A v) { const int k = s / Q, j = s - k * Q;
                     out[e * S + o * QQ + j * Q + k] = v; });
         }
         __syncthreads();
@@ -612,7 +685,7 @@ struct HelmStages {
     template <class TP>
     static __device__ __forceinline__ void last_grad1(TP tab, const A *in, A *U, A *V1)
     {
-        const TP Ba = tab + L.Ba, D1 = tab + L.D1;
+        const TP Bs = tab + L.Bs, D1 = tab + L.D1;
         int rot = 0;
         for_items<EPB, NT>(PER, rot, [&](int e, int s, int z) {
             A x[N];
@@ -627,14 +700,34 @@ struct HelmStages {
                 for (int r = 0; r < N; ++r) x[r] = b[r * Q];
             }
             A u[Q];
+            {  // u = psiA x in even/odd form (see sym_bwd)
+                constexpr int QL = Q / 2, NE = sym_ne(N), NO = sym_no(N), W = NE + NO;
+                A xe[NE], xo[NO];
+                xe[0] = x[0] + x[1];
+                xo[0] = x[0] - x[1];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                A acc = A(0);
+                for (int k = 1; k < NE; ++k) xe[k] = x[2 * k];
 #pragma unroll
-                for (int r = 0; r < N; ++r) acc = fmaa(Ba(z, i * N + r), x[r], acc);
-                u[i] = acc;
-                U[e * S + i + Q * s] = acc;
+                for (int k = 1; k < NO; ++k) xo[k] = x[2 * k + 1];
+#pragma unroll
+                for (int i = 0; i < QL; ++i) {
+                    A E = A(0), O = A(0);
+#pragma unroll
+                    for (int k = 0; k < NE; ++k) E = fmaa(Bs(z, i * W + k), xe[k], E);
+#pragma unroll
+                    for (int k = 0; k < NO; ++k) O = fmaa(Bs(z, i * W + NE + k), xo[k], O);
+                    u[i] = E + O;
+                    u[Q - 1 - i] = E - O;
+                }
+                if constexpr (Q % 2 == 1) {
+                    A E = A(0);
+#pragma unroll
+                    for (int k = 0; k < NE; ++k) E = fmaa(Bs(z, QL * W + k), xe[k], E);
+                    u[QL] = E;
+                }
             }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) U[e * S + i + Q * s] = u[i];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 A acc = A(0);
@@ -773,7 +866,7 @@ struct HelmStages {
     template <class TP>
     static __device__ __forceinline__ void t1_first(TP tab, const A *U, const A *V1, A *out)
     {
-        const TP Ba = tab + L.Ba, D1 = tab + L.D1;
+        const TP Bs = tab + L.Bs, D1 = tab + L.D1;
         int rot = 0;
         for_items<EPB, NT>(PER, rot, [&](int e, int s, int z) {
             const A *bv = V1 + e * S + Q * s;
@@ -788,16 +881,46 @@ struct HelmStages {
                 for (int r = 0; r < Q; ++r) acc = fmaa(D1(z, r * Q + i), v[r], acc);
                 y[i] = acc;
             }
+            // t[p] = sum_i psiA_p(z_i) y_i in even/odd form (see sym_iprod)
+            constexpr int QL = Q / 2, QH = (Q + 1) / 2, NE = sym_ne(N), NO = sym_no(N), W = NE + NO;
+            A t[N];
+            {
+                A fe[QH], fo[QL];
+#pragma unroll
+                for (int i = 0; i < QL; ++i) {
+                    fe[i] = y[i] + y[Q - 1 - i];
+                    fo[i] = y[i] - y[Q - 1 - i];
+                }
+                if constexpr (Q % 2 == 1) fe[QL] = y[QL];
+                A Se = A(0), So = A(0);
+#pragma unroll
+                for (int i = 0; i < QH; ++i) Se = fmaa(Bs(z, i * W), fe[i], Se);
+#pragma unroll
+                for (int i = 0; i < QL; ++i) So = fmaa(Bs(z, i * W + NE), fo[i], So);
+                t[0] = Se + So;
+                t[1] = Se - So;
+#pragma unroll
+                for (int k = 1; k < NE; ++k) {
+                    A acc = A(0);
+#pragma unroll
+                    for (int i = 0; i < QH; ++i) acc = fmaa(Bs(z, i * W + k), fe[i], acc);
+                    t[2 * k] = acc;
+                }
+#pragma unroll
+                for (int k = 1; k < NO; ++k) {
+                    A acc = A(0);
+#pragma unroll
+                    for (int i = 0; i < QL; ++i) acc = fmaa(Bs(z, i * W + NE + k), fo[i], acc);
+                    t[2 * k + 1] = acc;
+                }
+            }
 #pragma unroll
             for (int p = 0; p < N; ++p) {
-                A acc = A(0);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) acc = fmaa(Ba(z, i * N + p), y[i], acc);
                 if constexpr (D == 3) {
                     const int k = s / Q, j = s - k * Q;
-                    out[e * S + p * QQ + j * Q + k] = acc;
+                    out[e * S + p * QQ + j * Q + k] = t[p];
                 } else {
-                    out[e * S + p * Q + s] = acc;
+                    out[e * S + p * Q + s] = t[p];
                 }
             }
         });

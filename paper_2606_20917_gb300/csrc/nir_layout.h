@@ -77,13 +77,19 @@ NIR_HD constexpr int prism_m0(int N, int p, int q)
 //  Bc : ragged classes c = 0..N-1, Q x (N-c): psiB_cr(z3_k)  (tet eta3; c = p+q)
 //  D1, D2, D3 : Q x Q collocation derivative matrices, D[i*Q + i'] = l'_i'(z_i)
 //  wq : reference quadrature weight per point (collapse factors included)
+//  Bs : even/odd form of Ba on the symmetric first-direction points, ceil(Q/2)
+//       rows of sym_ne(N) + sym_no(N) values: [(Ba_i0 + Ba_i1)/2, Ba_i2, Ba_i4, ...]
+//       then [(Ba_i0 - Ba_i1)/2, Ba_i3, Ba_i5, ...]
 struct TabLayout {
-    int Ba, Bb, Bc, D1, D2, D3, wq, total;
+    int Ba, Bb, Bc, D1, D2, D3, wq, Bs, total;
 };
+
+NIR_HD constexpr int sym_ne(int N) { return 1 + (N - 1) / 2; }
+NIR_HD constexpr int sym_no(int N) { return 1 + (N - 2) / 2; }
 
 NIR_HD constexpr TabLayout layout(int s, int N, int Q)
 {
-    TabLayout L{0, 0, 0, 0, 0, 0, 0, 0};
+    TabLayout L{0, 0, 0, 0, 0, 0, 0, 0, 0};
     int o = 0;
     L.Ba = o; o += Q * N;
     L.Bb = o; if (s == TRI || s == TET || s == PRISM) o += cls_size(N, Q);
@@ -92,6 +98,7 @@ NIR_HD constexpr TabLayout layout(int s, int N, int Q)
     L.D2 = o; if (s == TRI || s == TET) o += Q * Q;
     L.D3 = o; if (s == TET || s == PRISM) o += Q * Q;
     L.wq = o; o += npts(s, Q);
+    L.Bs = o; o += ((Q + 1) / 2) * (sym_ne(N) + sym_no(N));
     L.total = o;
     // directions sharing a rule share a table
     if (s == QUAD || s == HEX) { L.D2 = L.D1; L.D3 = L.D1; }
