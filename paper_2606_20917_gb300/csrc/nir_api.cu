@@ -506,8 +506,24 @@ extern "C" int nir_helmholtz_host(nir_block *b, int prec, double lambda, const v
     }
     cudaStream_t st = b->ctx->stream;
     const long long E = b->d.nelem;
-    long long chunk = ((E + NIR_HOST_CHUNKS - 1) / NIR_HOST_CHUNKS + 63) / 64 * 64;
-    if (chunk < 256) chunk = E;  // small blocks: one chunk
+    // chunks of whole waves (CTAs x elements per CTA), about four of them, so
+    // the chunked launches keep full waves and only the first copy-in and
+    // the last copy-out stay exposed
+    long long chunk = E;
+    {
+        KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, nirk::OP_HELM, b->helm_variant[prec]);
+        if (!ki.fn) ki = nir_kinfo(b->d.shape, b->d.P, prec, nirk::OP_HELM, 0);
+        const int occ = ki.fn ? nir_occupancy(b->ctx, ki) : -1;
+        if (occ > 0) {
+            const long long grid = b->helm_grid[prec] > 0 ? b->helm_grid[prec] : (long long)occ * b->ctx->num_sms;
+            const long long wave = ((grid * ki.epb + 63) / 64) * 64;
+            const long long waves = (E + wave - 1) / wave;
+            const long long per = (waves + 3) / 4;
+            if (waves >= 2) chunk = per * wave;
+        }
+    }
+    if ((E + chunk - 1) / chunk > NIR_HOST_CHUNKS)  // never more chunks than events
+        chunk = ((E + NIR_HOST_CHUNKS - 1) / NIR_HOST_CHUNKS + 63) / 64 * 64;
     const size_t row = (size_t)b->M * es;
     int k = 0;
     for (long long e0 = 0; e0 < E; e0 += chunk, ++k) {
