@@ -43,6 +43,30 @@ def helm_flops_per_elem(shape: str, N: int, Q: int) -> int:
     raise ValueError("roofline accounting implemented for the hexahedral workloads")
 
 
+def op_work_per_elem(op: str, N: int, Q: int, wb: int, deformed: bool):
+    """(algorithmic flops, algorithmic bytes) per hexahedron for each operator.
+
+    Flops are the plain sum-factorised counts: one psiA contraction sweep is
+    2N(N^2 Q + N Q^2 + Q^3), a collocation derivative 2 Q^4 per direction,
+    a physical-derivative chain rule 2 d^2 Q^3.  Bytes are the arrays read
+    and written once (coefficients M, point fields Q^3, per-point factors:
+    W alone, 9 + 1 for d eta/d x with W)."""
+    M, P3 = N ** 3, Q ** 3
+    sweep = 2 * N * (N * N * Q + N * Q * Q + Q ** 3)
+    fac = 1 if deformed else 0
+    if op == "bwd":
+        return sweep, (M + P3) * wb
+    if op == "iprod":
+        return sweep + P3, (P3 + M + fac * P3) * wb
+    if op == "physderiv":
+        return 3 * 2 * Q ** 4 + 18 * P3, (P3 + 3 * P3 + fac * 10 * P3) * wb
+    if op == "iprod_deriv":
+        return 3 * 2 * Q ** 4 + 19 * P3 + sweep, (3 * P3 + M + fac * 10 * P3) * wb
+    if op == "mass":
+        return 2 * sweep + P3, (2 * M + fac * P3) * wb
+    raise KeyError(op)
+
+
 def helm_bytes_per_elem(shape: str, N: int, Q: int, wb: int, deformed: bool) -> int:
     M = N ** 3
     geo = 7 * Q ** 3 if deformed else 7
@@ -311,6 +335,10 @@ def run_nir(args, ws, rank, local):
                     "traffic": profiled_traffic(f"helm_{args.workload}_{args.prec}"),
                     "bytes_per_elem": work_bytes // E,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "_fallback" not in peaks else "fallback 6.8 TB/s"}
+    operators = {}
+    if shape == "hex" and ws == 1 and not args.no_operators:
+        operators = operator_table(blk, args.prec, dev, stream, wl, ctx if args.prec == "f64" else None, peaks,
+                                   roof["peak"] if (roof and args.prec == "f64") else None)
     extras = {}
     if args.extras and ws == 1:
         for p in ("f32", "bf16"):
@@ -335,11 +363,61 @@ def run_nir(args, ws, rank, local):
                            l2=f"no flush: {work_bytes / 2**20:.0f} MiB streamed per step > 129 MiB L2"),
             "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk.summary(),
             "kernel_ms_per_launch": statistics.mean(per_launch)}
+    if operators:
+        line["operators"] = operators
     if extras:
         line["extras"] = extras
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, wl)
     print(json.dumps(line), flush=True)
+
+
+def operator_table(blk, prec, dev, stream, wl, ctx, peaks, fp64_peak):
+    """Throughput and roofline fraction of every elemental operator (not only
+    the fused Helmholtz) on the same block, timed with CUDA events."""
+    import torch
+    import paper_2606_20917_gb300 as nir
+    E, M, NQ = blk.nelem, blk.M, blk.NQ
+    dt = nir.DTYPE[prec]
+    wb = torch.empty((), dtype=dt).element_size()
+    N, Q = wl["P"] + 1, wl["Q"]
+    u = torch.from_numpy(W.coefficients(E, M, seed=0)).to(dev, dt)
+    f = torch.from_numpy(W.phys_samples(E, NQ, seed=1)).to(dev, dt)
+    fs = [torch.from_numpy(W.phys_samples(E, NQ, seed=2 + i)).to(dev, dt) for i in range(3)]
+    outs = {"bwd": torch.empty((E, NQ), dtype=dt, device=dev), "m": torch.empty((E, M), dtype=dt, device=dev),
+            "d": [torch.empty((E, NQ), dtype=dt, device=dev) for _ in range(3)]}
+    calls = {
+        "bwd": lambda: blk.bwd_trans(u, prec=prec, out=outs["bwd"]),
+        "iprod": lambda: blk.iproduct_wrt_base(f, prec=prec, out=outs["m"]),
+        "physderiv": lambda: blk.phys_deriv(f, prec=prec, outs=outs["d"]),
+        "iprod_deriv": lambda: blk.iproduct_wrt_deriv_base(fs, prec=prec, out=outs["m"]),
+        "mass": lambda: blk.mass(u, prec=prec, out=outs["m"]),
+    }
+    res = {}
+    for op, fn in calls.items():
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(10):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) / 10 * 1e-3
+        flops, byts = op_work_per_elem(op, N, Q, wb, wl["deformed"])
+        r = {"gdofs": E * M / sec / 1e9, "ms": sec * 1e3, "flops_per_elem": flops, "bytes_per_elem": byts}
+        if prec == "f64" and fp64_peak:
+            # FP64 on GB300: the ridge is ~0.19 flop/B, so every operator is FP64-pipe bound
+            ach = flops * E / sec / 1e12
+            r["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                             "frac": ach / fp64_peak}
+        else:
+            gbs = byts * E / sec / 1e9
+            pk = peaks.get("hbm_gbs", 6800.0)
+            r["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": pk, "unit": "GB/s", "frac": gbs / pk}
+        res[op] = r
+    return res
 
 
 def run_solve(args, ws, rank, local):
@@ -480,6 +558,7 @@ def main():
     ap.add_argument("--sample", type=int, default=256, help="reference arm: elements per step")
     ap.add_argument("--extras", action="store_true", help="also time the FP32/BF16 applies")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-operators", action="store_true", help="skip the per-operator table")
     ap.add_argument("--mode", choices=["apply", "solve", "hybrid"], default="apply")
     ap.add_argument("--solve-precs", default="f64,f32,bf16")
     ap.add_argument("--tol", type=float, default=1e-10)

@@ -1221,10 +1221,13 @@ __global__ void __launch_bounds__(512)
     const T *in = reinterpret_cast<const T *>(a.in0);
     const T *G = reinterpret_cast<const T *>(a.geo);
     // issue the copy of group g (thread 0); returns whether it was issued
-    auto prefetch_metric = [&](long long e0) {  // EPB / 32 whole chunks of the metric
-        if (a.pf && a.geo_pp && (EPB % 32) == 0) {
+    // the whole 32-element chunks of the metric covering the group (a group
+    // smaller than a chunk prefetches its whole chunk)
+    auto prefetch_metric = [&](long long e0) {
+        constexpr int span = EPB >= 32 ? EPB : 32;
+        if (a.pf && a.geo_pp && ((EPB % 32) == 0 || (32 % EPB) == 0)) {
             const char *gp = reinterpret_cast<const char *>(G + (((e0 >> 5) * NQ * NG) << 5));
-            const long long gbytes = (long long)NQ * NG * EPB * (long long)sizeof(T);
+            const long long gbytes = (long long)NQ * NG * span * (long long)sizeof(T);
             for (long long off = 0; off < gbytes; off += 32768)
                 l2_prefetch(gp + off, (unsigned)((gbytes - off) < 32768 ? (gbytes - off) : 32768));
         }

@@ -402,7 +402,7 @@ extern "C" int nir_tune(nir_mesh *m, const char *cache_path)
                 KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, 5, v);
                 if (!ki.fn || (v > 0 && ki.epb == nir_kinfo(b->d.shape, b->d.P, prec, 5, 0).epb)) continue;
                 int occ = nir_occupancy(ctx, ki);
-                const int npf = (prec != NIR_F64 && b->geo_pp && ki.epb % 32 == 0) ? 2 : 1;
+                const int npf = (prec != NIR_F64 && b->geo_pp && (ki.epb % 32 == 0 || 32 % ki.epb == 0)) ? 2 : 1;
                 for (int c = 1; c <= std::max(1, occ) && !rc; ++c)
                     for (int pf = 0; pf < npf && !rc; ++pf) {
                         b->helm_variant[prec] = v;
