@@ -221,3 +221,80 @@ def hybrid_mesh(seed: int = 0, scale: int = 1) -> list[dict]:
             blocks.append(dict(shape=shape, P=int(P), Q=int(P) + 2, gorder=g,
                                nodes=np.ascontiguousarray(nd), deformed=deformed))
     return blocks
+
+
+# --- conforming meshes (vertex connectivity) --------------------------------------
+
+def grid_vertices(n: int, d: int, count: int | None = None) -> np.ndarray:
+    """Global vertex ids of the cells of an n^d grid, in the cell order of
+    ``quad_grid(n, n)`` / ``hex_grid(n, g)`` (x fastest).
+
+    Local vertex v = a + 2b (+ 4c) sits at reference xi = (-1 + 2a, -1 + 2b(, -1 + 2c));
+    global vertex (I, J(, K)) has id I + (n+1)(J + (n+1)K).  Returns int64 [E][2^d].
+    """
+    cells = np.arange(n ** d)
+    ci = [(cells // n ** k) % n for k in range(d)]
+    out = np.zeros((cells.size, 2 ** d), dtype=np.int64)
+    for v in range(2 ** d):
+        bits = [(v >> k) & 1 for k in range(d)]
+        gid = np.zeros(cells.size, dtype=np.int64)
+        for k in range(d - 1, -1, -1):
+            gid = gid * (n + 1) + ci[k] + bits[k]
+        out[:, v] = gid
+    return out if count is None else out[:count]
+
+
+def _rotations(d: int) -> list[np.ndarray]:
+    """Signed permutation matrices of determinant +1 (the proper symmetries of
+    the reference square or cube)."""
+    import itertools
+    out = []
+    for perm in itertools.permutations(range(d)):
+        for signs in itertools.product((1, -1), repeat=d):
+            R = np.zeros((d, d))
+            for i in range(d):
+                R[i, perm[i]] = signs[i]
+            if np.linalg.det(R) > 0.5:
+                out.append(R)
+    return out
+
+
+def rotate_elements(nodes: np.ndarray, verts: np.ndarray, g: int, seed: int = 0):
+    """Re-describe every element in a randomly rotated local frame.
+
+    Element e gets a proper symmetry R_e of the reference element; its new
+    local point xi' is the old local point R_e xi'.  The lattice nodes [E][(g+1)^d][d]
+    and the vertex ids [E][2^d] are permuted accordingly, so the physical
+    elements are unchanged while neighbouring elements see their shared faces
+    in different orientations.  Returns (nodes, verts, rotation index per element).
+    """
+    d = nodes.shape[-1]
+    rots = _rotations(d)
+    rng = np.random.default_rng(seed)
+    which = rng.integers(0, len(rots), size=nodes.shape[0])
+
+    def index_map(gg):
+        t = np.arange(gg + 1)
+        grids = np.meshgrid(*([t] * d), indexing="ij")  # grids[k][..] = index along axis k
+        new_idx = np.stack([gr.ravel() for gr in grids], axis=1)  # rows: (a0, a1, ...) new indices
+        maps = []
+        for R in rots:
+            xi_new = -1.0 + 2.0 * new_idx / gg
+            xi_old = xi_new @ R.T
+            old_idx = np.rint((xi_old + 1.0) * gg / 2.0).astype(np.int64)
+            lin_new = sum(new_idx[:, k] * (gg + 1) ** k for k in range(d))
+            lin_old = sum(old_idx[:, k] * (gg + 1) ** k for k in range(d))
+            m = np.empty((gg + 1) ** d, dtype=np.int64)
+            m[lin_new] = lin_old
+            maps.append(m)
+        return maps
+
+    nmap, vmap = index_map(g), index_map(1)
+    new_nodes = np.empty_like(nodes)
+    new_verts = np.empty_like(verts)
+    for r in range(len(rots)):
+        sel = np.nonzero(which == r)[0]
+        if sel.size:
+            new_nodes[sel] = nodes[sel][:, nmap[r], :]
+            new_verts[sel] = verts[sel][:, vmap[r]]
+    return new_nodes, new_verts, which
