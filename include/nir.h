@@ -213,6 +213,74 @@ typedef struct {
 int nir_cg_solve(nir_mesh *mesh, double lambda, const double *b, double *x, const nir_cg_opts *opts,
                  nir_cg_stats *stats);
 
+/* ---------------------------------------------------------------------------
+ * Conforming C0 assembly (quadrilateral and hexahedral blocks).
+ *
+ * The elemental operators above act on broken (element-local) expansions; the
+ * paper's solve leaves assembly out (Sec. 2.1).  An assembly object joins the
+ * elements of conforming blocks into the continuous spectral/hp space of the
+ * modified basis: a global vector x_g maps to element coefficients by
+ * x_loc = A x_g (every local mode takes +-1 times one global dof; the sign
+ * accounts for the orientation of shared edges and faces), and element
+ * results are summed back by y_g = A^T y_loc.  The assembled Helmholtz
+ * operator is A^T H A (H = L + lambda M elementwise), the assembled mass
+ * operator A^T M A.
+ *   - Global vectors hold n_global entries: the n_free dofs not on the mesh
+ *     boundary first, then the boundary dofs.  Local vectors are the
+ *     concatenation of the blocks' [E][M] arrays in block order.
+ *   - Boundary = faces (2-D: edges) held by one element, with their vertices
+ *     and edges.
+ * --------------------------------------------------------------------------- */
+typedef struct nir_asm nir_asm;
+
+enum { NIR_ASM_HELMHOLTZ = 0, NIR_ASM_MASS = 1 };
+
+/* Build the global numbering of conforming blocks of one shape (NIR_QUAD or
+ * NIR_HEX) and one P.  vertex_ids[b]: HOST int64 array [nelem_b][2^d] of the
+ * global vertex ids of block b's elements, local vertex v = a + 2b (+ 4c) at
+ * reference coordinates xi = (-1+2a, -1+2b(, -1+2c)) -- the corners of the
+ * geometry lattice of nir_block_set_geometry.  Elements may see shared faces
+ * in any orientation.  The object keeps pointers to the blocks, which must
+ * outlive it.  Errors: INVALID_ARG (null pointers, a face held by more than
+ * two elements), UNSUPPORTED (other shapes, mixed shapes or orders),
+ * TOO_LARGE (2^31 or more dofs), NO_MEMORY, CUDA. */
+int nir_asm_create(nir_ctx *ctx, nir_block *const *blocks, const int64_t *const *vertex_ids, int nblocks,
+                   nir_asm **out);
+void nir_asm_destroy(nir_asm *a);
+/* The numbering alone, on the host (no GPU needed): nblocks blocks of nelem[b]
+ * elements of `shape` (NIR_QUAD / NIR_HEX) and degree P with vertex ids as for
+ * nir_asm_create.  map_out: HOST int64 [sum_b nelem[b] * M] receiving
+ * s (g + 1) per local dof (may be NULL); n_global, n_free as for
+ * nir_asm_num_dofs.  nir_asm_create uses exactly this numbering. */
+int nir_c0_numbering(int shape, int P, int nblocks, const int64_t *nelem, const int64_t *const *vertex_ids,
+                     int64_t *map_out, int64_t *n_global, int64_t *n_free);
+/* Sizes: global dofs, free (non-boundary) dofs, local dofs; NULL outputs skipped. */
+int nir_asm_num_dofs(const nir_asm *a, int64_t *n_global, int64_t *n_free, int64_t *n_local);
+/* HOST copy of the map: map_out[i] = s (g + 1) for local dof i, s = +-1. */
+int nir_asm_local_map(const nir_asm *a, int64_t *map_out);
+/* x_local = A x_global; DEVICE arrays in the precision's type. */
+int nir_asm_gather(nir_asm *a, int prec, const void *x_global, void *x_local);
+/* y_global = A^T y_local (sums in FP64, a fixed order per dof: deterministic). */
+int nir_asm_assemble(nir_asm *a, int prec, const void *y_local, void *y_global);
+/* x_global from a continuous local vector: each dof takes its first local
+ * copy times its sign (the inverse of nir_asm_gather on its range); FP64. */
+int nir_asm_pick(nir_asm *a, const double *x_local, double *x_global);
+/* y_global = A^T K A x_global with K the elemental Helmholtz (op
+ * NIR_ASM_HELMHOLTZ, lambda) or mass (NIR_ASM_MASS) operator: gather, one
+ * elemental launch per block, assembly.  DEVICE arrays [n_global] in prec. */
+int nir_asm_apply(nir_asm *a, int op, double lambda, int prec, const void *x_global, void *y_global);
+/* Solve the assembled system (options as nir_cg_solve).  b, x: DEVICE FP64
+ * [n_global].  fix_boundary = 1: the boundary entries of x are Dirichlet
+ * data and stay fixed; the free entries solve rows 0..n_free-1 of
+ * A^T K A x = b (the boundary values enter through the FP64 residual).
+ * fix_boundary = 0: all n_global entries are unknowns (e.g. the L2
+ * projection with NIR_ASM_MASS, or natural boundaries with lambda > 0).  x holds
+ * the initial guess on entry.  lambda is ignored for NIR_ASM_MASS.
+ * Synchronous.  Errors: INVALID_ARG, STATE, NOT_CONVERGED, NONFINITE, CUDA,
+ * NO_MEMORY. */
+int nir_asm_cg_solve(nir_asm *a, int op, double lambda, int fix_boundary, const double *b, double *x,
+                     const nir_cg_opts *opts, nir_cg_stats *stats);
+
 /* Measure the FP64 FMA throughput of the device (TFLOP/s) with a register-
  * resident DFMA loop; used as the FP64 roofline ceiling. Synchronous. */
 int nir_probe_fp64_peak(nir_ctx *ctx, double *tflops);

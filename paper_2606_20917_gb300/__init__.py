@@ -69,12 +69,20 @@ _SIGS = {
     "nir_tune": [_vp, C.c_char_p],
     "nir_cg_solve": [_vp, _d, _vp, _vp, C.POINTER(CGOpts), C.POINTER(CGStats)],
     "nir_probe_fp64_peak": [_vp, C.POINTER(_d)],
+    "nir_asm_create": [_vp, C.POINTER(_vp), C.POINTER(_vp), _i, C.POINTER(_vp)],
+    "nir_asm_num_dofs": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)],
+    "nir_asm_local_map": [_vp, _vp],
+    "nir_asm_gather": [_vp, _i, _vp, _vp],
+    "nir_asm_assemble": [_vp, _i, _vp, _vp],
+    "nir_asm_pick": [_vp, _vp, _vp],
+    "nir_asm_apply": [_vp, _i, _d, _i, _vp, _vp],
+    "nir_asm_cg_solve": [_vp, _i, _d, _i, _vp, _vp, C.POINTER(CGOpts), C.POINTER(CGStats)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
     _f.restype = _i
-for _name in ("nir_ctx_destroy", "nir_block_destroy", "nir_mesh_destroy"):
+for _name in ("nir_ctx_destroy", "nir_block_destroy", "nir_mesh_destroy", "nir_asm_destroy"):
     getattr(_lib, _name).argtypes = [_vp]
     getattr(_lib, _name).restype = None
 _lib.nir_strerror.argtypes = [_i]
@@ -300,5 +308,95 @@ class Mesh:
         o = CGOpts(PREC[inner_prec], float(tol), int(max_outer), int(max_inner), float(inner_tol), int(jacobi))
         s = CGStats()
         rc = _lib.nir_cg_solve(self.h, float(lam), _ptr(b), _ptr(x), C.byref(o), C.byref(s))
+        return rc, dict(outer=s.outer, inner_total=s.inner_total, rel_residual=s.rel_residual,
+                        seconds=s.seconds)
+
+
+ASM_OPS = {"helmholtz": 0, "mass": 1}
+
+
+class Assembly:
+    """Conforming C0 assembly of quad or hex blocks (global vectors: free dofs
+    first, then boundary dofs; local vectors: the blocks' [E][M] arrays
+    concatenated)."""
+
+    def __init__(self, ctx: Context, blocks: list[Block], vertex_ids: list):
+        import numpy as np
+        self.ctx, self.blocks = ctx, list(blocks)
+        nv = 4 if blocks[0].dim == 2 else 8
+        self._verts = []
+        for b, v in zip(blocks, vertex_ids):
+            v = np.ascontiguousarray(np.asarray(v, dtype=np.int64))
+            if v.shape != (b.nelem, nv):
+                raise ValueError(f"vertex ids must be [{b.nelem}][{nv}]")
+            self._verts.append(v)
+        if len(self._verts) != len(blocks):
+            raise ValueError("one vertex-id array per block")
+        barr = (_vp * len(blocks))(*[b.h for b in blocks])
+        varr = (_vp * len(blocks))(*[v.ctypes.data_as(_vp) for v in self._verts])
+        h = _vp()
+        _chk(_lib.nir_asm_create(ctx.h, barr, varr, len(blocks), C.byref(h)), "nir_asm_create")
+        self.h = h
+        ng, nf, nl = _i64(), _i64(), _i64()
+        _chk(_lib.nir_asm_num_dofs(h, C.byref(ng), C.byref(nf), C.byref(nl)), "nir_asm_num_dofs")
+        self.n_global, self.n_free, self.n_local = ng.value, nf.value, nl.value
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            _lib.nir_asm_destroy(h)
+            self.h = None
+
+    def _vec(self, t, n, prec, name):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != DTYPE[prec] or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous CUDA {DTYPE[prec]} tensor")
+        if t.numel() != n:
+            raise ValueError(f"{name} must hold {n} values")
+        return t
+
+    def _new(self, n, prec):
+        return torch.empty(n, dtype=DTYPE[prec], device=f"cuda:{self.ctx.device}")
+
+    def local_map(self):
+        """Host int64 [n_local]: s * (g + 1) per local dof."""
+        import numpy as np
+        out = np.zeros(self.n_local, dtype=np.int64)
+        _chk(_lib.nir_asm_local_map(self.h, out.ctypes.data_as(_vp)), "nir_asm_local_map")
+        return out
+
+    def gather(self, xg, prec="f64", out=None):
+        self._vec(xg, self.n_global, prec, "x_global")
+        out = self._new(self.n_local, prec) if out is None else self._vec(out, self.n_local, prec, "out")
+        _chk(_lib.nir_asm_gather(self.h, PREC[prec], _ptr(xg), _ptr(out)), "nir_asm_gather")
+        return out
+
+    def assemble(self, yl, prec="f64", out=None):
+        self._vec(yl, self.n_local, prec, "y_local")
+        out = self._new(self.n_global, prec) if out is None else self._vec(out, self.n_global, prec, "out")
+        _chk(_lib.nir_asm_assemble(self.h, PREC[prec], _ptr(yl), _ptr(out)), "nir_asm_assemble")
+        return out
+
+    def pick(self, xl, out=None):
+        self._vec(xl, self.n_local, "f64", "x_local")
+        out = self._new(self.n_global, "f64") if out is None else self._vec(out, self.n_global, "f64", "out")
+        _chk(_lib.nir_asm_pick(self.h, _ptr(xl), _ptr(out)), "nir_asm_pick")
+        return out
+
+    def apply(self, xg, op="helmholtz", lam=1.0, prec="f64", out=None):
+        self._vec(xg, self.n_global, prec, "x_global")
+        out = self._new(self.n_global, prec) if out is None else self._vec(out, self.n_global, prec, "out")
+        _chk(_lib.nir_asm_apply(self.h, ASM_OPS[op], float(lam), PREC[prec], _ptr(xg), _ptr(out)),
+             "nir_asm_apply")
+        return out
+
+    def cg_solve(self, b, x, op="helmholtz", lam=1.0, fix_boundary=True, inner_prec="f32", tol=1e-10,
+                 max_outer=50, max_inner=5000, inner_tol=1e-3, jacobi=True):
+        """Returns (status code, stats dict); x is updated in place."""
+        self._vec(b, self.n_global, "f64", "b")
+        self._vec(x, self.n_global, "f64", "x")
+        o = CGOpts(PREC[inner_prec], float(tol), int(max_outer), int(max_inner), float(inner_tol), int(jacobi))
+        s = CGStats()
+        rc = _lib.nir_asm_cg_solve(self.h, ASM_OPS[op], float(lam), int(bool(fix_boundary)), _ptr(b), _ptr(x),
+                                   C.byref(o), C.byref(s))
         return rc, dict(outer=s.outer, inner_total=s.inner_total, rel_residual=s.rel_residual,
                         seconds=s.seconds)

@@ -40,7 +40,8 @@ def _units():
         for p in range(3):
             units.append((os.path.join(CSRC, "nir_mesh_inst.cu"), f"mesh_d{d}_p{p}.o",
                           [f"-DNIR_MESH_DIM={d}", f"-DNIR_PREC={p}"]))
-    for src in ("nir_api.cu", "nir_geom.cu", "nir_solve.cu", "nir_cg.cu", "nir_noalloc.cu", "nir_basis.cpp"):
+    for src in ("nir_api.cu", "nir_geom.cu", "nir_solve.cu", "nir_cg.cu", "nir_asm.cu", "nir_noalloc.cu",
+                "nir_basis.cpp"):
         units.append((os.path.join(CSRC, src), os.path.splitext(src)[0] + ".o", []))
     return units
 

@@ -1,6 +1,7 @@
-// nir_cg.cu -- conjugate-gradient Helmholtz solve on a mesh's broken
-// (element-block-diagonal) operator, plain FP64 or mixed precision with FP64
-// iterative refinement (defect correction).
+// nir_cg.cu -- conjugate-gradient solve of an SPD operator (a mesh's broken,
+// element-block-diagonal Helmholtz operator, or an assembled C0 operator),
+// plain FP64 or mixed precision with FP64 iterative refinement (defect
+// correction).
 //
 // The paper uses the Helmholtz operator inside CG iterations (Sec. 4, first
 // paragraph); the solver itself is not described there.  Mixed precision:
@@ -8,11 +9,11 @@
 //   repeat: solve H_lo d = r / |r| by preconditioned CG with the operator in
 //           FP32 (or BF16 storage), FP32 vectors and FP64 dot products;
 //           x += |r| d;  r = b - H64 x   until |r| / |b| <= tol.
-// The Jacobi preconditioner's diagonal is extracted by probing: the operator
-// is block diagonal per element with the same mode numbering in every element
-// of a block, so applying it to the vector that is 1 at mode m of every
-// element returns column m of every element matrix, whose mode-m entries are
-// diagonal entries.
+// The Jacobi preconditioner's diagonal comes from the operator (for the mesh
+// operator by probing: it is block diagonal per element with the same mode
+// numbering in every element of a block, so applying it to the vector that is
+// 1 at mode m of every element returns column m of every element matrix, whose
+// mode-m entries are diagonal entries).
 //
 // Scalars (alpha, beta, r.z, r.r) live on the device.  Every reduction writes
 // one partial per CTA; the last CTA to finish (atomic ticket, no waiting)
@@ -27,10 +28,15 @@
 #include <cmath>
 #include <vector>
 
+#include "nir_cg.h"
 #include "nir_internal.h"
 #include "nir_solve.h"
+#include "nir_vec.cuh"
 
 namespace {
+
+using nirv::st_v;
+using nirv::to_d;
 
 struct CGScal {
     double rz, pAp, alpha, beta, rr, thresh;
@@ -38,13 +44,6 @@ struct CGScal {
 };
 
 constexpr int kThreads = 256;
-
-__device__ __forceinline__ double to_d(double v) { return v; }
-__device__ __forceinline__ double to_d(float v) { return (double)v; }
-__device__ __forceinline__ double to_d(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
-__device__ __forceinline__ void st_v(double *p, double v) { *p = v; }
-__device__ __forceinline__ void st_v(float *p, double v) { *p = (float)v; }
-__device__ __forceinline__ void st_v(__nv_bfloat16 *p, double v) { *p = __float2bfloat16_rn((float)v); }
 
 // Block-wide sum of NV doubles; the result is valid in thread 0.
 template <int NV>
@@ -273,7 +272,8 @@ __global__ void k_invert(double *d64, float *d32, long long n, int *bad)
 }  // namespace
 
 struct CGWork {
-    long long n = 0;
+    long long n = 0;              // unknowns
+    long long n_full = 0;         // entries of x (unknowns, then fixed values)
     int grid = 0;                 // CTAs of the vector kernels
     double *x64 = nullptr, *r64 = nullptr, *z64 = nullptr, *p64 = nullptr, *Ap64 = nullptr;
     float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *d32 = nullptr;
@@ -290,55 +290,57 @@ struct CGWork {
     // chunk graphs per inner precision (0: FP64 plain, 1: FP32, 2: BF16)
     cudaGraphExec_t chunk[3] = {nullptr, nullptr, nullptr};
     double chunk_lambda[3] = {0, 0, 0};
-    nirk::MeshBlk *chunk_blk[3] = {nullptr, nullptr, nullptr};
-    nirk::MeshBlk *res_blk = nullptr;   // FP64 residual apply x64 -> Ap64
-    double res_lambda = 0.0;
+    void *chunk_op[3] = {nullptr, nullptr, nullptr};   // operator launch bindings of the graphs
+    CgOperator *chunk_owner[3] = {nullptr, nullptr, nullptr};
     int chunk_len = 25;
 };
 
-void nir_cg_invalidate(nir_mesh *m)
+void nir_cg_work_invalidate(CGWork *w)
 {
-    CGWork *w = m->cg;
     if (!w) return;
     for (int i = 0; i < 3; ++i) {
         if (w->chunk[i]) cudaGraphExecDestroy(w->chunk[i]);
-        if (w->chunk_blk[i]) cudaFree(w->chunk_blk[i]);
+        if (w->chunk_op[i] && w->chunk_owner[i]) w->chunk_owner[i]->release(w->chunk_op[i]);
         w->chunk[i] = nullptr;
-        w->chunk_blk[i] = nullptr;
+        w->chunk_op[i] = nullptr;
+        w->chunk_owner[i] = nullptr;
     }
     w->diag_ready = false;
 }
 
-void nir_cg_free(nir_mesh *m)
+void nir_cg_work_free(CGWork *&w)
 {
-    CGWork *w = m->cg;
     if (!w) return;
-    for (int i = 0; i < 3; ++i) {
-        if (w->chunk[i]) cudaGraphExecDestroy(w->chunk[i]);
-        if (w->chunk_blk[i]) cudaFree(w->chunk_blk[i]);
-    }
+    nir_cg_work_invalidate(w);
     void *ptrs[] = {w->x64, w->r64, w->z64, w->p64, w->Ap64, w->r32, w->z32, w->p32, w->Ap32, w->d32, w->pb16,
-                    w->Apb16, w->dinv64, w->dinv32, w->part, w->ticket, w->scal, w->dots, w->flag, w->res_blk};
+                    w->Apb16, w->dinv64, w->dinv32, w->part, w->ticket, w->scal, w->dots, w->flag};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete w;
-    m->cg = nullptr;
+    w = nullptr;
 }
+
+void nir_cg_invalidate(nir_mesh *m) { nir_cg_work_invalidate(m->cg); }
+void nir_cg_free(nir_mesh *m) { nir_cg_work_free(m->cg); }
 
 namespace {
 
-int cg_alloc(nir_mesh *m)
+int cg_alloc(CgOperator &op, CGWork *&wout)
 {
-    if (m->cg) return NIR_OK;
+    if (wout) {
+        if (wout->n == op.n() && wout->n_full == op.n_full()) return NIR_OK;
+        nir_cg_work_free(wout);
+    }
     CGWork *w = new (std::nothrow) CGWork();
     if (!w) return NIR_ERR_NO_MEMORY;
-    m->cg = w;
-    const long long n = m->ndof;
+    wout = w;
+    const long long n = op.n();
     w->n = n;
-    w->grid = m->ctx->num_sms * 4;
+    w->n_full = op.n_full();
+    w->grid = op.context()->num_sms * 4;
     const size_t d = sizeof(double) * n, f = sizeof(float) * n, h = sizeof(__nv_bfloat16) * n;
-    bool ok = cudaMalloc(&w->x64, d) == cudaSuccess && cudaMalloc(&w->r64, d) == cudaSuccess &&
-              cudaMalloc(&w->z64, d) == cudaSuccess &&
+    bool ok = cudaMalloc(&w->x64, sizeof(double) * w->n_full) == cudaSuccess &&
+              cudaMalloc(&w->r64, d) == cudaSuccess && cudaMalloc(&w->z64, d) == cudaSuccess &&
               cudaMalloc(&w->p64, d) == cudaSuccess && cudaMalloc(&w->Ap64, d) == cudaSuccess &&
               cudaMalloc(&w->r32, f) == cudaSuccess && cudaMalloc(&w->z32, f) == cudaSuccess &&
               cudaMalloc(&w->p32, f) == cudaSuccess && cudaMalloc(&w->Ap32, f) == cudaSuccess &&
@@ -350,7 +352,7 @@ int cg_alloc(nir_mesh *m)
               cudaMalloc(&w->scal, sizeof(CGScal)) == cudaSuccess &&
               cudaMalloc(&w->dots, sizeof(double) * 4) == cudaSuccess && cudaMalloc(&w->flag, sizeof(int)) == cudaSuccess;
     if (!ok) {
-        nir_cg_free(m);
+        nir_cg_work_free(wout);
         return NIR_ERR_NO_MEMORY;
     }
     cudaMemset(w->ticket, 0, sizeof(unsigned) * 4);
@@ -359,42 +361,19 @@ int cg_alloc(nir_mesh *m)
 
 int vgrid(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 16); }
 
-// Jacobi diagonal by probing with the FP32 operator.
-int cg_diagonal(nir_mesh *m, double lambda, cudaStream_t st)
+// Jacobi diagonal from the operator, inverted in FP64 and FP32.
+int cg_diagonal(CgOperator &op, CGWork *w, double lambda, cudaStream_t st)
 {
-    CGWork *w = m->cg;
     if (w->diag_ready && w->diag_lambda == lambda) return NIR_OK;
-    std::vector<ProbeBlk> hb(m->blocks.size());
-    int Mmax = 0;
-    for (size_t i = 0; i < m->blocks.size(); ++i) {
-        hb[i].off = m->off[i];
-        hb[i].nelem = m->blocks[i]->d.nelem;
-        hb[i].M = m->blocks[i]->M;
-        hb[i].pad = 0;
-        Mmax = std::max(Mmax, hb[i].M);
-    }
-    ProbeBlk *db = nullptr;
-    NIR_CUDA_TRY(cudaMalloc(&db, sizeof(ProbeBlk) * hb.size()));
-    int rc = NIR_OK;
-    if (cudaMemcpyAsync(db, hb.data(), sizeof(ProbeBlk) * hb.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
-        rc = NIR_ERR_CUDA;
     const long long n = w->n;
-    const int nb = (int)hb.size();
-    for (int mm = 0; mm < Mmax && !rc; ++mm) {
-        k_probe_fill<float><<<vgrid(n), 256, 0, st>>>(w->p32, db, nb, mm, n);
-        rc = nir_mesh_apply(m, NIR_F32, lambda, w->p32, w->Ap32, st);
-        if (!rc) k_probe_gather<float><<<vgrid(n), 256, 0, st>>>(w->dinv64, w->Ap32, db, nb, mm, n);
-    }
-    int bad = 0;
-    if (!rc) {
-        cudaMemsetAsync(w->flag, 0, sizeof(int), st);
-        k_invert<<<vgrid(n), 256, 0, st>>>(w->dinv64, w->dinv32, n, w->flag);
-        if (cudaMemcpyAsync(&bad, w->flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            rc = NIR_ERR_CUDA;
-    }
-    cudaFree(db);
+    int rc = op.diagonal(lambda, w->dinv64, st);
     if (rc) return rc;
+    int bad = 0;
+    cudaMemsetAsync(w->flag, 0, sizeof(int), st);
+    k_invert<<<vgrid(n), 256, 0, st>>>(w->dinv64, w->dinv32, n, w->flag);
+    if (cudaMemcpyAsync(&bad, w->flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return NIR_ERR_CUDA;
     if (bad) return NIR_ERR_NONFINITE;  // a non-positive diagonal: the operator is not SPD
     w->diag_ready = true;
     w->diag_lambda = lambda;
@@ -403,22 +382,24 @@ int cg_diagonal(nir_mesh *m, double lambda, cudaStream_t st)
 
 // Capture `len` CG iterations for the given inner precision into a graph.
 template <class V, class T>
-int capture_chunk(nir_mesh *m, int mode, int prec, double lambda, V *x, V *r, V *z, V *p, T *pT, T *Ap,
-                  const V *dinv)
+int capture_chunk(CgOperator &op, CGWork *w, int mode, int prec, double lambda, V *x, V *r, V *z, V *p, T *pT,
+                  T *Ap, const V *dinv)
 {
-    CGWork *w = m->cg;
-    if (w->chunk[mode] && w->chunk_lambda[mode] == lambda) return NIR_OK;
+    if (w->chunk[mode] && w->chunk_lambda[mode] == lambda && w->chunk_owner[mode] == &op) return NIR_OK;
     if (w->chunk[mode]) { cudaGraphExecDestroy(w->chunk[mode]); w->chunk[mode] = nullptr; }
-    if (w->chunk_blk[mode]) { cudaFree(w->chunk_blk[mode]); w->chunk_blk[mode] = nullptr; }
+    if (w->chunk_op[mode] && w->chunk_owner[mode]) w->chunk_owner[mode]->release(w->chunk_op[mode]);
+    w->chunk_op[mode] = nullptr;
+    w->chunk_owner[mode] = nullptr;
     const void *apply_in = pT ? (const void *)pT : (const void *)p;
-    int rc = nir_mesh_block_table(m, prec, lambda, apply_in, Ap, &w->chunk_blk[mode]);
+    int rc = op.prepare(prec, lambda, apply_in, Ap, &w->chunk_op[mode]);
     if (rc) return rc;
-    cudaStream_t cs = m->cap_stream;
+    w->chunk_owner[mode] = &op;
+    cudaStream_t cs = op.capture_stream();
     cudaGraph_t g;
     NIR_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     const long long n = w->n;
     for (int it = 0; it < w->chunk_len && !rc; ++it) {
-        rc = nir_mesh_launch_raw(m, prec, w->chunk_blk[mode], cs);
+        rc = op.launch(w->chunk_op[mode], cs);
         k_alpha<V, T><<<w->grid, kThreads, 0, cs>>>(p, Ap, n, w->part, w->ticket, w->scal);
         k_update<V, T><<<w->grid, kThreads, 0, cs>>>(x, r, z, p, Ap, dinv, n, w->part, w->ticket + 1, w->scal);
         k_pupdate<V, T><<<w->grid, kThreads, 0, cs>>>(p, dinv ? z : r, (pT == (T *)p) ? nullptr : pT, n, w->scal);
@@ -434,11 +415,11 @@ int capture_chunk(nir_mesh *m, int mode, int prec, double lambda, V *x, V *r, V 
 }
 
 // FP64 true residual r64 = b - H x; returns |r|^2 and |b|^2 on the host.
-int residual64(nir_mesh *m, double lambda, const double *b, const double *x, double *rr, double *bb, cudaStream_t st)
+int residual64(CgOperator &op, CGWork *w, double lambda, const double *b, const double *x, double *rr, double *bb,
+               cudaStream_t st)
 {
-    CGWork *w = m->cg;
     const long long n = w->n;
-    int rc = nir_mesh_apply(m, NIR_F64, lambda, x, w->Ap64, st);
+    int rc = op.apply64(lambda, x, w->Ap64, st);
     if (rc) return rc;
     k_residual<<<vgrid(n), 256, 0, st>>>(w->r64, b, w->Ap64, n);
     k_dot<double><<<w->grid, kThreads, 0, st>>>(w->r64, w->r64, n, w->part, w->ticket + 2, w->dots);
@@ -453,14 +434,13 @@ int residual64(nir_mesh *m, double lambda, const double *b, const double *x, dou
 
 // Run PCG chunks until done or max_iter; returns iterations and final rr.
 template <class V, class T>
-int run_pcg(nir_mesh *m, int mode, int prec, double lambda, V *x, V *r, V *z, V *p, T *pT, T *Ap, const V *dinv,
-            double thresh, int max_iter, int *iters, double *rr_out, int *bad_out, cudaStream_t st)
+int run_pcg(CgOperator &op, CGWork *w, int mode, int prec, double lambda, V *x, V *r, V *z, V *p, T *pT, T *Ap,
+            const V *dinv, double thresh, int max_iter, int *iters, double *rr_out, int *bad_out, cudaStream_t st)
 {
-    CGWork *w = m->cg;
     const long long n = w->n;
     k_start<V, T><<<w->grid, kThreads, 0, st>>>(r, z, p, (pT == (T *)p) ? nullptr : pT, dinv, n, w->part,
                                                 w->ticket + 3, w->scal, thresh);
-    int rc = capture_chunk<V, T>(m, mode, prec, lambda, x, r, z, p, pT, Ap, dinv);
+    int rc = capture_chunk<V, T>(op, w, mode, prec, lambda, x, r, z, p, pT, Ap, dinv);
     if (rc) return rc;
     CGScal hs;
     NIR_CUDA_TRY(cudaMemcpyAsync(&hs, w->scal, sizeof(CGScal), cudaMemcpyDeviceToHost, st));
@@ -476,29 +456,108 @@ int run_pcg(nir_mesh *m, int mode, int prec, double lambda, V *x, V *r, V *z, V 
     return NIR_OK;
 }
 
+// The mesh's broken Helmholtz operator (one persistent launch per apply).
+struct MeshLaunch {
+    int prec;
+    nirk::MeshBlk *blk;
+};
+
+struct MeshOp final : CgOperator {
+    nir_mesh *m;
+    explicit MeshOp(nir_mesh *mm) : m(mm) {}
+    nir_ctx *context() override { return m->ctx; }
+    long long n() override { return m->ndof; }
+    long long n_full() override { return m->ndof; }
+    cudaStream_t capture_stream() override { return m->cap_stream; }
+    int prepare(int prec, double lambda, const void *x, void *y, void **handle) override
+    {
+        nirk::MeshBlk *blk = nullptr;
+        int rc = nir_mesh_block_table(m, prec, lambda, x, y, &blk);
+        if (rc) return rc;
+        MeshLaunch *h = new (std::nothrow) MeshLaunch{prec, blk};
+        if (!h) {
+            cudaFree(blk);
+            return NIR_ERR_NO_MEMORY;
+        }
+        *handle = h;
+        return NIR_OK;
+    }
+    int launch(void *handle, cudaStream_t st) override
+    {
+        MeshLaunch *h = static_cast<MeshLaunch *>(handle);
+        return nir_mesh_launch_raw(m, h->prec, h->blk, st);
+    }
+    void release(void *handle) override
+    {
+        MeshLaunch *h = static_cast<MeshLaunch *>(handle);
+        if (!h) return;
+        if (h->blk) cudaFree(h->blk);
+        delete h;
+    }
+    int apply64(double lambda, const double *x, double *y, cudaStream_t st) override
+    {
+        return nir_mesh_apply(m, NIR_F64, lambda, x, y, st);
+    }
+    // Probing with the FP32 operator (block diagonal per element, same mode
+    // numbering in every element of a block).
+    int diagonal(double lambda, double *d, cudaStream_t st) override
+    {
+        std::vector<ProbeBlk> hb(m->blocks.size());
+        int Mmax = 0;
+        for (size_t i = 0; i < m->blocks.size(); ++i) {
+            hb[i].off = m->off[i];
+            hb[i].nelem = m->blocks[i]->d.nelem;
+            hb[i].M = m->blocks[i]->M;
+            hb[i].pad = 0;
+            Mmax = std::max(Mmax, hb[i].M);
+        }
+        const long long n = m->ndof;
+        ProbeBlk *db = nullptr;
+        float *x32 = nullptr, *y32 = nullptr;
+        int rc = NIR_OK;
+        if (cudaMalloc(&db, sizeof(ProbeBlk) * hb.size()) != cudaSuccess ||
+            cudaMalloc(&x32, sizeof(float) * n) != cudaSuccess || cudaMalloc(&y32, sizeof(float) * n) != cudaSuccess)
+            rc = NIR_ERR_NO_MEMORY;
+        if (!rc && cudaMemcpyAsync(db, hb.data(), sizeof(ProbeBlk) * hb.size(), cudaMemcpyHostToDevice, st) !=
+                       cudaSuccess)
+            rc = NIR_ERR_CUDA;
+        const int nb = (int)hb.size();
+        for (int mm = 0; mm < Mmax && !rc; ++mm) {
+            k_probe_fill<float><<<vgrid(n), 256, 0, st>>>(x32, db, nb, mm, n);
+            rc = nir_mesh_apply(m, NIR_F32, lambda, x32, y32, st);
+            if (!rc) k_probe_gather<float><<<vgrid(n), 256, 0, st>>>(d, y32, db, nb, mm, n);
+        }
+        if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = NIR_ERR_CUDA;
+        if (db) cudaFree(db);
+        if (x32) cudaFree(x32);
+        if (y32) cudaFree(y32);
+        return rc;
+    }
+};
+
 }  // namespace
 
-extern "C" int nir_cg_solve(nir_mesh *m, double lambda, const double *b, double *x, const nir_cg_opts *o,
-                            nir_cg_stats *stats)
+int nir_cg_run(CgOperator &op, CGWork *&wref, double lambda, const double *b, double *x, const nir_cg_opts *o,
+               nir_cg_stats *stats)
 {
-    if (!m || !b || !x || !o || (const void *)b == (const void *)x) return NIR_ERR_INVALID_ARG;
-    if (!(o->tol > 0.0) || o->max_inner < 1 || !std::isfinite(lambda) || !(lambda > 0.0)) return NIR_ERR_INVALID_ARG;
+    if (!b || !x || !o || (const void *)b == (const void *)x) return NIR_ERR_INVALID_ARG;
+    if (!(o->tol > 0.0) || o->max_inner < 1 || !std::isfinite(lambda)) return NIR_ERR_INVALID_ARG;
     if (o->inner_prec != NIR_F64 && o->inner_prec != NIR_F32 && o->inner_prec != NIR_BF16) return NIR_ERR_INVALID_ARG;
     if (o->inner_prec != NIR_F64 && (o->max_outer < 1 || !(o->inner_tol > 0.0) || !(o->inner_tol < 1.0)))
         return NIR_ERR_INVALID_ARG;
-    NIR_CUDA_TRY(cudaSetDevice(m->ctx->device));
+    NIR_CUDA_TRY(cudaSetDevice(op.context()->device));
     const auto t0 = std::chrono::steady_clock::now();
-    int rc = cg_alloc(m);
+    int rc = cg_alloc(op, wref);
     if (rc) return rc;
-    CGWork *w = m->cg;
-    cudaStream_t st = m->ctx->stream;
+    CGWork *w = wref;
+    cudaStream_t st = op.context()->stream;
     const long long n = w->n;
     if (o->jacobi) {
-        rc = cg_diagonal(m, lambda, st);
+        rc = cg_diagonal(op, w, lambda, st);
         if (rc) return rc;
     }
     double rr = 0.0, bb = 0.0;
-    rc = residual64(m, lambda, b, x, &rr, &bb, st);
+    rc = residual64(op, w, lambda, b, x, &rr, &bb, st);
     if (rc) return rc;
     if (!std::isfinite(rr) || !std::isfinite(bb)) return NIR_ERR_NONFINITE;
     nir_cg_stats s{0, 0, 0.0, 0.0};
@@ -509,18 +568,18 @@ extern "C" int nir_cg_solve(nir_mesh *m, double lambda, const double *b, double 
         // captured iteration graph holds fixed vector addresses).  The recursive
         // residual drifts from the true one, so CG restarts from b - H x until
         // the true residual meets the tolerance or the iteration cap is hit.
-        NIR_CUDA_TRY(cudaMemcpyAsync(w->x64, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        NIR_CUDA_TRY(cudaMemcpyAsync(w->x64, x, sizeof(double) * w->n_full, cudaMemcpyDeviceToDevice, st));
         for (int restart = 0; restart < 50; ++restart) {
             int iters = 0, bad = 0;
             double rr_it = 0.0;
-            rc = run_pcg<double, double>(m, 0, NIR_F64, lambda, w->x64, w->r64, w->z64, w->p64, w->p64, w->Ap64,
-                                         o->jacobi ? w->dinv64 : nullptr, o->tol * o->tol * bb,
+            rc = run_pcg<double, double>(op, w, 0, NIR_F64, lambda, w->x64, w->r64, w->z64, w->p64, w->p64,
+                                         w->Ap64, o->jacobi ? w->dinv64 : nullptr, o->tol * o->tol * bb,
                                          o->max_inner - s.inner_total, &iters, &rr_it, &bad, st);
             if (rc) return rc;
             s.inner_total += iters;
             s.outer += 1;
             const double prev = rr;
-            rc = residual64(m, lambda, b, w->x64, &rr, nullptr, st);  // also refreshes r64 for a restart
+            rc = residual64(op, w, lambda, b, w->x64, &rr, nullptr, st);  // also refreshes r64 for a restart
             if (rc) return rc;
             if (bad == 2 || !std::isfinite(rr)) { status = NIR_ERR_NONFINITE; break; }
             if (bad == 1) { status = NIR_ERR_NOT_CONVERGED; break; }
@@ -538,19 +597,20 @@ extern "C" int nir_cg_solve(nir_mesh *m, double lambda, const double *b, double 
             double rr_in = 0.0;
             const double th = o->inner_tol * o->inner_tol;
             if (mode == 1)
-                rc = run_pcg<float, float>(m, 1, NIR_F32, lambda, w->d32, w->r32, w->z32, w->p32, w->p32, w->Ap32,
-                                           o->jacobi ? w->dinv32 : nullptr, th, o->max_inner, &iters, &rr_in, &bad, st);
+                rc = run_pcg<float, float>(op, w, 1, NIR_F32, lambda, w->d32, w->r32, w->z32, w->p32, w->p32,
+                                           w->Ap32, o->jacobi ? w->dinv32 : nullptr, th, o->max_inner, &iters,
+                                           &rr_in, &bad, st);
             else
-                rc = run_pcg<float, __nv_bfloat16>(m, 2, NIR_BF16, lambda, w->d32, w->r32, w->z32, w->p32, w->pb16,
-                                                   w->Apb16, o->jacobi ? w->dinv32 : nullptr, th, o->max_inner,
-                                                   &iters, &rr_in, &bad, st);
+                rc = run_pcg<float, __nv_bfloat16>(op, w, 2, NIR_BF16, lambda, w->d32, w->r32, w->z32, w->p32,
+                                                   w->pb16, w->Apb16, o->jacobi ? w->dinv32 : nullptr, th,
+                                                   o->max_inner, &iters, &rr_in, &bad, st);
             if (rc) return rc;
             s.inner_total += iters;
             s.outer += 1;
             if (bad == 2) { status = NIR_ERR_NONFINITE; break; }
             k_correct<<<vgrid(n), 256, 0, st>>>(x, w->d32, rn, n);
             const double prev = rr;
-            rc = residual64(m, lambda, b, x, &rr, nullptr, st);
+            rc = residual64(op, w, lambda, b, x, &rr, nullptr, st);
             if (rc) return rc;
             if (!std::isfinite(rr)) { status = NIR_ERR_NONFINITE; break; }
             if (rr >= prev) { status = NIR_ERR_NOT_CONVERGED; break; }  // refinement stalled
@@ -562,4 +622,16 @@ extern "C" int nir_cg_solve(nir_mesh *m, double lambda, const double *b, double 
     s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = s;
     return status;
+}
+
+extern "C" int nir_cg_solve(nir_mesh *m, double lambda, const double *b, double *x, const nir_cg_opts *o,
+                            nir_cg_stats *stats)
+{
+    if (!m) return NIR_ERR_INVALID_ARG;
+    if (!std::isfinite(lambda) || !(lambda > 0.0)) return NIR_ERR_INVALID_ARG;
+    if (!m->cg_op) {
+        m->cg_op = new (std::nothrow) MeshOp(m);
+        if (!m->cg_op) return NIR_ERR_NO_MEMORY;
+    }
+    return nir_cg_run(*m->cg_op, m->cg, lambda, b, x, o, stats);
 }

@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "nir_cg.h"
 #include "nir_internal.h"
 #include "nir_mesh.h"
 #include "nir_solve.h"
@@ -267,6 +268,7 @@ extern "C" void nir_mesh_destroy(nir_mesh *m)
     if (m->counter) cudaFree(m->counter);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     nir_cg_free(m);
+    delete m->cg_op;
     delete m;
 }
 

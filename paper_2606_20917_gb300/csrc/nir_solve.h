@@ -32,6 +32,7 @@ struct MeshGraph {
 };
 
 struct CGWork;
+struct CgOperator;
 
 struct nir_mesh {
     nir_ctx *ctx = nullptr;
@@ -45,6 +46,7 @@ struct nir_mesh {
     std::vector<MeshGraph> graphs;
     std::vector<unsigned> geo_seen;  // blocks' geometry versions the captured graphs use
     CGWork *cg = nullptr;
+    CgOperator *cg_op = nullptr;     // the CG solver's view of this mesh
 };
 
 int nir_mesh_build_items(nir_mesh *m, int prec, int gran);

@@ -32,7 +32,8 @@ def test_header_declares_the_operator_set():
     names = declared_functions()
     for n in ("nir_bwd_trans", "nir_iproduct_wrt_base", "nir_phys_deriv", "nir_iproduct_wrt_deriv_base",
               "nir_mass", "nir_helmholtz", "nir_helmholtz_host", "nir_block_set_geometry", "nir_mesh_create",
-              "nir_mesh_helmholtz", "nir_cg_solve", "nir_tune", "nir_probe_fp64_peak", "nir_strerror"):
+              "nir_mesh_helmholtz", "nir_cg_solve", "nir_tune", "nir_probe_fp64_peak", "nir_strerror",
+              "nir_asm_create", "nir_asm_gather", "nir_asm_assemble", "nir_asm_apply", "nir_asm_cg_solve"):
         assert n in names
 
 
