@@ -191,3 +191,69 @@ def test_invalid_arguments(nir, ctx):
     with pytest.raises(nir.NirError) as e:
         nir.Assembly(ctx, [tet], [np.zeros((6, 8), np.int64)])
     assert e.value.code == -2
+
+
+def _face_trace_mismatch(P, c1, c2, verts1, verts2):
+    """Largest trace difference of two elements' expansions (coefficients c1,
+    c2) over their shared face, evaluated by the oracle at Gauss points."""
+    shared = set(verts1.tolist()) & set(verts2.tolist())
+    assert len(shared) == 4
+    s = cf._face_samples(3, P)
+    f1 = next(f for f in cf._face_list(3) if {int(verts1[v]) for v in cf._face_corners(3, *f)} == shared)
+    f2 = next(f for f in cf._face_list(3) if {int(verts2[v]) for v in cf._face_corners(3, *f)} == shared)
+    k1 = cf._face_corners(3, *f1)
+    pos2 = {int(verts2[v]): v for v in cf._face_corners(3, *f2)}
+    xi1 = cf._bilinear(s, np.stack([cf._vertex_xi(3, v) for v in k1]))
+    xi2 = cf._bilinear(s, np.stack([cf._vertex_xi(3, pos2[int(verts1[v])]) for v in k1]))
+    B1, _ = oracle.eval_basis("hex", P, xi1)
+    B2, _ = oracle.eval_basis("hex", P, xi2)
+    return np.abs(B1 @ c1 - B2 @ c2).max(), np.abs(B1 @ c1).max()
+
+
+def test_full_size_dirichlet_solve_properties(nir, ctx):
+    """48^3 curved hexes, P = 6 (the solve workload): the mixed-precision
+    solve converges, holds the Dirichlet values, matches the exact solution to
+    the discretisation error, and its traces agree across sampled shared faces
+    (oracle evaluation, element pair by element pair)."""
+    wl = W.workload("hex48_curved_p6")
+    n, P, E = 48, 6, wl["nodes"].shape[0]
+    verts = W.grid_vertices(n, 3)
+    blk = nir.Block(ctx, "hex", E, P, deformed=True)
+    blk.set_geometry(wl["gorder"], torch.from_numpy(wl["nodes"]).cuda())
+    asm = nir.Assembly(ctx, [blk], [verts])
+    assert asm.n_global == (n * P + 1) ** 3 and asm.n_free == (n * P - 1) ** 3
+    lam = 1.0
+    rng = np.random.default_rng(0)
+    ids = np.sort(rng.choice(E, 24, replace=False))
+    X = oracle.geom_factors("hex", P + 2, wl["gorder"], wl["nodes"][ids], with_x=True)[2]
+    # exact solution at all points (input generation on the device)
+    eta, xi = blk.points()
+    import bench
+    f = bench.manufactured_rhs_points(wl, xi, lam, torch.device("cuda"))
+    u = f / (3 * np.pi ** 2 + lam)
+    assert np.allclose(u[ids].cpu().numpy(), np.prod(np.sin(np.pi * X), axis=-1), atol=1e-13)
+    bu = asm.assemble(blk.iproduct_wrt_base(u).reshape(-1))
+    up = torch.zeros_like(bu)
+    rc, st = asm.cg_solve(bu, up, op="mass", fix_boundary=False, inner_prec="f32", tol=1e-10, max_outer=60)
+    assert rc == 0, st
+    b = asm.assemble(blk.iproduct_wrt_base(f).reshape(-1))
+    x = up.clone()
+    x[:asm.n_free] = 0.0
+    rc, st = asm.cg_solve(b, x, lam=lam, inner_prec="f32", tol=1e-10, max_outer=60)
+    assert rc == 0 and st["rel_residual"] <= 1e-10, st
+    assert torch.equal(x[asm.n_free:], up[asm.n_free:])
+    # the FP64 residual recomputed through the assembled FP64 operator
+    r = (b - asm.apply(x, lam=lam))[:asm.n_free]
+    assert float(r.norm() / b[:asm.n_free].norm()) <= 1.5e-10
+    ul = asm.gather(x).view(E, blk.M)
+    err = float((blk.bwd_trans(ul) - u).abs().max() / u.abs().max())
+    assert err < 1e-6, err
+    # traces across sampled interior faces (x-neighbours) agree
+    cl = ul.cpu().numpy()
+    worst = 0.0
+    for e1 in ids[:12]:
+        i = e1 % n
+        e2 = e1 + 1 if i < n - 1 else e1 - 1
+        d, s = _face_trace_mismatch(P, cl[e1], cl[e2], verts[e1], verts[e2])
+        worst = max(worst, d / max(s, 1e-300))
+    assert worst < 1e-12, worst
