@@ -35,6 +35,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -52,34 +53,88 @@ constexpr int kVT = 256;
 
 int vgrid(long long n) { return (int)std::min<long long>((n + kVT - 1) / kVT, 152LL * 16); }
 
+// Gather and assembly are bound by memory latency (an index load, then the
+// indexed load): every grid-stride step handles kU entries i0 + k * stride
+// with all their loads issued before the arithmetic.
+constexpr int kU = 4;
+
 // x_loc[i] = s_i x_g[g_i]; entries g >= n_avail read as zero (held boundary values).
-template <class TI, class TO>
+template <class TI>
 __global__ void __launch_bounds__(kVT) k_gather(const TI *__restrict__ xg, long long n_avail,
-                                                const int *__restrict__ map, long long nloc, TO *__restrict__ xl)
+                                                const int *__restrict__ map, long long nloc, TI *__restrict__ xl)
 {
-    for (long long i = blockIdx.x * (long long)kVT + threadIdx.x; i < nloc; i += (long long)gridDim.x * kVT) {
-        const int s = map[i];
-        const long long g = (long long)(s > 0 ? s : -s) - 1;
-        const double v = g < n_avail ? to_d(xg[g]) : 0.0;
-        st_v(xl + i, s > 0 ? v : -v);
+    const long long S = (long long)gridDim.x * kVT;
+    for (long long i0 = blockIdx.x * (long long)kVT + threadIdx.x; i0 < nloc; i0 += S * kU) {
+        int sv[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const long long i = i0 + k * S;
+            sv[k] = map[i < nloc ? i : i0];
+        }
+        TI v[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const long long g = (long long)(sv[k] > 0 ? sv[k] : -sv[k]) - 1;
+            v[k] = g < n_avail ? xg[g] : TI(0.0f);
+        }
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const long long i = i0 + k * S;
+            if (i < nloc) xl[i] = sv[k] > 0 ? v[k] : -v[k];  // a signed copy: exact in every type
+        }
     }
 }
 
-// y_g[g] = sum over the copies k of g: s_k y_loc[i_k]   (g < nrows); with
-// absval the signs are dropped (diagonal assembly: s_k^2 = 1).
-template <class TI, class TO>
+// Sums run in FP64 for FP64 data and in FP32 for FP32 / bfloat16 data (FP64
+// arithmetic and conversions are slow on GB300 and would bound the kernel).
+__device__ __forceinline__ double acc_of(double v) { return v; }
+__device__ __forceinline__ float acc_of(float v) { return v; }
+__device__ __forceinline__ float acc_of(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ void st_acc(double *p, double v) { *p = v; }
+__device__ __forceinline__ void st_acc(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_acc(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
+// y_g[g] = sum over the copies k of g: s_k y_loc[i_k]   (g < nrows), the copies
+// summed in their stored order; with absval the signs are dropped (diagonal
+// assembly: s_k^2 = 1).
+template <class TI, class TO, class Acc = typename std::conditional<sizeof(TI) == 8, double, float>::type>
 __global__ void __launch_bounds__(kVT) k_assemble(const TI *__restrict__ yl, const int *__restrict__ rowptr,
                                                   const int *__restrict__ pos, long long nrows, TO *__restrict__ yg,
                                                   int absval)
 {
-    for (long long g = blockIdx.x * (long long)kVT + threadIdx.x; g < nrows; g += (long long)gridDim.x * kVT) {
-        double acc = 0.0;
-        for (int k = rowptr[g]; k < rowptr[g + 1]; ++k) {
-            const int s = pos[k];
-            const double v = to_d(yl[(s > 0 ? s : -s) - 1]);
-            acc += (s > 0 || absval) ? v : -v;
+    const long long S = (long long)gridDim.x * kVT;
+    for (long long g0 = blockIdx.x * (long long)kVT + threadIdx.x; g0 < nrows; g0 += S * kU) {
+        int beg[kU], end[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const long long g = g0 + k * S;
+            beg[k] = g < nrows ? rowptr[g] : 0;
+            end[k] = g < nrows ? rowptr[g + 1] : 0;
         }
-        st_v(yg + g, acc);
+        Acc acc[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) acc[k] = Acc(0);
+        for (int c = 0;; ++c) {
+            int sv[kU];
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < kU; ++k) {
+                const int q = beg[k] + c;
+                sv[k] = q < end[k] ? pos[q] : 0;
+                any |= q < end[k];
+            }
+            if (!any) break;
+            Acc v[kU];
+#pragma unroll
+            for (int k = 0; k < kU; ++k) v[k] = sv[k] ? acc_of(yl[(sv[k] > 0 ? sv[k] : -sv[k]) - 1]) : Acc(0);
+#pragma unroll
+            for (int k = 0; k < kU; ++k) acc[k] += (sv[k] > 0 || absval) ? v[k] : -v[k];
+        }
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const long long g = g0 + k * S;
+            if (g < nrows) st_acc(yg + g, acc[k]);
+        }
     }
 }
 
@@ -210,7 +265,7 @@ int launch_apply_t(nir_asm *a, int op, int prec, double lambda, const T *x, long
                    long long nrows, cudaStream_t st)
 {
     T *xl = static_cast<T *>(a->xl[prec]), *yl = static_cast<T *>(a->yl[prec]);
-    k_gather<T, T><<<vgrid(a->nloc), kVT, 0, st>>>(x, n_avail, a->map, a->nloc, xl);
+    k_gather<T><<<vgrid(a->nloc), kVT, 0, st>>>(x, n_avail, a->map, a->nloc, xl);
     int rc = launch_blocks(a, op, prec, lambda, xl, yl, st);
     if (rc) return rc;
     k_assemble<T, T><<<vgrid(nrows), kVT, 0, st>>>(yl, a->rowptr, a->pos, nrows, y, 0);
@@ -661,13 +716,13 @@ extern "C" int nir_asm_gather(nir_asm *a, int prec, const void *x_global, void *
     if (!a || !valid_prec(prec) || !x_global || !x_local || x_global == x_local) return NIR_ERR_INVALID_ARG;
     cudaStream_t st = a->ctx->stream;
     if (prec == NIR_F64)
-        k_gather<double, double><<<vgrid(a->nloc), kVT, 0, st>>>(static_cast<const double *>(x_global), a->nglob,
+        k_gather<double><<<vgrid(a->nloc), kVT, 0, st>>>(static_cast<const double *>(x_global), a->nglob,
                                                                  a->map, a->nloc, static_cast<double *>(x_local));
     else if (prec == NIR_F32)
-        k_gather<float, float><<<vgrid(a->nloc), kVT, 0, st>>>(static_cast<const float *>(x_global), a->nglob, a->map,
+        k_gather<float><<<vgrid(a->nloc), kVT, 0, st>>>(static_cast<const float *>(x_global), a->nglob, a->map,
                                                                a->nloc, static_cast<float *>(x_local));
     else
-        k_gather<__nv_bfloat16, __nv_bfloat16><<<vgrid(a->nloc), kVT, 0, st>>>(
+        k_gather<__nv_bfloat16><<<vgrid(a->nloc), kVT, 0, st>>>(
             static_cast<const __nv_bfloat16 *>(x_global), a->nglob, a->map, a->nloc,
             static_cast<__nv_bfloat16 *>(x_local));
     if (cudaPeekAtLastError() != cudaSuccess) {
@@ -738,5 +793,9 @@ extern "C" int nir_asm_cg_solve(nir_asm *a, int op, double lambda, int fix_bound
         a->state_seen = state;
     }
     if (op == NIR_ASM_MASS) lambda = 0.0;
+    if (a->ops[op][fix_boundary]->n() == 0) {  // every dof held: nothing to solve
+        if (stats) *stats = nir_cg_stats{0, 0, 0.0, 0.0};
+        return NIR_OK;
+    }
     return nir_cg_run(*a->ops[op][fix_boundary], a->cg[op][fix_boundary], lambda, b, x, o, stats);
 }

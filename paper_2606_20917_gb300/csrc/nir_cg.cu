@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "nir_cg.h"
@@ -69,7 +70,9 @@ __device__ __forceinline__ void block_sum(double (&v)[NV])
 }
 
 // Publish this CTA's partials; returns true in thread 0 of the last CTA,
-// with the totals (summed in CTA order) in tot.
+// with the totals in tot.  The last CTA sums the partials with all its
+// threads (thread t takes CTAs t, t + blockDim, ...) and a block reduction:
+// a fixed order for a fixed grid, so results are deterministic.
 template <int NV>
 __device__ __forceinline__ bool finish_reduce(double (&v)[NV], double *part, unsigned *ticket, double (&tot)[NV])
 {
@@ -81,27 +84,87 @@ __device__ __forceinline__ bool finish_reduce(double (&v)[NV], double *part, uns
         last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return false;
+    if (!last) return false;
     __threadfence();
+    double acc[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile double *)part)[k * gridDim.x + b];
-        tot[k] = s;
+        acc[k] = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) acc[k] += __ldcg(part + k * gridDim.x + b);
     }
+    block_sum(acc);
+    if (threadIdx.x != 0) return false;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = acc[k];
     *ticket = 0u;
     return true;
 }
 
+// The vector kernels are bound by memory latency unless every thread keeps
+// several independent loads in flight: each grid-stride step handles kU
+// elements i0 + k * stride (coalesced across the warp for every k), loading
+// all operands before any arithmetic.
+//
+// Arithmetic follows the vectors' type.  FP64 vectors (plain CG) compute in
+// FP64.  FP32 vectors (the inner solver of the refinement) compute their
+// updates in FP32: GB300's FP64 rate is a small fraction of its FP32 rate and
+// conversions to and from FP64 run on the same pipe, so FP64 arithmetic per
+// element would bound these kernels.  Their dot products keep FP64-level
+// accuracy without FP64 operations per element: each thread accumulates
+// exact products (TwoProduct by FMA) with compensated summation (TwoSum) in a
+// pair of floats -- the Dot2 algorithm of Ogita, Rump and Oishi, "Accurate sum
+// and dot product", SIAM J. Sci. Comput. 26 (2005) -- and the per-thread
+// results are summed in FP64.
+constexpr int kU = 4;
+
+struct FF {
+    float hi = 0.0f, lo = 0.0f;
+};
+
+__device__ __forceinline__ void ff_add_prod(FF &s, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -p);  // a * b = p + e exactly
+    const float t = __fadd_rn(s.hi, p);
+    const float bb = __fsub_rn(t, s.hi);
+    const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bb)), __fsub_rn(p, bb));  // s.hi + p = t + err
+    s.hi = t;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ double ff_value(const FF &s) { return (double)s.hi + (double)s.lo; }
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ void st_f(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_f(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
 // pAp = p . Ap ; alpha = rz / pAp
 template <class V, class T>
-__global__ void __launch_bounds__(kThreads) k_alpha(const V *p, const T *Ap, long long n, double *part,
-                                                    unsigned *ticket, CGScal *s)
+__global__ void __launch_bounds__(kThreads) k_alpha(const V *__restrict__ p, const T *__restrict__ Ap, long long n,
+                                                    double *part, unsigned *ticket, CGScal *s)
 {
     if (s->done) return;
+    const long long S = (long long)gridDim.x * kThreads;
     double v[1] = {0.0};
-    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
-        v[0] += to_d(p[i]) * to_d(Ap[i]);
+    FF acc;
+    for (long long i0 = blockIdx.x * (long long)kThreads + threadIdx.x; i0 < n; i0 += S * kU) {
+        V pv[kU];
+        T av[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const long long i = i0 + k * S, j = i < n ? i : i0;  // in-range dummy for the tail
+            pv[k] = p[j];
+            av[k] = Ap[j];
+        }
+#pragma unroll
+        for (int k = 0; k < kU; ++k)
+            if (i0 + k * S < n) {
+                if constexpr (std::is_same<V, double>::value) v[0] += to_d(pv[k]) * to_d(av[k]);
+                else ff_add_prod(acc, pv[k], to_f(av[k]));
+            }
+    }
+    if constexpr (!std::is_same<V, double>::value) v[0] = ff_value(acc);
     block_sum(v);
     double t[1];
     if (finish_reduce(v, part, ticket, t)) {
@@ -114,25 +177,62 @@ __global__ void __launch_bounds__(kThreads) k_alpha(const V *p, const T *Ap, lon
 
 // x += alpha p; r -= alpha Ap; z = dinv r; rz' = r.z; rr = r.r; beta = rz'/rz
 template <class V, class T>
-__global__ void __launch_bounds__(kThreads) k_update(V *x, V *r, V *z, const V *p, const T *Ap, const V *dinv,
-                                                     long long n, double *part, unsigned *ticket, CGScal *s)
+__global__ void __launch_bounds__(kThreads, sizeof(V) == 8 ? 3 : 4) k_update(V *__restrict__ x, V *__restrict__ r,
+                                                     V *__restrict__ z,
+                                                     const V *__restrict__ p, const T *__restrict__ Ap,
+                                                     const V *__restrict__ dinv, long long n, double *part,
+                                                     unsigned *ticket, CGScal *s)
 {
     if (s->done) return;
     const double a = s->alpha;
+    const float af = (float)a;
+    const long long S = (long long)gridDim.x * kThreads;
     double v[2] = {0.0, 0.0};
-    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
-        st_v(x + i, to_d(x[i]) + a * to_d(p[i]));
-        const double ri = to_d(r[i]) - a * to_d(Ap[i]);
-        st_v(r + i, ri);
-        const double rv = to_d(r[i]);  // the stored (rounded) residual
-        double zi = rv;
-        if (dinv) {
-            zi = to_d(dinv[i]) * rv;
-            st_v(z + i, zi);
-            zi = to_d(z[i]);
+    FF arz, arr;
+    for (long long i0 = blockIdx.x * (long long)kThreads + threadIdx.x; i0 < n; i0 += S * kU) {
+        V xv[kU], pv[kU], rv[kU], dv[kU];
+        T av[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const long long i = i0 + k * S, j = i < n ? i : i0;  // in-range dummy for the tail
+            xv[k] = x[j];
+            pv[k] = p[j];
+            rv[k] = r[j];
+            av[k] = Ap[j];
+            if (dinv) dv[k] = dinv[j];
         }
-        v[0] += rv * zi;
-        v[1] += rv * rv;
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const long long i = i0 + k * S;
+            if (i >= n) continue;
+            if constexpr (std::is_same<V, double>::value) {
+                x[i] = xv[k] + a * pv[k];
+                const double ri = rv[k] - a * to_d(av[k]);
+                r[i] = ri;
+                double zi = ri;
+                if (dinv) {
+                    zi = dv[k] * ri;
+                    z[i] = zi;
+                }
+                v[0] += ri * zi;
+                v[1] += ri * ri;
+            } else {
+                x[i] = fmaf(af, pv[k], xv[k]);
+                const float ri = fmaf(-af, to_f(av[k]), rv[k]);
+                r[i] = ri;
+                float zi = ri;
+                if (dinv) {
+                    zi = dv[k] * ri;
+                    z[i] = zi;
+                }
+                ff_add_prod(arz, ri, zi);
+                ff_add_prod(arr, ri, ri);
+            }
+        }
+    }
+    if constexpr (!std::is_same<V, double>::value) {
+        v[0] = ff_value(arz);
+        v[1] = ff_value(arr);
     }
     block_sum(v);
     double t[2];
@@ -148,34 +248,79 @@ __global__ void __launch_bounds__(kThreads) k_update(V *x, V *r, V *z, const V *
 
 // p = z + beta p ; pT = p in the operator's storage type
 template <class V, class T>
-__global__ void __launch_bounds__(kThreads) k_pupdate(V *p, const V *z, T *pT, long long n, const CGScal *s)
+__global__ void __launch_bounds__(kThreads) k_pupdate(V *__restrict__ p, const V *__restrict__ z, T *__restrict__ pT,
+                                                      long long n, const CGScal *s)
 {
     if (s->done) return;
     const double b = s->beta;
-    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
-        const double pi = to_d(z[i]) + b * to_d(p[i]);
-        st_v(p + i, pi);
-        if (pT) st_v(pT + i, to_d(p[i]));
+    const float bf = (float)b;
+    const long long S = (long long)gridDim.x * kThreads;
+    for (long long i0 = blockIdx.x * (long long)kThreads + threadIdx.x; i0 < n; i0 += S * kU) {
+        V zv[kU], pv[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const long long i = i0 + k * S, j = i < n ? i : i0;
+            zv[k] = z[j];
+            pv[k] = p[j];
+        }
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const long long i = i0 + k * S;
+            if (i >= n) continue;
+            if constexpr (std::is_same<V, double>::value) {
+                const double pi = zv[k] + b * pv[k];
+                p[i] = pi;
+                if (pT) st_v(pT + i, pi);
+            } else {
+                const float pi = fmaf(bf, pv[k], zv[k]);
+                p[i] = pi;
+                if (pT) st_f(pT + i, pi);
+            }
+        }
     }
 }
 
 // start of a CG run: r given; z = dinv r; p = z; rz, rr
 template <class V, class T>
-__global__ void __launch_bounds__(kThreads) k_start(const V *r, V *z, V *p, T *pT, const V *dinv, long long n,
+__global__ void __launch_bounds__(kThreads) k_start(const V *__restrict__ r, V *__restrict__ z, V *__restrict__ p,
+                                                    T *__restrict__ pT, const V *__restrict__ dinv, long long n,
                                                     double *part, unsigned *ticket, CGScal *s, double thresh)
 {
+    const long long S = (long long)gridDim.x * kThreads;
     double v[2] = {0.0, 0.0};
-    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
-        const double rv = to_d(r[i]);
-        double zi = rv;
-        if (dinv) {
-            st_v(z + i, to_d(dinv[i]) * rv);
-            zi = to_d(z[i]);
+    FF arz, arr;
+    for (long long i0 = blockIdx.x * (long long)kThreads + threadIdx.x; i0 < n; i0 += S * kU) {
+        V rv[kU], dv[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const long long i = i0 + k * S, j = i < n ? i : i0;
+            rv[k] = r[j];
+            if (dinv) dv[k] = dinv[j];
         }
-        st_v(p + i, zi);
-        if (pT) st_v(pT + i, to_d(p[i]));
-        v[0] += rv * zi;
-        v[1] += rv * rv;
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const long long i = i0 + k * S;
+            if (i >= n) continue;
+            V zi = rv[k];
+            if (dinv) {
+                zi = dv[k] * rv[k];
+                z[i] = zi;
+            }
+            p[i] = zi;
+            if constexpr (std::is_same<V, double>::value) {
+                if (pT) st_v(pT + i, zi);
+                v[0] += rv[k] * zi;
+                v[1] += rv[k] * rv[k];
+            } else {
+                if (pT) st_f(pT + i, zi);
+                ff_add_prod(arz, rv[k], zi);
+                ff_add_prod(arr, rv[k], rv[k]);
+            }
+        }
+    }
+    if constexpr (!std::is_same<V, double>::value) {
+        v[0] = ff_value(arz);
+        v[1] = ff_value(arr);
     }
     block_sum(v);
     double t[2];
@@ -191,12 +336,23 @@ __global__ void __launch_bounds__(kThreads) k_start(const V *r, V *z, V *p, T *p
 
 // out[0] = a . b (FP64)
 template <class V>
-__global__ void __launch_bounds__(kThreads) k_dot(const V *a, const V *b, long long n, double *part, unsigned *ticket,
-                                                  double *out)
+__global__ void __launch_bounds__(kThreads) k_dot(const V *__restrict__ a, const V *__restrict__ b, long long n,
+                                                  double *part, unsigned *ticket, double *out)
 {
+    const long long S = (long long)gridDim.x * kThreads;
     double v[1] = {0.0};
-    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
-        v[0] += to_d(a[i]) * to_d(b[i]);
+    for (long long i0 = blockIdx.x * (long long)kThreads + threadIdx.x; i0 < n; i0 += S * kU) {
+        V av[kU], bv[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const long long i = i0 + k * S, j = i < n ? i : i0;
+            av[k] = a[j];
+            bv[k] = b[j];
+        }
+#pragma unroll
+        for (int k = 0; k < kU; ++k)
+            if (i0 + k * S < n) v[0] += to_d(av[k]) * to_d(bv[k]);
+    }
     block_sum(v);
     double t[1];
     if (finish_reduce(v, part, ticket, t)) *out = t[0];
@@ -337,7 +493,7 @@ int cg_alloc(CgOperator &op, CGWork *&wout)
     const long long n = op.n();
     w->n = n;
     w->n_full = op.n_full();
-    w->grid = op.context()->num_sms * 4;
+    w->grid = op.context()->num_sms * 8;   // 8 CTAs of 256 threads fill an SM
     const size_t d = sizeof(double) * n, f = sizeof(float) * n, h = sizeof(__nv_bfloat16) * n;
     bool ok = cudaMalloc(&w->x64, sizeof(double) * w->n_full) == cudaSuccess &&
               cudaMalloc(&w->r64, d) == cudaSuccess && cudaMalloc(&w->z64, d) == cudaSuccess &&
