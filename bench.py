@@ -449,7 +449,7 @@ def run_solve(args, ws, rank, local):
                       max_inner=args.max_inner, inner_tol=args.inner_tol)
         torch.cuda.synchronize()
         barrier(ws)
-        with ClockSampler(local) as clk:
+        with ClockSampler(local) as clk, ProfileRegion(args.profile_region):
             t0 = time.perf_counter()
             rc, st = mesh.cg_solve(b, x, lam=lam, inner_prec=inner, tol=args.tol, max_outer=60,
                                    max_inner=args.max_inner, inner_tol=args.inner_tol)
@@ -499,6 +499,25 @@ def manufactured_rhs_points(wl, xi, lam, dev):
     return ((3 * np.pi ** 2 + lam) * s[..., 0] * s[..., 1] * s[..., 2]).contiguous()
 
 
+class ProfileRegion:
+    """cudaProfilerStart/Stop around a timed region when --profile-region is set."""
+
+    def __init__(self, on: bool):
+        self.on = on
+
+    def __enter__(self):
+        if self.on:
+            import torch
+            torch.cuda.cudart().cudaProfilerStart()
+        return self
+
+    def __exit__(self, *a):
+        if self.on:
+            import torch
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStop()
+
+
 def run_gsolve(args, ws, rank, local):
     """Global C0 Helmholtz solve with Dirichlet data on the P = 6 curved-hex
     workload: the elements are assembled into the continuous space, the
@@ -546,7 +565,7 @@ def run_gsolve(args, ws, rank, local):
         del xw
         torch.cuda.synchronize()
         barrier(ws)
-        with ClockSampler(local) as clk:
+        with ClockSampler(local) as clk, ProfileRegion(args.profile_region):
             t0 = time.perf_counter()
             rc, st = asm.cg_solve(b, x, lam=lam, inner_prec=inner, tol=args.tol, max_outer=60,
                                   max_inner=args.max_inner, inner_tol=args.inner_tol)
@@ -646,6 +665,8 @@ def main():
     ap.add_argument("--max-inner", type=int, default=20000)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner set-up")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file (read if present, else written)")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="bracket the timed region with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

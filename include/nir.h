@@ -182,7 +182,9 @@ int nir_mesh_create(nir_ctx *ctx, nir_block *const *blocks, int nblocks, nir_mes
 void nir_mesh_destroy(nir_mesh *mesh);
 int nir_mesh_num_dofs(const nir_mesh *mesh, int64_t *ndof);
 /* Helmholtz apply over all blocks in one persistent kernel launch, replayed
- * from a CUDA graph captured on first use for each (prec, buffers) pair. */
+ * from a CUDA graph captured on first use for each (prec, buffers) pair.  A
+ * mesh of a single block launches that block's own (tuned) kernel instead: a
+ * work queue has nothing to balance there. */
 int nir_mesh_helmholtz(nir_mesh *mesh, int prec, double lambda, const void *in, void *out);
 /* Autotune elements-per-CTA and grid size of every (shape, P, prec) of the mesh
  * by timing candidates; reads/writes a JSON cache when cache_path != NULL. */

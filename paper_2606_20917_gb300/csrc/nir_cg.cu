@@ -612,10 +612,14 @@ int run_pcg(CgOperator &op, CGWork *w, int mode, int prec, double lambda, V *x, 
     return NIR_OK;
 }
 
-// The mesh's broken Helmholtz operator (one persistent launch per apply).
+// The mesh's broken Helmholtz operator: one persistent launch per apply, or
+// for a mesh of one block that block's own kernel.
 struct MeshLaunch {
     int prec;
-    nirk::MeshBlk *blk;
+    nirk::MeshBlk *blk;   // device block table (persistent launch), or null
+    double lambda;
+    const void *x;
+    void *y;
 };
 
 struct MeshOp final : CgOperator {
@@ -628,9 +632,15 @@ struct MeshOp final : CgOperator {
     int prepare(int prec, double lambda, const void *x, void *y, void **handle) override
     {
         nirk::MeshBlk *blk = nullptr;
-        int rc = nir_mesh_block_table(m, prec, lambda, x, y, &blk);
-        if (rc) return rc;
-        MeshLaunch *h = new (std::nothrow) MeshLaunch{prec, blk};
+        if (m->blocks.size() == 1) {
+            // one uncaptured launch sets up what is created lazily (factors, attributes)
+            int rc = nir_mesh_apply(m, prec, lambda, x, y, m->ctx->stream);
+            if (rc) return rc;
+        } else {
+            int rc = nir_mesh_block_table(m, prec, lambda, x, y, &blk);
+            if (rc) return rc;
+        }
+        MeshLaunch *h = new (std::nothrow) MeshLaunch{prec, blk, lambda, x, y};
         if (!h) {
             cudaFree(blk);
             return NIR_ERR_NO_MEMORY;
@@ -641,6 +651,7 @@ struct MeshOp final : CgOperator {
     int launch(void *handle, cudaStream_t st) override
     {
         MeshLaunch *h = static_cast<MeshLaunch *>(handle);
+        if (!h->blk) return nir_mesh_apply(m, h->prec, h->lambda, h->x, h->y, st);
         return nir_mesh_launch_raw(m, h->prec, h->blk, st);
     }
     void release(void *handle) override
@@ -789,5 +800,7 @@ extern "C" int nir_cg_solve(nir_mesh *m, double lambda, const double *b, double 
         m->cg_op = new (std::nothrow) MeshOp(m);
         if (!m->cg_op) return NIR_ERR_NO_MEMORY;
     }
+    int rc = nir_mesh_sync_geometry(m);  // before the preconditioner and graphs are reused
+    if (rc) return rc;
     return nir_cg_run(*m->cg_op, m->cg, lambda, b, x, o, stats);
 }

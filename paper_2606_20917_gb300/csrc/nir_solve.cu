@@ -117,7 +117,7 @@ int nir_mesh_launch_raw(nir_mesh *m, int prec, const nirk::MeshBlk *dblk, cudaSt
     return NIR_OK;
 }
 
-int nir_mesh_prepare(nir_mesh *m, int prec)
+int nir_mesh_sync_geometry(nir_mesh *m)
 {
     // a block whose geometry was set again has new factor arrays: every
     // captured graph and block table of the mesh is out of date
@@ -131,6 +131,13 @@ int nir_mesh_prepare(nir_mesh *m, int prec)
         for (size_t i = 0; i < m->blocks.size(); ++i)
             if (!m->blocks[i]->geo_set) return NIR_ERR_STATE;
     }
+    return NIR_OK;
+}
+
+int nir_mesh_prepare(nir_mesh *m, int prec)
+{
+    int rc = nir_mesh_sync_geometry(m);
+    if (rc) return rc;
     if (m->ps[prec].ready) return NIR_OK;
     return nir_mesh_build_items(m, prec, m->ps[prec].gran > 0 ? m->ps[prec].gran : 1);
 }
@@ -170,6 +177,12 @@ int nir_mesh_block_table(nir_mesh *m, int prec, double lambda, const void *in, v
 // Apply through a cached CUDA graph (captured on first use per key).
 int nir_mesh_apply(nir_mesh *m, int prec, double lambda, const void *in, void *out, cudaStream_t st)
 {
+    if (m->blocks.size() == 1) {  // one block: its own tuned kernel (a work queue has nothing to balance)
+        int rc = nir_mesh_sync_geometry(m);
+        if (rc) return rc;
+        return nir_launch_op(m->blocks[0], prec, nirk::OP_HELM, lambda, in, nullptr, nullptr, out, nullptr, nullptr,
+                             st, 0);
+    }
     {
         int rc = nir_mesh_prepare(m, prec);
         if (rc) return rc;

@@ -50,6 +50,8 @@ struct nir_mesh {
 };
 
 int nir_mesh_build_items(nir_mesh *m, int prec, int gran);
+// Drop the mesh's captured graphs and CG state when a block's geometry changed.
+int nir_mesh_sync_geometry(nir_mesh *m);
 int nir_mesh_prepare(nir_mesh *m, int prec);
 int nir_mesh_launch_raw(nir_mesh *m, int prec, const nirk::MeshBlk *dblk, cudaStream_t st);
 int nir_mesh_block_table(nir_mesh *m, int prec, double lambda, const void *in, void *out, nirk::MeshBlk **dout);
