@@ -36,11 +36,26 @@ L2_BYTES = 129 * 2 ** 20
 
 
 def helm_flops_per_elem(shape: str, N: int, Q: int) -> int:
-    """Algorithmic flops of one sum-factorised Helmholtz apply (hex: 3 contraction
-    stages each way, collocation gradient and its transpose, metric)."""
+    """Algorithmic flops of one sum-factorised Helmholtz apply: the BwdTrans
+    contraction stages and their transposes (2 flops per multiply-add, each
+    stage's count = outputs x summed modes), the collocation gradient and its
+    transpose (2 Q^(d+1) flops per direction each way) and the per-point
+    metric (20 flops in 3-D, 10 in 2-D).  Collapsed shapes contract their
+    ragged mode ranges in the order of Eq. bwdsumfactet: tet M Q + N(N+1)/2 Q^2
+    + N Q^3, prism M Q + N^2 Q^2 + N Q^3, triangle M Q + N Q^2."""
     if shape == "hex":
-        return 4 * N * (N * N * Q + N * Q * Q + Q ** 3) + 12 * Q ** 4 + 20 * Q ** 3
-    raise ValueError("roofline accounting implemented for the hexahedral workloads")
+        stages = N * N * N * Q + N * N * Q * Q + N * Q ** 3
+    elif shape == "tet":
+        stages = (N * (N + 1) * (N + 2) // 6) * Q + (N * (N + 1) // 2) * Q * Q + N * Q ** 3
+    elif shape == "prism":
+        stages = (N * N * (N + 1) // 2) * Q + N * N * Q * Q + N * Q ** 3
+    elif shape == "quad":
+        return 4 * (N * N * Q + N * Q * Q) + 8 * Q ** 3 + 10 * Q ** 2
+    elif shape == "tri":
+        return 4 * ((N * (N + 1) // 2) * Q + N * Q * Q) + 8 * Q ** 3 + 10 * Q ** 2
+    else:
+        raise ValueError(shape)
+    return 4 * stages + 12 * Q ** 4 + 20 * Q ** 3
 
 
 def op_work_per_elem(op: str, N: int, Q: int, wb: int, deformed: bool):
@@ -67,10 +82,20 @@ def op_work_per_elem(op: str, N: int, Q: int, wb: int, deformed: bool):
     raise KeyError(op)
 
 
+def num_modes(shape: str, N: int) -> int:
+    return {"quad": N * N, "tri": N * (N + 1) // 2, "hex": N ** 3, "prism": N * N * (N + 1) // 2,
+            "tet": N * (N + 1) * (N + 2) // 6}[shape]
+
+
 def helm_bytes_per_elem(shape: str, N: int, Q: int, wb: int, deformed: bool) -> int:
-    M = N ** 3
-    geo = 7 * Q ** 3 if deformed else 7
-    return 2 * M * wb + geo * wb
+    """Coefficients in and out, plus the metric: per point (deformed quad/hex and
+    every collapsed shape, whose factors vary across the element) or once per
+    element (undeformed quad/hex)."""
+    d = 2 if shape in ("quad", "tri") else 3
+    ng = 4 if d == 2 else 7
+    per_point = deformed or shape in ("tri", "tet", "prism")
+    geo = ng * Q ** d if per_point else ng
+    return 2 * num_modes(shape, N) * wb + geo * wb
 
 
 KERNEL_SOURCES = ("paper_2606_20917_gb300/csrc/nir_kernels.cuh", "paper_2606_20917_gb300/csrc/nir_inst.cu",
@@ -273,7 +298,7 @@ def run_nir(args, ws, rank, local):
     u = torch.from_numpy(W.coefficients(E, M, seed=0)).to(dev, dt_t)
     y = torch.empty_like(u)
     wb = u.element_size()
-    work_bytes = E * M * wb * 2 + (E * Q ** 3 * 7 * wb if wl["deformed"] else 0)
+    work_bytes = E * helm_bytes_per_elem(shape, P + 1, Q, wb, wl["deformed"])
 
     for _ in range(args.warmup):
         blk.helmholtz(u, lam=1.0, prec=args.prec, out=y)
@@ -316,25 +341,23 @@ def run_nir(args, ws, rank, local):
         return
     peaks = measured_peaks()
     avg_launch_s = statistics.mean(per_launch) * 1e-3
-    roof = None
-    if shape == "hex":
-        flops = helm_flops_per_elem(shape, P + 1, Q) * E
-        if args.prec == "f64":
-            fp64 = ctx.probe_fp64_peak()
-            roof = {"bound": "alu", "achieved": flops / avg_launch_s / 1e12, "peak": fp64, "unit": "TFLOP/s",
-                    "frac": flops / avg_launch_s / 1e12 / fp64,
-                    "traffic": profiled_traffic(f"helm_{args.workload}_{args.prec}"),
-                    "peak_source": "FP64 FMA throughput measured in this run by nir_probe_fp64_peak "
-                                   "(register-resident DFMA chains); nominal GB300 FP64 is 1.25 TFLOP/s",
-                    "flops_per_elem": flops // E,
-                    "hbm_gbs_at_this_rate": work_bytes / avg_launch_s / 1e9}
-        else:
-            gbs = work_bytes / avg_launch_s / 1e9
-            peak = peaks.get("hbm_gbs", 6800.0)
-            roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                    "traffic": profiled_traffic(f"helm_{args.workload}_{args.prec}"),
-                    "bytes_per_elem": work_bytes // E,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "_fallback" not in peaks else "fallback 6.8 TB/s"}
+    flops = helm_flops_per_elem(shape, P + 1, Q) * E
+    if args.prec == "f64":
+        fp64 = ctx.probe_fp64_peak()
+        roof = {"bound": "alu", "achieved": flops / avg_launch_s / 1e12, "peak": fp64, "unit": "TFLOP/s",
+                "frac": flops / avg_launch_s / 1e12 / fp64,
+                "traffic": profiled_traffic(f"helm_{args.workload}_{args.prec}"),
+                "peak_source": "FP64 FMA throughput measured in this run by nir_probe_fp64_peak "
+                               "(register-resident DFMA chains); nominal GB300 FP64 is 1.25 TFLOP/s",
+                "flops_per_elem": flops // E,
+                "hbm_gbs_at_this_rate": work_bytes / avg_launch_s / 1e9}
+    else:
+        gbs = work_bytes / avg_launch_s / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                "traffic": profiled_traffic(f"helm_{args.workload}_{args.prec}"),
+                "bytes_per_elem": work_bytes // E,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "_fallback" not in peaks else "fallback 6.8 TB/s"}
     operators = {}
     if shape == "hex" and ws == 1 and not args.no_operators:
         operators = operator_table(blk, args.prec, dev, stream, wl, ctx if args.prec == "f64" else None, peaks,
@@ -618,6 +641,8 @@ def run_hybrid(args, ws, rank, local):
         mesh.tune(args.tune_cache)  # set-up, untimed
     res = {}
     nel = sum(b.nelem for b in blocks)
+    peaks = measured_peaks()
+    fp64_peak = ctx.probe_fp64_peak()
     for prec in ("f64", "f32"):
         x = torch.from_numpy(W.coefficients(1, mesh.ndof, seed=0)[0]).to(dev, nir.DTYPE[prec])
         y = torch.empty_like(x)
@@ -633,16 +658,48 @@ def run_hybrid(args, ws, rank, local):
             bev.record(stream)
             torch.cuda.synchronize()
         ms = max_over_ranks(ws, a.elapsed_time(bev) / args.steps, dev)
-        res[prec] = {"gdofs": ws * mesh.ndof / (ms * 1e-3) / 1e9, "ms_per_apply": ms, "clocks": clk.summary()}
+        res[prec] = {"gdofs": ws * mesh.ndof / (ms * 1e-3) / 1e9, "ms_per_apply": ms, "clocks": clk.summary(),
+                     "launch": mesh.get_launch(prec)}
+        # the other launch form, for comparison (the tuner picked the one above)
+        chosen = mesh.get_launch(prec)
+        other = "blocks" if chosen == "persistent" else "persistent"
+        mesh.set_launch(prec, other)
+        for _ in range(args.warmup):
+            mesh.helmholtz(x, prec=prec, out=y)
+        a.record(stream)
+        for _ in range(args.steps):
+            mesh.helmholtz(x, prec=prec, out=y)
+        bev.record(stream)
+        torch.cuda.synchronize()
+        res[prec]["ms_per_apply_" + other] = a.elapsed_time(bev) / args.steps
+        mesh.set_launch(prec, chosen)
+        wb = {"f64": 8, "f32": 4}[prec]
+        flops = sum(p["nodes"].shape[0] * helm_flops_per_elem(p["shape"], p["P"] + 1, p["Q"]) for p in parts)
+        nbytes = sum(p["nodes"].shape[0] * helm_bytes_per_elem(p["shape"], p["P"] + 1, p["Q"], wb, p["deformed"])
+                     for p in parts)
+        t = ms * 1e-3
+        if prec == "f64":
+            ach = flops / t / 1e12
+            res[prec]["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                                     "frac": ach / fp64_peak, "flops_per_apply": flops,
+                                     "peak_source": "FP64 FMA throughput measured in this run"}
+        else:
+            ach = nbytes / t / 1e9
+            res[prec]["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                     "frac": ach / peaks["hbm_gbs"], "bytes_per_apply": nbytes,
+                                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
     if rank != 0:
         return
-    line = {"metric": "Helmholtz apply GDOF/s (hybrid mesh, one persistent launch)", "value": res["f64"]["gdofs"],
+    line = {"metric": "Helmholtz apply GDOF/s (hybrid mesh, one graph launch)", "value": res["f64"]["gdofs"],
             "unit": "GDOF/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["f64"]["ms_per_apply"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "hybrid mesh: 50000 curved hex + 25000 prism + 75000 tet, P ~ U{2..8}, Q = P+2",
+                       "launch": "one CUDA graph per apply: the persistent queue or the block kernels in "
+                                 "sequence, whichever the tuner measured faster (per precision)",
                        "nelem": nel, "ndof": mesh.ndof, "blocks": len(blocks), "tuned": not args.no_tune},
-            "precisions": res, "gpu_launches": args.steps}
+            "precisions": res,
+            "gpu_launches": args.steps * (1 if res["f64"]["launch"] == "persistent" else len(blocks))}
     print(json.dumps(line), flush=True)
 
 

@@ -187,8 +187,19 @@ int nir_mesh_num_dofs(const nir_mesh *mesh, int64_t *ndof);
  * work queue has nothing to balance there. */
 int nir_mesh_helmholtz(nir_mesh *mesh, int prec, double lambda, const void *in, void *out);
 /* Autotune elements-per-CTA and grid size of every (shape, P, prec) of the mesh
- * by timing candidates; reads/writes a JSON cache when cache_path != NULL. */
+ * by timing candidates, and per precision the launch form (below); reads/writes
+ * a JSON cache when cache_path != NULL. */
 int nir_tune(nir_mesh *mesh, const char *cache_path);
+
+/* Launch form of a mesh apply: NIR_MESH_PERSISTENT = one persistent kernel
+ * pulling (block, element-group) items from a queue (the default for meshes of
+ * several blocks); NIR_MESH_BLOCKS = each block's own tuned kernel, launched in
+ * sequence.  Either form is captured in one CUDA graph per (prec, buffers,
+ * lambda) and replayed.  nir_tune picks the faster per precision; set/get
+ * override and report it (a mesh of one block always reports BLOCKS). */
+enum { NIR_MESH_PERSISTENT = 0, NIR_MESH_BLOCKS = 1 };
+int nir_mesh_set_launch(nir_mesh *mesh, int prec, int mode);
+int nir_mesh_get_launch(const nir_mesh *mesh, int prec, int *mode);
 
 typedef struct {
     int inner_prec;        /* nir_prec of the operator inside CG (F64: plain CG) */

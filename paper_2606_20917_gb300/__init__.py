@@ -67,6 +67,8 @@ _SIGS = {
     "nir_mesh_num_dofs": [_vp, C.POINTER(_i64)],
     "nir_mesh_helmholtz": [_vp, _i, _d, _vp, _vp],
     "nir_tune": [_vp, C.c_char_p],
+    "nir_mesh_set_launch": [_vp, _i, _i],
+    "nir_mesh_get_launch": [_vp, _i, C.POINTER(_i)],
     "nir_cg_solve": [_vp, _d, _vp, _vp, C.POINTER(CGOpts), C.POINTER(CGStats)],
     "nir_probe_fp64_peak": [_vp, C.POINTER(_d)],
     "nir_asm_create": [_vp, C.POINTER(_vp), C.POINTER(_vp), _i, C.POINTER(_vp)],
@@ -299,6 +301,17 @@ class Mesh:
 
     def tune(self, cache_path: str | None = None):
         _chk(_lib.nir_tune(self.h, None if cache_path is None else cache_path.encode()), "nir_tune")
+
+    LAUNCH = {"persistent": 0, "blocks": 1}
+
+    def set_launch(self, prec: str, form: str):
+        """Force the launch form of applies in one precision ("persistent" or "blocks")."""
+        _chk(_lib.nir_mesh_set_launch(self.h, PREC[prec], self.LAUNCH[form]), "nir_mesh_set_launch")
+
+    def get_launch(self, prec: str) -> str:
+        v = _i()
+        _chk(_lib.nir_mesh_get_launch(self.h, PREC[prec], C.byref(v)), "nir_mesh_get_launch")
+        return {0: "persistent", 1: "blocks"}[v.value]
 
     def cg_solve(self, b, x, lam=1.0, inner_prec="f32", tol=1e-10, max_outer=50, max_inner=2000,
                  inner_tol=1e-4, jacobi=True):

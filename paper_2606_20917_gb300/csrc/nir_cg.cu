@@ -632,7 +632,7 @@ struct MeshOp final : CgOperator {
     int prepare(int prec, double lambda, const void *x, void *y, void **handle) override
     {
         nirk::MeshBlk *blk = nullptr;
-        if (m->blocks.size() == 1) {
+        if (m->blocks.size() == 1 || m->ps[prec].mode == 1) {
             // one uncaptured launch sets up what is created lazily (factors, attributes)
             int rc = nir_mesh_apply(m, prec, lambda, x, y, m->ctx->stream);
             if (rc) return rc;
@@ -651,7 +651,7 @@ struct MeshOp final : CgOperator {
     int launch(void *handle, cudaStream_t st) override
     {
         MeshLaunch *h = static_cast<MeshLaunch *>(handle);
-        if (!h->blk) return nir_mesh_apply(m, h->prec, h->lambda, h->x, h->y, st);
+        if (!h->blk) return nir_mesh_launch_blocks(m, h->prec, h->lambda, h->x, h->y, st);
         return nir_mesh_launch_raw(m, h->prec, h->blk, st);
     }
     void release(void *handle) override

@@ -37,7 +37,57 @@ constexpr int kShapes[2] = {QUAD, TRI};
 #endif
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(int);
 
-template <int SH, int N>
+// FP32/BF16 kernels take the contractions' table values as constant-bank
+// operands, as the single-block kernels do with their table parameter: the
+// tables of every (shape, P) variant of this kernel live in one __constant__
+// array at compile-time offsets (tables depend on shape and P only, so all
+// blocks of a variant share them).  The reference weights, read only by the
+// per-element-factor path and the gathers, are left out (they stay in the
+// shared-memory copy), which keeps all 3-D variants within 31 KB.
+template <int VID>
+NIR_HD constexpr int ctab_size()
+{
+    constexpr int SH = kShapes[VID / 8], N = VID % 8 + 2, Q = N + 1;
+    return layout(SH, N, Q).total - npts(SH, Q);
+}
+
+template <int VID>
+NIR_HD constexpr int ctab_base()
+{
+    if constexpr (VID == 0) return 0;
+    else return ctab_base<VID - 1>() + ctab_size<VID - 1>();
+}
+
+constexpr int kCTabN = ctab_base<kNumShapes * 8 - 1>() + ctab_size<kNumShapes * 8 - 1>();
+
+#if NIR_PREC != 0
+__constant__ float c_tab[kCTabN];
+
+// VB: the variant's base; WQ, GAP: where the omitted weights started and how many
+template <int VB, int WQ, int GAP>
+struct CTab {
+    int base;
+    __device__ __forceinline__ CTab operator+(int o) const { return CTab{base + o}; }
+    __device__ __forceinline__ float operator()(int, int i) const
+    {
+        const int k = base + i;
+        return c_tab[VB + (k < WQ ? k : k - GAP)];
+    }
+};
+#endif
+
+// Constant-bank table operands let the compiler keep more values live: the
+// high-order variants would need up to 128 registers, and one persistent
+// kernel has a single register budget for all variants.  Variants whose
+// constant-table form fits in 64 registers use it; the others read their
+// tables from shared memory (the kernel is capped at 64 registers, two
+// 512-thread CTAs per SM).
+NIR_HD constexpr bool use_ctab(int SH, int N)
+{
+    return SH == HEX ? N <= 4 : SH == PRISM ? N <= 5 : SH == TET ? N <= 3 : true;
+}
+
+template <int SH, int N, int VID>
 __device__ __noinline__ void run_item(const MeshBlk &mb, const MeshItem &m, unsigned char *smem, int &cur)
 {
     using C = Config<SH, N, N + 1, TT, OP_HELM, 0>;
@@ -54,7 +104,17 @@ __device__ __noinline__ void run_item(const MeshBlk &mb, const MeshItem &m, unsi
         const long long e0 = (long long)g * C::EPB;
         const long long left = mb.a.nelem - e0;
         const int ne = (int)(left < C::EPB ? left : C::EPB);
+#if NIR_PREC != 0
+        if constexpr (use_ctab(SH, N)) {
+            constexpr TabLayout L = layout(SH, N, N + 1);
+            using CT = CTab<ctab_base<VID>(), L.wq, npts(SH, N + 1)>;
+            run_group<SH, N, N + 1, TT, OP_HELM, 0>(mb.a, CT{0}, tab, buf, e0, ne);
+        } else {
+            run_group<SH, N, N + 1, TT, OP_HELM, 0>(mb.a, STab<A>{tab}, tab, buf, e0, ne);
+        }
+#else
         run_group<SH, N, N + 1, TT, OP_HELM, 0>(mb.a, STab<A>{tab}, tab, buf, e0, ne);
+#endif
     }
 }
 
@@ -64,7 +124,7 @@ __device__ __forceinline__ void dispatch_one(int vid, const MeshBlk &mb, const M
 {
     if constexpr (VID < kNumShapes * 8) {
         if (vid == VID) {
-            run_item<kShapes[VID / 8], VID % 8 + 2>(mb, m, smem, cur);
+            run_item<kShapes[VID / 8], VID % 8 + 2, VID>(mb, m, smem, cur);
             return;
         }
         dispatch_one<VID + 1>(vid, mb, m, smem, cur);
@@ -73,7 +133,7 @@ __device__ __forceinline__ void dispatch_one(int vid, const MeshBlk &mb, const M
 
 constexpr int kMeshNT = Config<HEX, 5, 6, TT, OP_HELM, 0>::NT;  // the same for every variant
 
-__global__ void __launch_bounds__(kMeshNT) k_mesh(const MeshBlk *__restrict__ blks, const MeshItem *__restrict__ items,
+__global__ void __launch_bounds__(kMeshNT, 2) k_mesh(const MeshBlk *__restrict__ blks, const MeshItem *__restrict__ items,
                                               int nitems, int *counter)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -114,8 +174,52 @@ int epb_of(int vid)
 }  // namespace
 }  // namespace nirk
 
+namespace nirk {
+namespace {
+template <int VID>
+void ctab_range(int vid, int &base, int &wq, int &gap, int &total)
+{
+    if constexpr (VID < kNumShapes * 8) {
+        if (vid == VID) {
+            constexpr int SH = kShapes[VID / 8], N = VID % 8 + 2, Q = N + 1;
+            base = ctab_base<VID>();
+            wq = layout(SH, N, Q).wq;
+            gap = npts(SH, Q);
+            total = layout(SH, N, Q).total;
+            return;
+        }
+        ctab_range<VID + 1>(vid, base, wq, gap, total);
+    }
+}
+}  // namespace
+}  // namespace nirk
+
 #define NIR_MCAT2(a, b) nir_mesh_kinfo_d##a##_p##b
 #define NIR_MCAT(a, b) NIR_MCAT2(a, b)
+#define NIR_TCAT2(a, b) nir_mesh_tables_d##a##_p##b
+#define NIR_TCAT(a, b) NIR_TCAT2(a, b)
+
+// Copy variant vid's FP32 table blob (the full layout, n values) into the
+// kernel's constant tables, without the reference weights.  FP64 kernels keep
+// their tables in shared memory: nothing to do.
+int NIR_TCAT(NIR_MESH_DIM, NIR_PREC)(int vid, const float *blob, int n, cudaStream_t st)
+{
+#if NIR_PREC != 0
+    using namespace nirk;
+    int base = -1, wq = 0, gap = 0, total = 0;
+    ctab_range<0>(vid, base, wq, gap, total);
+    if (base < 0 || n != total || !blob) return NIR_ERR_INVALID_ARG;
+    if (cudaMemcpyToSymbolAsync(c_tab, blob, sizeof(float) * wq, sizeof(float) * base, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyToSymbolAsync(c_tab, blob + wq + gap, sizeof(float) * (total - wq - gap), sizeof(float) * (base + wq),
+                                cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return NIR_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? NIR_OK : NIR_ERR_CUDA;
+#else
+    (void)vid; (void)blob; (void)n; (void)st;
+    return NIR_OK;
+#endif
+}
 
 MeshKInfo NIR_MCAT(NIR_MESH_DIM, NIR_PREC)(int shape, int P)
 {

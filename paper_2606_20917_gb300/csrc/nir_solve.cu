@@ -19,7 +19,9 @@
 #include "nir_mesh.h"
 #include "nir_solve.h"
 
-#define NIR_MDECL(d, p) MeshKInfo nir_mesh_kinfo_d##d##_p##p(int shape, int P);
+#define NIR_MDECL(d, p)                                        \
+    MeshKInfo nir_mesh_kinfo_d##d##_p##p(int shape, int P);    \
+    int nir_mesh_tables_d##d##_p##p(int vid, const float *blob, int n, cudaStream_t st);
 NIR_MDECL(2, 0) NIR_MDECL(2, 1) NIR_MDECL(2, 2)
 NIR_MDECL(3, 0) NIR_MDECL(3, 1) NIR_MDECL(3, 2)
 #undef NIR_MDECL
@@ -31,6 +33,16 @@ MeshKInfo nir_mesh_kinfo(int dim, int prec, int shape, int P)
                                 {nir_mesh_kinfo_d3_p0, nir_mesh_kinfo_d3_p1, nir_mesh_kinfo_d3_p2}};
     if ((dim != 2 && dim != 3) || prec < 0 || prec > 2) return MeshKInfo{};
     return tab[dim - 2][prec](shape, P);
+}
+
+// Load a variant's FP32 tables into the mesh kernel's constant tables.
+int nir_mesh_tables(int dim, int prec, int vid, const float *blob, int n, cudaStream_t st)
+{
+    typedef int (*F)(int, const float *, int, cudaStream_t);
+    static const F tab[2][3] = {{nir_mesh_tables_d2_p0, nir_mesh_tables_d2_p1, nir_mesh_tables_d2_p2},
+                                {nir_mesh_tables_d3_p0, nir_mesh_tables_d3_p1, nir_mesh_tables_d3_p2}};
+    if ((dim != 2 && dim != 3) || prec < 0 || prec > 2) return NIR_ERR_INVALID_ARG;
+    return tab[dim - 2][prec](vid, blob, n, st);
 }
 
 namespace {
@@ -62,6 +74,10 @@ int nir_mesh_build_items(nir_mesh *m, int prec, int gran)
         ps.nt = k.nt;
         ps.smem = std::max(ps.smem, k.smem);
         ps.vid[bi] = k.vid;
+        if (prec != NIR_F64) {  // constant tables of the FP32/BF16 kernel (same for all blocks of a variant)
+            int rc = nir_mesh_tables(m->dim, prec, k.vid, b->tab32_h.data(), (int)b->tab32_h.size(), m->ctx->stream);
+            if (rc) return rc;
+        }
         const long long ngroups = (b->d.nelem + k.epb - 1) / k.epb;
         for (long long g = 0; g < ngroups; g += gran) {
             nirk::MeshItem it;
@@ -174,6 +190,62 @@ int nir_mesh_block_table(nir_mesh *m, int prec, double lambda, const void *in, v
     return NIR_OK;
 }
 
+int nir_mesh_blocks_ready(nir_mesh *m, int prec)
+{
+    for (nir_block *b : m->blocks) {
+        int rc = nir_block_ensure_prec(b, prec);
+        if (rc) return rc;
+        const int v = b->helm_variant[prec];
+        KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, nirk::OP_HELM, v);
+        if (!ki.fn) ki = nir_kinfo(b->d.shape, b->d.P, prec, nirk::OP_HELM, 0);
+        if (!ki.fn) return NIR_ERR_UNSUPPORTED;
+        if (nir_occupancy(m->ctx, ki) < 0) return NIR_ERR_CUDA;  // sets the kernel's shared-memory attribute
+    }
+    return NIR_OK;
+}
+
+// The blocks' kernels run on kSide concurrent branches (forked from and
+// joined back into `st` by events, so a graph captured from `st` holds
+// parallel branches): a block too small to fill the GPU overlaps the others.
+// Blocks go to branches largest first, each to the least-loaded branch.
+int nir_mesh_launch_blocks(nir_mesh *m, int prec, double lambda, const void *in, void *out, cudaStream_t st)
+{
+    const size_t es = nir_prec_size(prec);
+    const int nb = (int)m->blocks.size();
+    if (m->side_of.size() != (size_t)nb) {
+        std::vector<std::pair<double, int>> cost;
+        for (int bi = 0; bi < nb; ++bi)
+            cost.push_back({(double)m->blocks[bi]->d.nelem * elem_cost(m->blocks[bi]->d.shape, m->blocks[bi]->d.P), bi});
+        std::stable_sort(cost.begin(), cost.end(),
+                         [](const std::pair<double, int> &a, const std::pair<double, int> &b) { return a.first > b.first; });
+        double load[nir_mesh::kSide] = {};
+        m->side_of.assign(nb, 0);
+        for (auto &c : cost) {
+            int k = 0;
+            for (int j = 1; j < nir_mesh::kSide; ++j)
+                if (load[j] < load[k]) k = j;
+            m->side_of[c.second] = k;
+            load[k] += c.first;
+        }
+    }
+    NIR_CUDA_TRY(cudaEventRecord(m->ev_fork, st));
+    for (int k = 0; k < nir_mesh::kSide; ++k) NIR_CUDA_TRY(cudaStreamWaitEvent(m->side[k], m->ev_fork, 0));
+    int rc = NIR_OK;
+    for (int bi = 0; bi < nb && !rc; ++bi) {
+        const char *xb = static_cast<const char *>(in) + (size_t)m->off[bi] * es;
+        char *yb = static_cast<char *>(out) + (size_t)m->off[bi] * es;
+        rc = nir_launch_op(m->blocks[bi], prec, nirk::OP_HELM, lambda, xb, nullptr, nullptr, yb, nullptr, nullptr,
+                           m->side[m->side_of[bi]], 0);
+    }
+    // join every branch back, also after a failed launch (a capture must end joined)
+    for (int k = 0; k < nir_mesh::kSide; ++k) {
+        if (cudaEventRecord(m->ev_join[k], m->side[k]) != cudaSuccess ||
+            cudaStreamWaitEvent(st, m->ev_join[k], 0) != cudaSuccess)
+            rc = rc ? rc : NIR_ERR_CUDA;
+    }
+    return rc;
+}
+
 // Apply through a cached CUDA graph (captured on first use per key).
 int nir_mesh_apply(nir_mesh *m, int prec, double lambda, const void *in, void *out, cudaStream_t st)
 {
@@ -208,14 +280,16 @@ int nir_mesh_apply(nir_mesh *m, int prec, double lambda, const void *in, void *o
         g.in = in;
         g.out = out;
         g.lambda = lambda;
-        int rc = nir_mesh_block_table(m, prec, lambda, in, out, &g.dblk);
+        const bool blocks = m->ps[prec].mode == 1;
+        int rc = blocks ? nir_mesh_blocks_ready(m, prec) : nir_mesh_block_table(m, prec, lambda, in, out, &g.dblk);
         if (rc) return rc;
         cudaGraph_t graph;
         if (cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaFree(g.dblk);
             return NIR_ERR_CUDA;
         }
-        rc = nir_mesh_launch_raw(m, prec, g.dblk, m->cap_stream);
+        rc = blocks ? nir_mesh_launch_blocks(m, prec, lambda, in, out, m->cap_stream)
+                    : nir_mesh_launch_raw(m, prec, g.dblk, m->cap_stream);
         cudaError_t ec = cudaStreamEndCapture(m->cap_stream, &graph);
         if (rc || ec != cudaSuccess) {
             cudaFree(g.dblk);
@@ -260,8 +334,13 @@ extern "C" int nir_mesh_create(nir_ctx *ctx, nir_block *const *blocks, int nbloc
     }
     m->ndof = o;
     for (int p = 0; p < 3; ++p) m->ps[p].vid.assign(nblocks, -1);
-    if (cudaMalloc(&m->counter, sizeof(int) * 4) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    bool ok = cudaMalloc(&m->counter, sizeof(int) * 4) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < nir_mesh::kSide && ok; ++k)
+        ok = cudaStreamCreateWithFlags(&m->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&m->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
         nir_mesh_destroy(m);
         return NIR_ERR_CUDA;
     }
@@ -280,6 +359,11 @@ extern "C" void nir_mesh_destroy(nir_mesh *m)
         if (m->ps[p].ditems) cudaFree(m->ps[p].ditems);
     if (m->counter) cudaFree(m->counter);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    for (int k = 0; k < nir_mesh::kSide; ++k) {
+        if (m->side[k]) cudaStreamDestroy(m->side[k]);
+        if (m->ev_join[k]) cudaEventDestroy(m->ev_join[k]);
+    }
+    if (m->ev_fork) cudaEventDestroy(m->ev_fork);
     nir_cg_free(m);
     delete m->cg_op;
     delete m;
@@ -444,10 +528,11 @@ extern "C" int nir_tune(nir_mesh *m, const char *cache_path)
                                          std::to_string(b->d.nelem) + ";";
         std::string key = gpu + "|mesh|" + std::to_string(std::hash<std::string>{}(sig)) + "|" + pname[prec];
         auto it = kv.find(key);
-        int gran = 1, grid = 0;
+        int gran = 1, grid = 0, mode = 0;
         if (it != kv.end()) {
-            std::sscanf(it->second.c_str(), "%d,%d", &gran, &grid);
+            std::sscanf(it->second.c_str(), "%d,%d,%d", &gran, &grid, &mode);
             m->ps[prec].grid = grid;
+            m->ps[prec].mode = (mode == 1 && m->blocks.size() > 1) ? 1 : 0;
             rc = nir_mesh_build_items(m, prec, gran);
             continue;
         }
@@ -473,14 +558,46 @@ extern "C" int nir_tune(nir_mesh *m, const char *cache_path)
         if (rc) break;
         m->ps[prec].grid = grid;
         rc = nir_mesh_build_items(m, prec, gran);
+        if (rc) break;
+        // the persistent queue against each block's own (tuned) kernel in sequence
+        m->ps[prec].mode = 0;
+        if (m->blocks.size() > 1) {
+            rc = nir_mesh_blocks_ready(m, prec);
+            if (rc) break;
+            float tb = time_ms(st, 5, [&] {
+                if (!rc) rc = nir_mesh_launch_blocks(m, prec, 1.0, x, y, st);
+            });
+            if (!rc && tb < best) m->ps[prec].mode = 1;
+        }
         char val[64];
-        std::snprintf(val, sizeof val, "%d,%d", gran, grid);
+        std::snprintf(val, sizeof val, "%d,%d,%d", gran, grid, m->ps[prec].mode);
         kv[key] = val;
     }
     cudaStreamSynchronize(st);
     cudaFree(x);
     cudaFree(y);
+    for (auto &g : m->graphs) g.stale = true;  // the launch form or block kernels may have changed
+    nir_cg_invalidate(m);
     if (rc) return rc;
     if (!write_cache(cache_path, kv)) return NIR_ERR_INVALID_ARG;
+    return NIR_OK;
+}
+
+extern "C" int nir_mesh_get_launch(const nir_mesh *m, int prec, int *mode)
+{
+    if (!m || !valid_prec(prec) || !mode) return NIR_ERR_INVALID_ARG;
+    *mode = m->blocks.size() == 1 ? NIR_MESH_BLOCKS : m->ps[prec].mode;
+    return NIR_OK;
+}
+
+extern "C" int nir_mesh_set_launch(nir_mesh *m, int prec, int mode)
+{
+    if (!m || !valid_prec(prec) || (mode != NIR_MESH_PERSISTENT && mode != NIR_MESH_BLOCKS)) return NIR_ERR_INVALID_ARG;
+    if (m->ps[prec].mode != mode) {
+        m->ps[prec].mode = mode;
+        for (auto &g : m->graphs)
+            if (g.prec == prec) g.stale = true;
+        nir_cg_invalidate(m);
+    }
     return NIR_OK;
 }

@@ -16,6 +16,7 @@ struct MeshPrec {
     int nt = 256;                    // threads per CTA of the persistent kernel
     int grid = 0;                    // CTAs launched (tuned; 0: occ * SMs)
     int gran = 1;                    // element groups per work item (tuned)
+    int mode = 0;                    // 0: persistent kernel; 1: each block's own kernel in sequence (tuned)
     std::vector<int> vid;            // variant id per block
     nirk::MeshItem *ditems = nullptr;
     int nitems = 0;
@@ -47,6 +48,11 @@ struct nir_mesh {
     std::vector<unsigned> geo_seen;  // blocks' geometry versions the captured graphs use
     CGWork *cg = nullptr;
     CgOperator *cg_op = nullptr;     // the CG solver's view of this mesh
+    // concurrent branches of the block-kernel launch form
+    static constexpr int kSide = 4;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kSide] = {};
+    std::vector<int> side_of;        // branch of each block (cost-balanced)
 };
 
 int nir_mesh_build_items(nir_mesh *m, int prec, int gran);
@@ -54,6 +60,11 @@ int nir_mesh_build_items(nir_mesh *m, int prec, int gran);
 int nir_mesh_sync_geometry(nir_mesh *m);
 int nir_mesh_prepare(nir_mesh *m, int prec);
 int nir_mesh_launch_raw(nir_mesh *m, int prec, const nirk::MeshBlk *dblk, cudaStream_t st);
+// Each block's own kernel, one launch per block, on `st` (capturable once the
+// blocks' low-precision factors and kernel attributes exist).
+int nir_mesh_launch_blocks(nir_mesh *m, int prec, double lambda, const void *in, void *out, cudaStream_t st);
+// Create what nir_mesh_launch_blocks needs before it is captured.
+int nir_mesh_blocks_ready(nir_mesh *m, int prec);
 int nir_mesh_block_table(nir_mesh *m, int prec, double lambda, const void *in, void *out, nirk::MeshBlk **dout);
 int nir_mesh_apply(nir_mesh *m, int prec, double lambda, const void *in, void *out, cudaStream_t st);
 void nir_cg_free(nir_mesh *m);

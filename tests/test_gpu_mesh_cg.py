@@ -198,6 +198,33 @@ def test_graphs_follow_retuning_and_new_geometry(nir, ctx):
     assert rel(y_old, ref.ravel()) > 1e-6
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_launch_forms_agree(nir, ctx, prec):
+    """The persistent queue and the sequence of block kernels run the same
+    per-element code: identical results, also inside CG."""
+    parts = small_hybrid()
+    mesh, blocks = build_mesh(nir, ctx, parts)
+    assert mesh.get_launch(prec) == "persistent"
+    x = torch.from_numpy(W.coefficients(1, mesh.ndof, seed=6)[0]).cuda().to(nir.DTYPE[prec])
+    y0 = mesh.helmholtz(x, prec=prec).clone()
+    mesh.set_launch(prec, "blocks")
+    assert mesh.get_launch(prec) == "blocks"
+    y1 = mesh.helmholtz(x, prec=prec)
+    assert torch.equal(y0, y1)
+    if prec == "f32":
+        b = torch.from_numpy(W.coefficients(1, mesh.ndof, seed=7)[0]).cuda()
+        xs = []
+        for form in ("persistent", "blocks"):
+            mesh.set_launch("f32", form)
+            mesh.set_launch("f64", form)
+            xx = torch.zeros_like(b)
+            rc, st = mesh.cg_solve(b, xx, inner_prec="f32", tol=1e-10, max_outer=60, max_inner=5000)
+            assert rc == 0, st
+            xs.append(xx)
+        assert torch.equal(xs[0], xs[1])
+    assert nir.lib().nir_mesh_set_launch(mesh.h, nir.PREC[prec], 7) == -1  # INVALID_ARG
+
+
 def test_full_hybrid_mesh_sampled(nir, ctx):
     """The ~150k-element hybrid mesh in one persistent launch (tuned, as the
     benchmark runs it); the oracle recomputes two elements of every block."""
