@@ -174,6 +174,15 @@ int nir_helmholtz_host(nir_block *blk, int prec, double lambda, const void *h_in
  *     on it, so serialise them. */
 int nir_helmholtz_host_noalloc(nir_block *blk, int prec, double lambda, const void *h_in, void *h_out);
 
+/* Launch tuning of a block's Helmholtz kernel in one precision (what nir_tune
+ * sets): variant 0 = default elements per CTA, 1 = half, 2 = double (where it
+ * fits in shared memory; otherwise the default); grid = CTAs launched (0: one
+ * wave at the kernel's occupancy); pf = 1 to prefetch each group's metric to
+ * L2 (FP32/BF16 with per-point factors; ignored elsewhere).  Errors:
+ * INVALID_ARG. */
+int nir_block_set_tuning(nir_block *blk, int prec, int variant, int grid, int pf);
+int nir_block_get_tuning(const nir_block *blk, int prec, int *variant, int *grid, int *pf);
+
 /* Hybrid mesh: the concatenation of blocks (each with geometry set), applied
  * by one persistent launch (Sec. 2.2: operators batched over blocks of alike
  * elements).  Vectors are the concatenation of the blocks' coefficient arrays

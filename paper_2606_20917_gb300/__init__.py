@@ -63,6 +63,8 @@ _SIGS = {
     "nir_mass": [_vp, _i, _vp, _vp],
     "nir_helmholtz": [_vp, _i, _d, _vp, _vp],
     "nir_helmholtz_host": [_vp, _i, _d, _vp, _vp],
+    "nir_block_set_tuning": [_vp, _i, _i, _i, _i],
+    "nir_block_get_tuning": [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
     "nir_mesh_create": [_vp, C.POINTER(_vp), _i, C.POINTER(_vp)],
     "nir_mesh_num_dofs": [_vp, C.POINTER(_i64)],
     "nir_mesh_helmholtz": [_vp, _i, _d, _vp, _vp],
@@ -172,6 +174,15 @@ class Block:
         if h:
             _lib.nir_block_destroy(h)
             self.h = None
+
+    def set_tuning(self, prec: str, variant: int = 0, grid: int = 0, pf: int = 0):
+        """Force the Helmholtz launch tuning in one precision (see nir_block_set_tuning)."""
+        _chk(_lib.nir_block_set_tuning(self.h, PREC[prec], int(variant), int(grid), int(pf)), "set_tuning")
+
+    def get_tuning(self, prec: str):
+        v, g, p = _i(), _i(), _i()
+        _chk(_lib.nir_block_get_tuning(self.h, PREC[prec], C.byref(v), C.byref(g), C.byref(p)), "get_tuning")
+        return v.value, g.value, p.value
 
     def points(self):
         import numpy as np

@@ -547,6 +547,25 @@ extern "C" int nir_helmholtz_host(nir_block *b, int prec, double lambda, const v
 }
 
 // --------------------------------------------------------------------------- probe / misc
+extern "C" int nir_block_set_tuning(nir_block *b, int prec, int variant, int grid, int pf)
+{
+    if (!b || !valid_prec(prec) || variant < 0 || variant > 2 || grid < 0 || (pf != 0 && pf != 1))
+        return NIR_ERR_INVALID_ARG;
+    b->helm_variant[prec] = variant;
+    b->helm_grid[prec] = grid;
+    b->helm_pf[prec] = pf;
+    return NIR_OK;
+}
+
+extern "C" int nir_block_get_tuning(const nir_block *b, int prec, int *variant, int *grid, int *pf)
+{
+    if (!b || !valid_prec(prec)) return NIR_ERR_INVALID_ARG;
+    if (variant) *variant = b->helm_variant[prec];
+    if (grid) *grid = b->helm_grid[prec];
+    if (pf) *pf = b->helm_pf[prec];
+    return NIR_OK;
+}
+
 extern "C" int nir_probe_fp64_peak(nir_ctx *ctx, double *tflops)
 {
     if (!ctx || !tflops) return NIR_ERR_INVALID_ARG;

@@ -22,14 +22,14 @@ using TT = float;
 using TT = __nv_bfloat16;
 #endif
 
-template <int N, int OP, int EPB>
+template <int N, int OP, int EPB, bool STAGE = true>
 KInfo make1()
 {
     using C = Config<NIR_SHAPE, N, N + 1, TT, OP, EPB>;
     KInfo k;
     if constexpr (C::FUSED) {  // FP32/BF16 Helmholtz: bulk-copy staged kernel
-        constexpr int stg = ((C::EPB * C::M * (int)sizeof(TT) + 15) / 16) * 16;
-        k.fn = reinterpret_cast<const void *>(&k_helm_tma<NIR_SHAPE, N, N + 1, TT, EPB>);
+        constexpr int stg = STAGE ? ((C::EPB * C::M * (int)sizeof(TT) + 15) / 16) * 16 : 0;
+        k.fn = reinterpret_cast<const void *>(&k_helm_tma<NIR_SHAPE, N, N + 1, TT, EPB, STAGE>);
         k.smem = C::SMEM + stg;
     } else {
         k.fn = reinterpret_cast<const void *>(&k_elem<NIR_SHAPE, N, N + 1, TT, OP, EPB>);
@@ -42,7 +42,9 @@ KInfo make1()
 }
 
 // Variant 0: default elements per CTA; 1: half; 2: double (when it fits in
-// 227 KB of shared memory).  Only the Helmholtz operator has variants.
+// 227 KB of shared memory; an FP32/BF16 double group that fits only without
+// its staging buffer loads its coefficients itself).  Only the Helmholtz
+// operator has variants.
 template <int N, int OP>
 KInfo make(int variant)
 {
@@ -50,10 +52,15 @@ KInfo make(int variant)
     constexpr int e0 = C0::EPB;
     constexpr int eh = e0 > 1 ? e0 / 2 : 1;
     constexpr int stg2 = C0::FUSED ? ((2 * e0 * C0::M * (int)sizeof(TT) + 15) / 16) * 16 : 0;
-    constexpr int ed = (C0::TABB + 2 * C0::BUFB + stg2 <= 227 * 1024 && e0 < 64) ? 2 * e0 : e0;
+    constexpr bool fits = C0::TABB + 2 * C0::BUFB + stg2 <= 227 * 1024 && e0 < 64;
+    constexpr bool fits_unstaged = C0::FUSED && !fits && C0::TABB + 2 * C0::BUFB <= 227 * 1024 && e0 < 64;
+    constexpr int ed = (fits || fits_unstaged) ? 2 * e0 : e0;
     if constexpr (OP == OP_HELM) {
         if (variant == 1) return make1<N, OP, eh>();
-        if (variant == 2) return make1<N, OP, ed>();
+        if (variant == 2) {
+            if constexpr (fits_unstaged) return make1<N, OP, ed, false>();
+            else return make1<N, OP, ed>();
+        }
     }
     if (variant != 0) return KInfo{};
     return make1<N, OP, 0>();

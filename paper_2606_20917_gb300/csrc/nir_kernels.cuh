@@ -1195,7 +1195,9 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 // stage finds it there; the autotuner decides whether that pays.  Groups whose
 // copy would not be 16-byte aligned, and the ragged last group, are loaded
 // with plain coalesced loads.
-template <int SH, int N, int Q, class T, int EPB_ = 0>
+// STAGE = false: no staging buffer (coefficients loaded by the group itself),
+// for groups whose buffers alone nearly fill shared memory.
+template <int SH, int N, int Q, class T, int EPB_ = 0, bool STAGE = true>
 __global__ void __launch_bounds__(512)
     k_helm_tma(KArgs a, const __grid_constant__ TabP<typename CT<T>::type, layout(SH, N, Q).total> tp)
 {
@@ -1203,7 +1205,7 @@ __global__ void __launch_bounds__(512)
     using A = typename C::A;
     static_assert(C::FUSED, "FP32/BF16 Helmholtz only");
     constexpr int EPB = C::EPB, NT = C::NT, M = C::M, S = C::S, NQ = C::NQ, NG = ngeo(SH);
-    constexpr int STG = ((EPB * M * (int)sizeof(T) + 15) / 16) * 16;
+    constexpr int STG = STAGE ? ((EPB * M * (int)sizeof(T) + 15) / 16) * 16 : 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A *tab = reinterpret_cast<A *>(smem_raw);
     T *stage = reinterpret_cast<T *>(smem_raw + C::TABB);
@@ -1233,7 +1235,7 @@ __global__ void __launch_bounds__(512)
         }
     };
     auto issue = [&](long long g) -> int {
-        if (g >= ngroups) return 0;
+        if (!STAGE || g >= ngroups) return 0;
         const long long e0 = g * EPB;
         if (e0 + EPB > a.nelem) return 0;
         const T *src = in + e0 * M;

@@ -184,6 +184,28 @@ def test_low_precision_all_ops(nir, ctx, prec, shape, P):
         assert rel(got, ref) <= TOL[prec], (op, prec, rel(got, ref))
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("shape,P", [("hex", 4), ("hex", 6), ("tet", 4), ("prism", 6), ("quad", 4), ("tri", 7)])
+def test_helmholtz_every_launch_variant(nir, ctx, prec, shape, P):
+    """Every elements-per-CTA variant the tuner may pick (default, half, double;
+    for FP32/BF16 at P = 6 the double group runs without its staging buffer),
+    with and without the L2 metric prefetch and at two grid sizes."""
+    deformed = shape in ("hex", "quad")
+    E = 300 if DIM[shape] == 2 else (150 if P <= 4 else 101)   # several groups of every variant + a ragged tail
+    g, nodes, blk = setup(nir, ctx, shape, P, E, deformed)
+    x = inputs(blk, "helm")
+    ref = oracle_op(shape, P, g, nodes, "helm", x, 1.0)
+    for variant in (0, 1, 2):
+        for pf in (0, 1):
+            for grid in (0, 152):
+                blk.set_tuning(prec, variant, grid, pf)
+                got = run_op(blk, "helm", prec, x, 1.0)
+                assert rel(got, ref) <= TOL[prec], (variant, pf, grid, rel(got, ref))
+    assert blk.get_tuning(prec) == (2, 152, 1)
+    with pytest.raises(nir.NirError):
+        blk.set_tuning(prec, 3)
+
+
 @pytest.mark.parametrize("shape", ["quad", "tri", "hex", "prism", "tet"])
 def test_single_element_and_exact_group(nir, ctx, shape):
     P = 3
