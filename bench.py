@@ -621,6 +621,73 @@ def run_gsolve(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args, ws, rank, local):
+    """Helmholtz throughput against problem size for P = 1..8 on hexahedra and
+    tetrahedra (the paper's GPU throughput study, Sec. 4.2): one block per
+    (shape, P, size), throughput = DOF / device time of one apply (CUDA events
+    over repeated applies), with the kernel's registers per thread."""
+    import torch
+    import paper_2606_20917_gb300 as nir
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ctx = nir.Context(local, stream)
+    fp64_peak = ctx.probe_fp64_peak()
+    peaks = measured_peaks()
+    prec = args.prec
+    wb = {"f64": 8, "f32": 4, "bf16": 2}[prec]
+    targets = [float(t) for t in args.sweep_dofs.split(",")]
+    recs = []
+    for shape in args.sweep_shapes.split(","):
+        for P in range(1, 9):
+            N, Q = P + 1, P + 2
+            M = num_modes(shape, N)
+            for target in targets:
+                E = max(1, int(round(target / M)))
+                if shape == "hex":
+                    n = max(1, int(round(E ** (1.0 / 3.0))))
+                    nodes, gorder, deformed = W.hex_grid(n, 2), 2, True
+                else:
+                    n = max(1, int(round((E / 6.0) ** (1.0 / 3.0))))
+                    nodes, gorder, deformed = W.tet_kuhn(n), 1, False
+                E = nodes.shape[0]
+                blk = nir.Block(ctx, shape, E, P, deformed=deformed)
+                blk.set_geometry(gorder, torch.from_numpy(nodes).to(dev))
+                if prec != "f64":
+                    blk.set_tuning(prec, 0, 0, 1)  # L2 metric prefetch on
+                x = torch.from_numpy(W.coefficients(E, M, seed=0)).to(dev, nir.DTYPE[prec])
+                y = torch.empty_like(x)
+                for _ in range(3):
+                    blk.helmholtz(x, prec=prec, out=y)
+                reps = max(3, min(50, int(2e8 / (E * M))))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(stream)
+                for _ in range(reps):
+                    blk.helmholtz(x, prec=prec, out=y)
+                b.record(stream)
+                torch.cuda.synchronize()
+                t = a.elapsed_time(b) / reps * 1e-3
+                rec = {"shape": shape, "P": P, "nelem": E, "dof": E * M, "gdofs": E * M / t / 1e9,
+                       "ms": t * 1e3, **blk.kernel_info(prec, "helm")}
+                if prec == "f64":
+                    rec["frac_fp64"] = E * helm_flops_per_elem(shape, N, Q) / t / 1e12 / fp64_peak
+                else:
+                    rec["frac_hbm"] = E * helm_bytes_per_elem(shape, N, Q, wb, deformed) / t / 1e9 / peaks["hbm_gbs"]
+                recs.append(rec)
+                del blk, x, y
+                torch.cuda.empty_cache()
+    if rank != 0:
+        return
+    line = {"metric": "Helmholtz apply GDOF/s vs DOF and P (sweep)", "value": None, "unit": "GDOF/s",
+            "n_gpus": ws, "higher_is_better": True, "dtype": prec, "data": "synthetic",
+            "config": {"workload": "hex (32-cell-style curved grids, lattice g = 2) and Kuhn-split tet meshes, "
+                                   "P = 1..8, Q = P + 2", "dof_targets": targets, "fp64_peak_tflops": fp64_peak},
+            "sweep": recs}
+    print(json.dumps(line), flush=True)
+
+
 def run_hybrid(args, ws, rank, local):
     """Hybrid mesh (~150k hex/prism/tet, P = 2..8) in one persistent launch."""
     import torch
@@ -715,7 +782,9 @@ def main():
     ap.add_argument("--extras", action="store_true", help="also time the FP32/BF16 applies")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-operators", action="store_true", help="skip the per-operator table")
-    ap.add_argument("--mode", choices=["apply", "solve", "gsolve", "hybrid"], default="apply")
+    ap.add_argument("--mode", choices=["apply", "solve", "gsolve", "hybrid", "sweep"], default="apply")
+    ap.add_argument("--sweep-shapes", default="hex,tet")
+    ap.add_argument("--sweep-dofs", default="1e5,1e6,1e7,3e7")
     ap.add_argument("--solve-precs", default="f64,f32,bf16")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--inner-tol", type=float, default=1e-3)
@@ -738,6 +807,8 @@ def main():
         run_gsolve(args, ws, rank, local)
     elif args.mode == "hybrid":
         run_hybrid(args, ws, rank, local)
+    elif args.mode == "sweep":
+        run_sweep(args, ws, rank, local)
     else:
         run_nir(args, ws, rank, local)
     if ws > 1:

@@ -183,6 +183,15 @@ int nir_helmholtz_host_noalloc(nir_block *blk, int prec, double lambda, const vo
 int nir_block_set_tuning(nir_block *blk, int prec, int variant, int grid, int pf);
 int nir_block_get_tuning(const nir_block *blk, int prec, int *variant, int *grid, int *pf);
 
+/* Resources of the kernel a block launches for operator `op` in `prec` (with
+ * the block's current tuning): registers per thread, shared memory per CTA
+ * (dynamic + static, bytes), threads per CTA and elements per CTA group.  op:
+ * 0 BwdTrans, 1 IProductWRTBase, 2 PhysDeriv, 3 IProductWRTDerivBase, 4 mass,
+ * 5 Helmholtz.  NULL outputs are skipped.  Errors: INVALID_ARG, UNSUPPORTED,
+ * CUDA. */
+int nir_block_kernel_info(const nir_block *blk, int prec, int op, int *regs, int *smem_bytes, int *threads,
+                          int *elems_per_cta);
+
 /* Hybrid mesh: the concatenation of blocks (each with geometry set), applied
  * by one persistent launch (Sec. 2.2: operators batched over blocks of alike
  * elements).  Vectors are the concatenation of the blocks' coefficient arrays

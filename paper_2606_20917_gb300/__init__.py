@@ -64,6 +64,7 @@ _SIGS = {
     "nir_helmholtz": [_vp, _i, _d, _vp, _vp],
     "nir_helmholtz_host": [_vp, _i, _d, _vp, _vp],
     "nir_block_set_tuning": [_vp, _i, _i, _i, _i],
+    "nir_block_kernel_info": [_vp, _i, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
     "nir_block_get_tuning": [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
     "nir_mesh_create": [_vp, C.POINTER(_vp), _i, C.POINTER(_vp)],
     "nir_mesh_num_dofs": [_vp, C.POINTER(_i64)],
@@ -183,6 +184,16 @@ class Block:
         v, g, p = _i(), _i(), _i()
         _chk(_lib.nir_block_get_tuning(self.h, PREC[prec], C.byref(v), C.byref(g), C.byref(p)), "get_tuning")
         return v.value, g.value, p.value
+
+    OPS = {"bwd": 0, "iprod": 1, "physderiv": 2, "iprod_deriv": 3, "mass": 4, "helm": 5}
+
+    def kernel_info(self, prec: str = "f64", op: str = "helm") -> dict:
+        """Registers, shared memory, threads and elements per CTA of the kernel this
+        block launches for `op` (with its current tuning)."""
+        r, sm, t, e = _i(), _i(), _i(), _i()
+        _chk(_lib.nir_block_kernel_info(self.h, PREC[prec], self.OPS[op], C.byref(r), C.byref(sm), C.byref(t),
+                                        C.byref(e)), "nir_block_kernel_info")
+        return {"registers": r.value, "smem_bytes": sm.value, "threads": t.value, "elems_per_cta": e.value}
 
     def points(self):
         import numpy as np

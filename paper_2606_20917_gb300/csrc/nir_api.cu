@@ -566,6 +566,23 @@ extern "C" int nir_block_get_tuning(const nir_block *b, int prec, int *variant, 
     return NIR_OK;
 }
 
+extern "C" int nir_block_kernel_info(const nir_block *b, int prec, int op, int *regs, int *smem_bytes, int *threads,
+                                     int *elems_per_cta)
+{
+    if (!b || !valid_prec(prec) || op < 0 || op > 5) return NIR_ERR_INVALID_ARG;
+    const int variant = op == nirk::OP_HELM ? b->helm_variant[prec] : 0;
+    KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, op, variant);
+    if (!ki.fn) ki = nir_kinfo(b->d.shape, b->d.P, prec, op, 0);
+    if (!ki.fn) return NIR_ERR_UNSUPPORTED;
+    cudaFuncAttributes fa;
+    NIR_CUDA_TRY(cudaFuncGetAttributes(&fa, ki.fn));
+    if (regs) *regs = fa.numRegs;
+    if (smem_bytes) *smem_bytes = ki.smem + (int)fa.sharedSizeBytes;
+    if (threads) *threads = ki.nt;
+    if (elems_per_cta) *elems_per_cta = ki.epb;
+    return NIR_OK;
+}
+
 extern "C" int nir_probe_fp64_peak(nir_ctx *ctx, double *tflops)
 {
     if (!ctx || !tflops) return NIR_ERR_INVALID_ARG;

@@ -312,3 +312,16 @@ def test_host_buffer_pipeline_chunks(nir, ctx):
         blk.helmholtz_host(u, out, lam=1.0, prec=prec)
         ref = blk.helmholtz(u.cuda(), lam=1.0, prec=prec).cpu()
         assert torch.equal(out, ref), prec
+
+
+def test_kernel_info_reports_the_launched_kernel(nir, ctx):
+    g, nodes, blk = setup(nir, ctx, "hex", 4, 40, True)
+    for prec in ("f64", "f32"):
+        for op in ("bwd", "helm"):
+            ki = blk.kernel_info(prec, op)
+            assert 0 < ki["registers"] <= 255 and ki["threads"] in (128, 256, 512, 1024)
+            assert ki["smem_bytes"] > 0 and ki["elems_per_cta"] >= 1
+    blk.set_tuning("f32", 1, 0, 0)
+    half = blk.kernel_info("f32", "helm")["elems_per_cta"]
+    blk.set_tuning("f32", 0, 0, 0)
+    assert blk.kernel_info("f32", "helm")["elems_per_cta"] == 2 * half
