@@ -84,8 +84,11 @@ constexpr int odd_stride(int n) { return (n % 2 == 0) ? n + 1 : n; }
 // inside the loop, so the compiler keeps the (warp-broadcast) table loads in
 // the loop instead of hoisting NIN x NOUT values into registers for threads
 // that only run one or two iterations.
-template <class A, int NIN, int NOUT, int NEX, int OEX, int EPB, int NT, class LD, class TB, class LDX,
-          class TBX, class ST>
+// ROLL keeps the output loop rolled (only the NIN multiply-adds of one output
+// are unrolled): the collapsed shapes' class-split stages at high order
+// otherwise unroll into more code than the instruction cache holds.
+template <class A, int NIN, int NOUT, int NEX, int OEX, int EPB, int NT, bool ROLL = false, class LD, class TB,
+          class LDX, class TBX, class ST>
 __device__ __forceinline__ void pencils(int per_e, int &rot, LD ld, TB tb, LDX ldx, TBX tbx, ST st)
 {
     // The bound is hidden from the compiler: with few elements per CTA it can
@@ -104,8 +107,7 @@ __device__ __forceinline__ void pencils(int per_e, int &rot, LD ld, TB tb, LDX l
         ld(e, s, x);
         A xx[NEX > 0 ? NEX : 1];
         if constexpr (NEX > 0) ldx(e, s, xx);
-#pragma unroll
-        for (int o = 0; o < NOUT; ++o) {
+        auto one = [&](int o) {
             A acc = A(0);
 #pragma unroll
             for (int r = 0; r < NIN; ++r) acc = fmaa(tb(z, o, r), x[r], acc);
@@ -116,6 +118,13 @@ __device__ __forceinline__ void pencils(int per_e, int &rot, LD ld, TB tb, LDX l
                 }
             }
             st(e, s, o, acc);
+        };
+        if constexpr (ROLL) {
+#pragma unroll 1
+            for (int o = 0; o < NOUT; ++o) one(o);
+        } else {
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) one(o);
         }
     }
     rot += total;
@@ -146,10 +155,10 @@ struct NoTX {
     __device__ int operator()(int, int) const { return 0; }
 };
 
-template <class A, int NIN, int NOUT, int EPB, int NT, class LD, class TB, class ST>
+template <class A, int NIN, int NOUT, int EPB, int NT, bool ROLL = false, class LD, class TB, class ST>
 __device__ __forceinline__ void pencils0(int per_e, int &rot, LD ld, TB tb, ST st)
 {
-    pencils<A, NIN, NOUT, 0, 0, EPB, NT>(per_e, rot, ld, tb, NoX{}, [](int, int) { return A(0); }, st);
+    pencils<A, NIN, NOUT, 0, 0, EPB, NT, ROLL>(per_e, rot, ld, tb, NoX{}, [](int, int) { return A(0); }, st);
 }
 
 // Table accessors.  Tables live either in shared memory (the persistent mesh
@@ -268,6 +277,9 @@ template <int SH, int N, int Q, class A, int EPB, int NT, int S>
 struct Modal {
     static constexpr TabLayout L = layout(SH, N, Q);
     static constexpr int QQ = Q * Q;
+    // class-split stages of the collapsed shapes keep their output loops
+    // rolled from P = 6 on in FP32/BF16 (code size; FP64 is bound by its FMA pipe)
+    static constexpr bool R = (SH == TRI || SH == TET || SH == PRISM) && N >= 7 && sizeof(A) == 4;
 
     // All BwdTrans stages but the last: 2-D p0 -> p1; 3-D p0 -> p1 -> p2.
     template <class TP>
@@ -290,7 +302,7 @@ struct Modal {
                     constexpr int nin = nc + (p == 1 ? 1 : 0);
                     const TP Bp = tab + L.Bb + cls_off(N, Q, p);
                     const TP B0 = tab + L.Bb;
-                    pencils0<A, nin, Q, EPB, NT>(1, rot,
+                    pencils0<A, nin, Q, EPB, NT, R>(1, rot,
                         [=](int e, int, A *x) { const A *b = p0 + e * S + tri_m0(N, p);
 #pragma unroll
                             for (int r = 0; r < nc; ++r) x[r] = b[r];
@@ -316,7 +328,7 @@ struct Modal {
                     constexpr int nin = nc + (p == 1 ? 1 : 0);
                     const TP Bp = tab + L.Bb + cls_off(N, Q, p);
                     const TP B0 = tab + L.Bb;
-                    pencils0<A, nin, Q, EPB, NT>(N, rot,
+                    pencils0<A, nin, Q, EPB, NT, R>(N, rot,
                         [=](int e, int q, A *x) { const A *b = p0 + e * S + prism_m0(N, p, q);
 #pragma unroll
                             for (int r = 0; r < nc; ++r) x[r] = b[r];
@@ -333,7 +345,7 @@ struct Modal {
                     constexpr int nin = nc + (c == 1 ? 1 : 0);
                     const TP Bc = tab + L.Bc + cls_off(N, Q, c);
                     const TP B0 = tab + L.Bc;
-                    pencils0<A, nin, Q, EPB, NT>(c + 1, rot,
+                    pencils0<A, nin, Q, EPB, NT, R>(c + 1, rot,
                         [=](int e, int p, A *x) { const A *b = p0 + e * S + tet_m0(N, p, c - p);
 #pragma unroll
                             for (int r = 0; r < nc; ++r) x[r] = b[r];
@@ -359,7 +371,7 @@ struct Modal {
                     constexpr int nin = nc + (p == 1 ? 1 : 0);
                     const TP Bp = tab + L.Bb + cls_off(N, Q, p);
                     const TP B0 = tab + L.Bb;
-                    pencils0<A, nin, Q, EPB, NT>(Q, rot,
+                    pencils0<A, nin, Q, EPB, NT, R>(Q, rot,
                         [=](int e, int k, A *x) { const A *b = p1 + e * S + tet_pair(N, p, 0) * Q + k;
 #pragma unroll
                             for (int r = 0; r < nc; ++r) x[r] = b[r * Q];
@@ -391,7 +403,7 @@ struct Modal {
                     constexpr int nex = (p == 0 && N > 1) ? Q : 0;
                     const TP Bp = tab + L.Bb + cls_off(N, Q, p);
                     const TP B0 = tab + L.Bb;
-                    pencils<A, Q, nc, nex, 1, EPB, NT>(1, rot,
+                    pencils<A, Q, nc, nex, 1, EPB, NT, R>(1, rot,
                         [=](int e, int, A *x) { const A *b = p1 + e * S + p * Q;
 #pragma unroll
                             for (int r = 0; r < Q; ++r) x[r] = b[r]; },
@@ -421,7 +433,7 @@ struct Modal {
                     constexpr int nex = (p == 0 && N > 1) ? Q : 0;
                     const TP Bp = tab + L.Bb + cls_off(N, Q, p);
                     const TP B0 = tab + L.Bb;
-                    pencils<A, Q, nc, nex, 1, EPB, NT>(Q, rot,
+                    pencils<A, Q, nc, nex, 1, EPB, NT, R>(Q, rot,
                         [=](int e, int k, A *x) { const A *b = p1 + e * S + p * QQ + k;
 #pragma unroll
                             for (int r = 0; r < Q; ++r) x[r] = b[r * Q]; },
@@ -448,7 +460,7 @@ struct Modal {
                     constexpr int nex = (p == 0 && N > 1) ? Q : 0;
                     const TP Bp = tab + L.Bb + cls_off(N, Q, p);
                     const TP B0 = tab + L.Bb;
-                    pencils<A, Q, nc, nex, 1, EPB, NT>(N, rot,
+                    pencils<A, Q, nc, nex, 1, EPB, NT, R>(N, rot,
                         [=](int e, int q, A *x) { const A *b = p2 + e * S + (p * N + q) * Q;
 #pragma unroll
                             for (int r = 0; r < Q; ++r) x[r] = b[r]; },
@@ -466,7 +478,7 @@ struct Modal {
                     constexpr int nex = (c == 0 && N > 1) ? 2 * Q : 0;
                     const TP Bc = tab + L.Bc + cls_off(N, Q, c);
                     const TP B0 = tab + L.Bc;
-                    pencils<A, Q, nc, nex, 1, EPB, NT>(c + 1, rot,
+                    pencils<A, Q, nc, nex, 1, EPB, NT, R>(c + 1, rot,
                         [=](int e, int p, A *x) { const A *b = p2 + e * S + tet_pair(N, p, c - p) * Q;
 #pragma unroll
                             for (int r = 0; r < Q; ++r) x[r] = b[r]; },
