@@ -583,7 +583,7 @@ struct Geo {
 // Default elements per CTA: fill about 110 KB (FP64) or 56 KB (FP32/BF16) of
 // shared memory with the operator's buffers.  EPB_ > 0 overrides it (the
 // autotuner picks among compiled alternatives).
-template <int SH, int N, int Q, class T, int OP, int EPB_ = 0>
+template <int SH, int N, int Q, class T, int OP, int EPB_ = 0, int NT_ = 0>
 struct Config {
     using A = typename CT<T>::type;
     static constexpr int D = dim(SH);
@@ -603,7 +603,15 @@ struct Config {
     static constexpr int EPB_DEF = raw >= 64 ? 64 : raw >= 32 ? 32 : raw >= 16 ? 16 : raw >= 8 ? 8 : raw >= 4 ? 4
                                  : raw >= 2 ? 2 : 1;
     static constexpr int EPB = EPB_ > 0 ? EPB_ : EPB_DEF;
-    static constexpr int NT = FUSED ? 512 : 256;
+    // Threads: 256 (512 for the fused FP32/BF16 Helmholtz), fewer when a group
+    // is small: the fused stages then have Q^2 (3-D) or Q (2-D) pencils per
+    // element, and a CTA of half that many threads runs its heaviest stages in
+    // two full rounds instead of leaving warps idle at every barrier.  NT_ > 0
+    // forces a size (the persistent mesh kernel shares one size).
+    static constexpr int PENCILS = (D == 3 ? Q * Q : Q) * EPB;
+    static constexpr int NT_HALF = ((PENCILS / 2 + 31) / 32) * 32;
+    static constexpr int NT_AUTO = FUSED ? (NT_HALF >= 512 ? 512 : NT_HALF < 128 ? 128 : NT_HALF) : 256;
+    static constexpr int NT = NT_ > 0 ? NT_ : NT_AUTO;
     static constexpr int BUFB = NBUF * EPB * S * (int)sizeof(A);
     static constexpr int SMEM = TABB + BUFB;
 };
@@ -982,11 +990,11 @@ __device__ __forceinline__ void helm_metric(const Geo<T, A, NQ, NG> &geo, long l
 // TP: table accessor for the contractions (STab or PTab); tab: the same
 // tables in shared memory (collocation gathers of PhysDeriv and
 // IProductWRTDerivBase, reference weights).
-template <int SH, int N, int Q, class T, int OP, int EPB_, class TP>
+template <int SH, int N, int Q, class T, int OP, int EPB_, int NT_, class TP>
 __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename CT<T>::type *tab,
                                           typename CT<T>::type *buf, long long e0, int ne, bool staged = false)
 {
-    using C = Config<SH, N, Q, T, OP, EPB_>;
+    using C = Config<SH, N, Q, T, OP, EPB_, NT_>;
     using A = typename C::A;
     constexpr int D = C::D, NQ = C::NQ, M = C::M, S = C::S, EPB = C::EPB, NT = C::NT;
     constexpr TabLayout L = layout(SH, N, Q);
@@ -1210,7 +1218,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 // STAGE = false: no staging buffer (coefficients loaded by the group itself),
 // for groups whose buffers alone nearly fill shared memory.
 template <int SH, int N, int Q, class T, int EPB_ = 0, bool STAGE = true>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(Config<SH, N, Q, T, OP_HELM, EPB_>::NT)
     k_helm_tma(KArgs a, const __grid_constant__ TabP<typename CT<T>::type, layout(SH, N, Q).total> tp)
 {
     using C = Config<SH, N, Q, T, OP_HELM, EPB_>;
@@ -1277,7 +1285,7 @@ __global__ void __launch_bounds__(512)
         }
         __syncthreads();
         if (threadIdx.x == 0) s_next = issue(g + gridDim.x);  // stage is free again
-        run_group<SH, N, Q, T, OP_HELM, EPB_>(a, ptab, tab, buf, e0, ne, staged);
+        run_group<SH, N, Q, T, OP_HELM, EPB_, 0>(a, ptab, tab, buf, e0, ne, staged);
     }
 }
 
@@ -1305,14 +1313,14 @@ __global__ void __launch_bounds__(256)
         for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
             const long long e0 = g * EPB;
             const int ne = (int)((a.nelem - e0) < EPB ? (a.nelem - e0) : EPB);
-            run_group<SH, N, Q, T, OP, EPB_>(a, ptab, tab, buf, e0, ne);
+            run_group<SH, N, Q, T, OP, EPB_, 0>(a, ptab, tab, buf, e0, ne);
         }
     } else {
         const STab<A> stab{tab};
         for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
             const long long e0 = g * EPB;
             const int ne = (int)((a.nelem - e0) < EPB ? (a.nelem - e0) : EPB);
-            run_group<SH, N, Q, T, OP, EPB_>(a, stab, tab, buf, e0, ne);
+            run_group<SH, N, Q, T, OP, EPB_, 0>(a, stab, tab, buf, e0, ne);
         }
     }
 }

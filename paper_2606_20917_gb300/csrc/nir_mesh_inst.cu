@@ -37,6 +37,9 @@ constexpr int kShapes[2] = {QUAD, TRI};
 #endif
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(int);
 
+// every variant of one persistent kernel runs with the same thread count
+constexpr int kMeshNT = sizeof(typename CT<TT>::type) == 8 ? 256 : 512;
+
 // FP32/BF16 kernels take the contractions' table values as constant-bank
 // operands, as the single-block kernels do with their table parameter: the
 // tables of every (shape, P) variant of this kernel live in one __constant__
@@ -90,7 +93,7 @@ NIR_HD constexpr bool use_ctab(int SH, int N)
 template <int SH, int N, int VID>
 __device__ __noinline__ void run_item(const MeshBlk &mb, const MeshItem &m, unsigned char *smem, int &cur)
 {
-    using C = Config<SH, N, N + 1, TT, OP_HELM, 0>;
+    using C = Config<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>;
     using A = typename C::A;
     A *tab = reinterpret_cast<A *>(smem);
     A *buf = reinterpret_cast<A *>(smem + C::TABB);
@@ -108,12 +111,12 @@ __device__ __noinline__ void run_item(const MeshBlk &mb, const MeshItem &m, unsi
         if constexpr (use_ctab(SH, N)) {
             constexpr TabLayout L = layout(SH, N, N + 1);
             using CT = CTab<ctab_base<VID>(), L.wq, npts(SH, N + 1)>;
-            run_group<SH, N, N + 1, TT, OP_HELM, 0>(mb.a, CT{0}, tab, buf, e0, ne);
+            run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, CT{0}, tab, buf, e0, ne);
         } else {
-            run_group<SH, N, N + 1, TT, OP_HELM, 0>(mb.a, STab<A>{tab}, tab, buf, e0, ne);
+            run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, STab<A>{tab}, tab, buf, e0, ne);
         }
 #else
-        run_group<SH, N, N + 1, TT, OP_HELM, 0>(mb.a, STab<A>{tab}, tab, buf, e0, ne);
+        run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, STab<A>{tab}, tab, buf, e0, ne);
 #endif
     }
 }
@@ -131,7 +134,6 @@ __device__ __forceinline__ void dispatch_one(int vid, const MeshBlk &mb, const M
     }
 }
 
-constexpr int kMeshNT = Config<HEX, 5, 6, TT, OP_HELM, 0>::NT;  // the same for every variant
 
 __global__ void __launch_bounds__(kMeshNT, 2) k_mesh(const MeshBlk *__restrict__ blks, const MeshItem *__restrict__ items,
                                               int nitems, int *counter)
@@ -155,7 +157,7 @@ template <int VID>
 int smem_of(int vid)
 {
     if constexpr (VID < kNumShapes * 8) {
-        if (vid == VID) return Config<kShapes[VID / 8], VID % 8 + 2, VID % 8 + 3, TT, OP_HELM, 0>::SMEM;
+        if (vid == VID) return Config<kShapes[VID / 8], VID % 8 + 2, VID % 8 + 3, TT, OP_HELM, 0, kMeshNT>::SMEM;
         return smem_of<VID + 1>(vid);
     }
     return -1;
@@ -165,7 +167,7 @@ template <int VID>
 int epb_of(int vid)
 {
     if constexpr (VID < kNumShapes * 8) {
-        if (vid == VID) return Config<kShapes[VID / 8], VID % 8 + 2, VID % 8 + 3, TT, OP_HELM, 0>::EPB;
+        if (vid == VID) return Config<kShapes[VID / 8], VID % 8 + 2, VID % 8 + 3, TT, OP_HELM, 0, kMeshNT>::EPB;
         return epb_of<VID + 1>(vid);
     }
     return -1;
