@@ -144,6 +144,13 @@ int nir_mass(nir_block *blk, int prec, const void *coeff_in, void *coeff_out);
 /* Helmholtz operator (L + lambda M) u_hat (Eqs. weakmatrixhelm, laplacian),
  * one fused launch.  [E][M] -> [E][M]; lambda > 0 for an SPD operator. */
 int nir_helmholtz(nir_block *blk, int prec, double lambda, const void *coeff_in, void *coeff_out);
+/* The Helmholtz operator applied to 1..3 fields of the same block in one
+ * launch (e.g. the velocity components of a velocity-correction step, which
+ * share the operator): in[f] -> out[f], each [E][M] in prec, all distinct.
+ * Each element group computes its fields back to back, so the group's
+ * geometric factors are read from HBM once.  Errors: INVALID_ARG, STATE. */
+int nir_helmholtz_fields(nir_block *blk, int prec, double lambda, int nfields, const void *const *in,
+                         void *const *out);
 /* nir_helmholtz on HOST buffers: copies h_in to the device, applies, copies
  * the result to h_out, and synchronises.  Pinned host memory gives full
  * copy bandwidth.  Device staging buffers are library-owned. */

@@ -63,6 +63,7 @@ _SIGS = {
     "nir_mass": [_vp, _i, _vp, _vp],
     "nir_helmholtz": [_vp, _i, _d, _vp, _vp],
     "nir_helmholtz_host": [_vp, _i, _d, _vp, _vp],
+    "nir_helmholtz_fields": [_vp, _i, _d, _i, C.POINTER(_vp), C.POINTER(_vp)],
     "nir_block_set_tuning": [_vp, _i, _i, _i, _i],
     "nir_block_kernel_info": [_vp, _i, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
     "nir_block_get_tuning": [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
@@ -278,6 +279,20 @@ class Block:
         out = self._out(self.M, prec, out)
         _chk(_lib.nir_helmholtz(self.h, PREC[prec], float(lam), _ptr(coeff), _ptr(out)), "nir_helmholtz")
         return out
+
+    def helmholtz_fields(self, fields, lam=1.0, prec="f64", outs=None):
+        """Helmholtz on 1..3 fields [E][M] in one launch; returns the outputs."""
+        if not 1 <= len(fields) <= 3:
+            raise ValueError("1 to 3 fields")
+        for f in fields:
+            self._dev(f, DTYPE[prec], "field"); self._chk_shape(f, self.M, "field")
+        outs = outs or [self._out(self.M, prec, None) for _ in fields]
+        for o in outs:
+            self._dev(o, DTYPE[prec], "out"); self._chk_shape(o, self.M, "out")
+        ins = (_vp * len(fields))(*[f.data_ptr() for f in fields])
+        ous = (_vp * len(outs))(*[o.data_ptr() for o in outs])
+        _chk(_lib.nir_helmholtz_fields(self.h, PREC[prec], float(lam), len(fields), ins, ous), "nir_helmholtz_fields")
+        return outs
 
     def helmholtz_host(self, coeff_host, out_host, lam=1.0, prec="f64"):
         """Helmholtz on host tensors (pinned for full bandwidth); synchronous."""

@@ -144,6 +144,7 @@ int nir_launch_op_range(nir_block *b, int prec, int op, double lambda, const voi
     a.geo_pp = b->geo_pp;
     a.pf = (op == nirk::OP_HELM && prec >= 0 && prec < 3) ? b->helm_pf[prec] : 0;
     a.err = b->ctx->derr;
+    a.nfields = op == nirk::OP_HELM ? (in2 ? 3 : in1 ? 2 : 1) : 1;
     // the kernel's second parameter is the table blob in its compute type
     const void *tabp = (prec == NIR_F64) ? (const void *)b->tab_h.data() : (const void *)b->tab32_h.data();
     if ((size_t)ki.tabp_bytes != (prec == NIR_F64 ? b->tab_h.size() * 8 : b->tab32_h.size() * 4))
@@ -474,6 +475,26 @@ extern "C" int nir_helmholtz(nir_block *b, int prec, double lambda, const void *
     if (!in || !out || in == out || !std::isfinite(lambda)) return NIR_ERR_INVALID_ARG;
     return nir_launch_op(b, prec, nirk::OP_HELM, lambda, in, nullptr, nullptr, out, nullptr, nullptr,
                          b->ctx->stream, 0);
+}
+
+extern "C" int nir_helmholtz_fields(nir_block *b, int prec, double lambda, int nfields, const void *const *in,
+                                    void *const *out)
+{
+    int rc = check_block(b, prec);
+    if (rc) return rc;
+    if (nfields < 1 || nfields > 3 || !in || !out || !std::isfinite(lambda)) return NIR_ERR_INVALID_ARG;
+    std::vector<const void *> ptrs;
+    for (int f = 0; f < nfields; ++f) {
+        if (!in[f] || !out[f]) return NIR_ERR_INVALID_ARG;
+        ptrs.push_back(in[f]);
+        ptrs.push_back(out[f]);
+    }
+    for (size_t i = 0; i < ptrs.size(); ++i)
+        for (size_t j = i + 1; j < ptrs.size(); ++j)
+            if (ptrs[i] == ptrs[j]) return NIR_ERR_INVALID_ARG;
+    return nir_launch_op(b, prec, nirk::OP_HELM, lambda, in[0], nfields > 1 ? in[1] : nullptr,
+                         nfields > 2 ? in[2] : nullptr, out[0], nfields > 1 ? out[1] : nullptr,
+                         nfields > 2 ? out[2] : nullptr, b->ctx->stream, 0);
 }
 
 // Host-buffer Helmholtz: the elements are split into chunks (multiples of 64

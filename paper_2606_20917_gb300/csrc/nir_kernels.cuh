@@ -52,7 +52,12 @@ struct KArgs {
     int geo_pp;                   // 1: per point, 32-element interleaved; 0: per element
     int pf;                       // FP32/BF16 Helmholtz: 1 = bulk-prefetch the group's metric into L2
     int *err;                     // device error word (bounded waits that gave up set it)
+    int nfields;                  // Helmholtz: fields in0..in2 -> out0..out2 sharing the operator (1..3)
 };
+
+// Field f of a multi-field Helmholtz call.
+__device__ __forceinline__ const void *field_in(const KArgs &a, int f) { return f == 0 ? a.in0 : f == 1 ? a.in1 : a.in2; }
+__device__ __forceinline__ void *field_out(const KArgs &a, int f) { return f == 0 ? a.out0 : f == 1 ? a.out1 : a.out2; }
 
 template <class T> struct CT { using type = float; };
 template <> struct CT<double> { using type = double; };
@@ -1254,38 +1259,48 @@ __global__ void __launch_bounds__(Config<SH, N, Q, T, OP_HELM, EPB_>::NT)
                 l2_prefetch(gp + off, (unsigned)((gbytes - off) < 32768 ? (gbytes - off) : 32768));
         }
     };
-    auto issue = [&](long long g) -> int {
+    // work items: (group g, field f), the fields of a group back to back so
+    // the group's metric is read from HBM once and from L2 for later fields
+    const int nf = a.nfields > 1 ? (a.nfields < 3 ? a.nfields : 3) : 1;
+    auto issue = [&](long long g, int f) -> int {
         if (!STAGE || g >= ngroups) return 0;
         const long long e0 = g * EPB;
         if (e0 + EPB > a.nelem) return 0;
-        const T *src = in + e0 * M;
+        const T *src = reinterpret_cast<const T *>(field_in(a, f)) + e0 * M;
         const unsigned bytes = (unsigned)(EPB * M * sizeof(T));
         if ((reinterpret_cast<unsigned long long>(src) & 15) || (bytes & 15)) return 0;
         tma_load_1d(stage, src, bytes, &bar);
         return 1;
     };
+    (void)in;
     unsigned phase = 0;
-    if (threadIdx.x == 0) s_next = issue(blockIdx.x);
+    if (threadIdx.x == 0) s_next = issue(blockIdx.x, 0);
     __syncthreads();
     for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
         const long long e0 = g * EPB;
         const int ne = (int)((a.nelem - e0) < EPB ? (a.nelem - e0) : EPB);
-        const bool staged = s_next != 0;
-        if (threadIdx.x == 0) prefetch_metric(e0);
-        if (staged) {
-            if (!mbar_wait(&bar, phase, a.err)) s_fail = 1;
-            phase ^= 1u;
-            __syncthreads();
-            if (s_fail) return;  // every thread leaves together; the error word is set
-            A *B1 = buf + EPB * S;
-            for (int i = threadIdx.x; i < EPB * M; i += NT) {
-                const int e = i / M, m = i - e * M;
-                B1[e * S + m] = to_a(stage[i], A());
+        for (int f = 0; f < nf; ++f) {
+            const bool staged = s_next != 0;
+            if (threadIdx.x == 0 && f == 0) prefetch_metric(e0);
+            if (staged) {
+                if (!mbar_wait(&bar, phase, a.err)) s_fail = 1;
+                phase ^= 1u;
+                __syncthreads();
+                if (s_fail) return;  // every thread leaves together; the error word is set
+                A *B1 = buf + EPB * S;
+                for (int i = threadIdx.x; i < EPB * M; i += NT) {
+                    const int e = i / M, m = i - e * M;
+                    B1[e * S + m] = to_a(stage[i], A());
+                }
             }
+            __syncthreads();
+            if (threadIdx.x == 0)  // stage is free again: the next field, or the next group's first
+                s_next = f + 1 < nf ? issue(g, f + 1) : issue(g + gridDim.x, 0);
+            KArgs af = a;
+            af.in0 = field_in(a, f);
+            af.out0 = field_out(a, f);
+            run_group<SH, N, Q, T, OP_HELM, EPB_, 0>(af, ptab, tab, buf, e0, ne, staged);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) s_next = issue(g + gridDim.x);  // stage is free again
-        run_group<SH, N, Q, T, OP_HELM, EPB_, 0>(a, ptab, tab, buf, e0, ne, staged);
     }
 }
 
@@ -1308,19 +1323,29 @@ __global__ void __launch_bounds__(256)
     // FP32 contractions take table entries as constant-bank operands; DFMA
     // would first load them into register pairs (and the compiler hoists
     // them), so FP64 reads its tables from shared memory instead.
+    // Helmholtz fields of a group run back to back (see k_helm_tma)
+    const int nf = (OP == OP_HELM && a.nfields > 1) ? (a.nfields < 3 ? a.nfields : 3) : 1;
     if constexpr (sizeof(A) == 4) {
         const PTab<A, C::TABN> ptab{&tp, 0};
         for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
             const long long e0 = g * EPB;
             const int ne = (int)((a.nelem - e0) < EPB ? (a.nelem - e0) : EPB);
-            run_group<SH, N, Q, T, OP, EPB_, 0>(a, ptab, tab, buf, e0, ne);
+            for (int f = 0; f < nf; ++f) {
+                KArgs af = a;
+                if (nf > 1) { af.in0 = field_in(a, f); af.out0 = field_out(a, f); }
+                run_group<SH, N, Q, T, OP, EPB_, 0>(af, ptab, tab, buf, e0, ne);
+            }
         }
     } else {
         const STab<A> stab{tab};
         for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
             const long long e0 = g * EPB;
             const int ne = (int)((a.nelem - e0) < EPB ? (a.nelem - e0) : EPB);
-            run_group<SH, N, Q, T, OP, EPB_, 0>(a, stab, tab, buf, e0, ne);
+            for (int f = 0; f < nf; ++f) {
+                KArgs af = a;
+                if (nf > 1) { af.in0 = field_in(a, f); af.out0 = field_out(a, f); }
+                run_group<SH, N, Q, T, OP, EPB_, 0>(af, stab, tab, buf, e0, ne);
+            }
         }
     }
 }

@@ -170,6 +170,7 @@ int nir_mesh_block_table(nir_mesh *m, int prec, double lambda, const void *in, v
         if (rc) return rc;
         nirk::KArgs &a = h[bi].a;
         std::memset(&a, 0, sizeof(a));
+        a.nfields = 1;
         a.in0 = (const char *)in + (size_t)m->off[bi] * es;
         a.out0 = (char *)out + (size_t)m->off[bi] * es;
         a.geo = nir_geo_ptr(b, prec, false);

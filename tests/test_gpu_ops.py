@@ -325,3 +325,26 @@ def test_kernel_info_reports_the_launched_kernel(nir, ctx):
     half = blk.kernel_info("f32", "helm")["elems_per_cta"]
     blk.set_tuning("f32", 0, 0, 0)
     assert blk.kernel_info("f32", "helm")["elems_per_cta"] == 2 * half
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("shape,P", [("hex", 4), ("tet", 3), ("quad", 5), ("prism", 6)])
+def test_multi_field_helmholtz(nir, ctx, prec, shape, P):
+    """1..3 fields in one launch equal the single-field applies exactly (the
+    same per-element code), and the oracle."""
+    deformed = shape in ("hex", "quad")
+    E = 75 if P <= 4 else 37
+    g, nodes, blk = setup(nir, ctx, shape, P, E, deformed)
+    xs = [W.coefficients(E, blk.M, seed=10 + f) for f in range(3)]
+    ts = [torch.from_numpy(x).to("cuda", TDT[prec]) for x in xs]
+    for nf in (1, 2, 3):
+        outs = blk.helmholtz_fields(ts[:nf], lam=1.5, prec=prec)
+        for f in range(nf):
+            single = blk.helmholtz(ts[f], lam=1.5, prec=prec)
+            assert torch.equal(outs[f], single), (nf, f)
+    ref = oracle.helmholtz(shape, P, P + 2, g, nodes, 1.5, xs[2])
+    assert rel(outs[2].double().cpu().numpy(), ref) <= TOL[prec]
+    with pytest.raises(nir.NirError):
+        blk.helmholtz_fields(ts[:2], prec=prec, outs=[ts[2], ts[2]])  # aliased outputs
+    with pytest.raises(ValueError):
+        blk.helmholtz_fields([], prec=prec)
