@@ -62,6 +62,18 @@ struct nir_block {
     size_t stage_bytes = 0;
     cudaStream_t copy_in = nullptr, copy_out = nullptr;   // host-buffer pipeline streams
     cudaEvent_t ev_in[NIR_HOST_CHUNKS] = {}, ev_done[NIR_HOST_CHUNKS] = {};
+    // host-buffer pipelines captured as graphs (pinned host buffers only)
+    struct HostGraph {
+        int prec = 0;
+        double lambda = 0.0;
+        const void *h_in = nullptr;
+        void *h_out = nullptr;
+        unsigned long long state = 0;   // geometry version and tuning at capture
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<HostGraph> host_graphs;
+    cudaStream_t cap = nullptr;                           // capture origin of those graphs
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 int nir_launch_op(nir_block *blk, int prec, int op, double lambda, const void *in0, const void *in1,

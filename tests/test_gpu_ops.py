@@ -314,6 +314,39 @@ def test_host_buffer_pipeline_chunks(nir, ctx):
         assert torch.equal(out, ref), prec
 
 
+def test_host_buffer_graph_replay(nir, ctx):
+    """Pinned host buffers replay a captured pipeline: new host contents, a new
+    lambda, new geometry and new tuning are all honoured; pageable buffers take
+    the direct path.  Every result equals the device apply bit for bit."""
+    g, nodes, blk = setup(nir, ctx, "hex", 3, 3001, True)
+    for prec in ("f64", "f32"):
+        u = torch.from_numpy(W.coefficients(3001, blk.M, 7)).to(nir.DTYPE[prec]).pin_memory()
+        out = torch.empty_like(u).pin_memory()
+        for it in range(4):
+            lam = 1.0 if it < 3 else 2.5
+            u.add_(0.125 * (it + 1))                      # new host contents each call
+            blk.helmholtz_host(u, out, lam=lam, prec=prec)
+            ref = blk.helmholtz(u.cuda(), lam=lam, prec=prec).cpu()
+            assert torch.equal(out, ref), (prec, it)
+    u = torch.from_numpy(W.coefficients(3001, blk.M, 8)).pin_memory()
+    out = torch.empty_like(u).pin_memory()
+    blk.helmholtz_host(u, out)
+    blk.helmholtz_host(u, out)                            # replayed
+    moved = nodes.copy()
+    moved[..., 0] += 0.01 * np.sin(3.0 * nodes[..., 1])
+    blk.set_geometry(g, torch.from_numpy(np.ascontiguousarray(moved)).cuda())
+    blk.helmholtz_host(u, out)
+    assert torch.equal(out, blk.helmholtz(u.cuda()).cpu())
+    blk.set_tuning("f64", 1, 0, 0)
+    blk.helmholtz_host(u, out)
+    blk.helmholtz_host(u, out)
+    assert torch.equal(out, blk.helmholtz(u.cuda()).cpu())
+    up = torch.from_numpy(W.coefficients(3001, blk.M, 9))  # pageable
+    op = torch.empty_like(up)
+    blk.helmholtz_host(up, op)
+    assert torch.equal(op, blk.helmholtz(up.cuda()).cpu())
+
+
 def test_kernel_info_reports_the_launched_kernel(nir, ctx):
     g, nodes, blk = setup(nir, ctx, "hex", 4, 40, True)
     for prec in ("f64", "f32"):
