@@ -76,6 +76,14 @@ typedef struct nir_mesh nir_mesh;
 
 /* A block: alike elements sharing shape, order, quadrature and deformation
  * (Sec. 3.1, the block type's SEShape/Basis/Quadrature/Deformed/Size). */
+/* Expansion basis of a block.  NIR_BASIS_MODIFIED: the modified C0 expansion
+ * (every shape).  NIR_BASIS_GLL_LAGRANGE: nodal, the tensor products of the
+ * Lagrange polynomials through the P+1 Gauss-Lobatto-Legendre points
+ * (quadrilaterals and hexahedra; the nodal expansion the paper lists as
+ * future work), coefficients = values at those points, packed like the
+ * modified modes (p along xi1 outermost). */
+typedef enum { NIR_BASIS_MODIFIED = 0, NIR_BASIS_GLL_LAGRANGE = 1 } nir_basis;
+
 typedef struct {
     int shape;       /* nir_shape */
     int64_t nelem;   /* E >= 1 */
@@ -83,6 +91,7 @@ typedef struct {
     int Q;           /* quadrature points per direction (= P + 2) */
     int deformed;    /* 1: per-point geometric factors; 0: the element maps are
                         affine and quad/hex factors are stored once per element */
+    int basis;       /* nir_basis (0, the modified expansion, when zero-initialised) */
 } nir_block_desc;
 
 /* Create a context on CUDA device `device` issuing work on `cuda_stream`
@@ -100,7 +109,8 @@ int nir_ctx_check(nir_ctx *ctx);
 
 /* Create a block; builds the FP64 basis/quadrature tables (Eqs. basis matrix,
  * bwdsumfachex, bwdsumfactet, stdderiv) and uploads them.  Errors:
- * INVALID_ARG, UNSUPPORTED, NO_MEMORY, CUDA. */
+ * INVALID_ARG, UNSUPPORTED (also a nodal basis on a collapsed shape),
+ * NO_MEMORY, CUDA. */
 int nir_block_create(nir_ctx *ctx, const nir_block_desc *desc, nir_block **out);
 void nir_block_destroy(nir_block *blk);
 /* M (modes per element, Sec. 3.1 storage size) and Nq (points per element). */
@@ -274,7 +284,7 @@ typedef struct nir_asm nir_asm;
 enum { NIR_ASM_HELMHOLTZ = 0, NIR_ASM_MASS = 1 };
 
 /* Build the global numbering of conforming blocks of one shape (NIR_QUAD or
- * NIR_HEX) and one P.  vertex_ids[b]: HOST int64 array [nelem_b][2^d] of the
+ * NIR_HEX), one P and the modified basis.  vertex_ids[b]: HOST int64 array [nelem_b][2^d] of the
  * global vertex ids of block b's elements, local vertex v = a + 2b (+ 4c) at
  * reference coordinates xi = (-1+2a, -1+2b(, -1+2c)) -- the corners of the
  * geometry lattice of nir_block_set_geometry.  Elements may see shared faces

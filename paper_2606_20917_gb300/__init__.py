@@ -34,7 +34,10 @@ _vp, _i, _d, _i64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
 
 class BlockDesc(C.Structure):
     _fields_ = [("shape", C.c_int), ("nelem", C.c_int64), ("P", C.c_int), ("Q", C.c_int),
-                ("deformed", C.c_int)]
+                ("deformed", C.c_int), ("basis", C.c_int)]
+
+
+BASIS = {"modified": 0, "nodal": 1}
 
 
 class CGOpts(C.Structure):
@@ -158,11 +161,13 @@ class Block:
     """A block of alike elements (shape, P, Q = P + 2, deformed flag)."""
 
     def __init__(self, ctx: Context, shape: str, nelem: int, P: int, Q: int | None = None,
-                 deformed: bool = False):
+                 deformed: bool = False, basis: str = "modified"):
+        """basis: "modified" (every shape) or "nodal" (GLL-Lagrange, quad/hex)."""
         self.ctx, self.shape, self.nelem, self.P = ctx, shape, int(nelem), int(P)
         self.Q = int(P) + 2 if Q is None else int(Q)
         self.dim = DIM[shape]
-        d = BlockDesc(SHAPES[shape], self.nelem, self.P, self.Q, int(bool(deformed)))
+        self.basis = basis
+        d = BlockDesc(SHAPES[shape], self.nelem, self.P, self.Q, int(bool(deformed)), BASIS[basis])
         h = _vp()
         _chk(_lib.nir_block_create(ctx.h, C.byref(d), C.byref(h)), "nir_block_create")
         self.h = h

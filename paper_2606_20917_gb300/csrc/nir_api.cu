@@ -146,6 +146,7 @@ int nir_launch_op_range(nir_block *b, int prec, int op, double lambda, const voi
     a.pf = (op == nirk::OP_HELM && prec >= 0 && prec < 3) ? b->helm_pf[prec] : 0;
     a.err = b->ctx->derr;
     a.nfields = op == nirk::OP_HELM ? (in2 ? 3 : in1 ? 2 : 1) : 1;
+    a.nodal = b->d.basis == NIR_BASIS_GLL_LAGRANGE;
     // the kernel's second parameter is the table blob in its compute type
     const void *tabp = (prec == NIR_F64) ? (const void *)b->tab_h.data() : (const void *)b->tab32_h.data();
     if ((size_t)ki.tabp_bytes != (prec == NIR_F64 ? b->tab_h.size() * 8 : b->tab32_h.size() * 4))
@@ -222,6 +223,8 @@ extern "C" int nir_block_create(nir_ctx *ctx, const nir_block_desc *d, nir_block
     *out = nullptr;
     if (d->shape < NIR_QUAD || d->shape > NIR_TET || d->nelem < 1) return NIR_ERR_INVALID_ARG;
     if (d->P < 1 || d->P > 8 || d->Q != d->P + 2) return NIR_ERR_UNSUPPORTED;
+    if (d->basis != NIR_BASIS_MODIFIED && d->basis != NIR_BASIS_GLL_LAGRANGE) return NIR_ERR_INVALID_ARG;
+    if (d->basis == NIR_BASIS_GLL_LAGRANGE && d->shape != NIR_QUAD && d->shape != NIR_HEX) return NIR_ERR_UNSUPPORTED;
     nir_block *b = new (std::nothrow) nir_block();
     if (!b) return NIR_ERR_NO_MEMORY;
     b->ctx = ctx;
@@ -236,7 +239,7 @@ extern "C" int nir_block_create(nir_ctx *ctx, const nir_block_desc *d, nir_block
     b->geo_pp = (d->deformed || d->shape == NIR_TRI || d->shape == NIR_TET || d->shape == NIR_PRISM) ? 1 : 0;
     const int ntab = nirb_table_size(d->shape, d->P, d->Q);
     b->tab_h.assign(ntab, 0.0);
-    if (!nirb_build_tables(d->shape, d->P, d->Q, b->tab_h.data())) {
+    if (!nirb_build_tables(d->shape, d->P, d->Q, b->tab_h.data(), d->basis)) {
         delete b;
         return NIR_ERR_CUDA;
     }

@@ -635,6 +635,7 @@ extern "C" int nir_asm_create(nir_ctx *ctx, nir_block *const *blocks, const int6
     for (int i = 0; i < nblocks; ++i) {
         if (!blocks[i] || !vertex_ids[i] || blocks[i]->ctx != ctx) return NIR_ERR_INVALID_ARG;
         if (blocks[i]->d.shape != shape || blocks[i]->d.P != blocks[0]->d.P) return NIR_ERR_UNSUPPORTED;
+        if (blocks[i]->d.basis != NIR_BASIS_MODIFIED) return NIR_ERR_UNSUPPORTED;
     }
     if (blocks[0]->d.P < 1) return NIR_ERR_UNSUPPORTED;
     NIR_CUDA_TRY(cudaSetDevice(ctx->device));

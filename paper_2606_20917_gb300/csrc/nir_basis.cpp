@@ -244,17 +244,42 @@ bool nirb_shape_rules(int shape, int Q, double *z /*[3][Q]*/, double *w /*[3][Q]
     return true;
 }
 
-bool nirb_build_tables(int shape, int P, int Q, double *blob)
+// Nodal (GLL-Lagrange) basis seen through its reflection pairs: with l_j the
+// Lagrange polynomials through the N GLL points, mode 0 is l_0, mode 1 is
+// l_{N-1}, modes 2k and 2k+1 (k = 1 .. (N-2)/2) are (l_k + l_{N-1-k})/2 and
+// (l_k - l_{N-1-k})/2, and for odd N mode N-1 is the middle l_{(N-1)/2}.  These
+// have the modified basis' symmetry (0 <-> 1 under z -> -z, mode p with
+// parity (-1)^p), so the even/odd contractions apply unchanged; nodal
+// coefficients are mapped to and from this form in the kernels.
+double nirb_nodal_pair(int p, int N, double z)
+{
+    std::vector<double> x(N), w(N);
+    nirb_gll(N, x.data(), w.data());
+    auto lag = [&](int j) {
+        double v = 1.0;
+        for (int m = 0; m < N; ++m)
+            if (m != j) v *= (z - x[m]) / (x[j] - x[m]);
+        return v;
+    };
+    if (p == 0) return lag(0);
+    if (p == 1) return lag(N - 1);
+    if (N % 2 == 1 && p == N - 1) return lag((N - 1) / 2);
+    const int k = p / 2;
+    return (p % 2 == 0) ? 0.5 * (lag(k) + lag(N - 1 - k)) : 0.5 * (lag(k) - lag(N - 1 - k));
+}
+
+bool nirb_build_tables(int shape, int P, int Q, double *blob, int basis)
 {
     using namespace nirk;
     const int N = P + 1;
     const TabLayout L = layout(shape, N, Q);
     std::vector<double> z(3 * Q), w(3 * Q);
     if (!nirb_shape_rules(shape, Q, z.data(), w.data())) return false;
+    if (basis != 0 && shape != QUAD && shape != HEX) return false;
     std::memset(blob, 0, sizeof(double) * L.total);
     const double *z1 = z.data(), *z2 = z.data() + Q, *z3 = z.data() + 2 * Q;
     for (int k = 0; k < Q; ++k)
-        for (int r = 0; r < N; ++r) blob[L.Ba + k * N + r] = nirb_psiA(r, z1[k]);
+        for (int r = 0; r < N; ++r) blob[L.Ba + k * N + r] = basis ? nirb_nodal_pair(r, N, z1[k]) : nirb_psiA(r, z1[k]);
     if (shape == TRI || shape == TET || shape == PRISM) {
         const double *zb = (shape == PRISM) ? z3 : z2;
         for (int p = 0; p < N; ++p) {

@@ -15,6 +15,8 @@ void nirb_colloc(int Q, const double *z, double *D);
 void nirb_lagrange_equi(int g, int Q, const double *z, double *L, double *dL);
 // Per-direction points and weights of a shape (collapse factors in w).
 bool nirb_shape_rules(int shape, int Q, double *z /*[3][Q]*/, double *w /*[3][Q]*/);
-// Fill the kernel table blob (layout in nir_layout.h) in FP64.
-bool nirb_build_tables(int shape, int P, int Q, double *blob);
+// Fill the kernel table blob (layout in nir_layout.h) in FP64; basis 0: the
+// modified expansion, 1: GLL-Lagrange in reflection-pair form (quad/hex).
+bool nirb_build_tables(int shape, int P, int Q, double *blob, int basis);
+double nirb_nodal_pair(int p, int N, double z);
 int nirb_table_size(int shape, int P, int Q);

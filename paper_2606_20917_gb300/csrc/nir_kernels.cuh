@@ -53,6 +53,7 @@ struct KArgs {
     int pf;                       // FP32/BF16 Helmholtz: 1 = bulk-prefetch the group's metric into L2
     int *err;                     // device error word (bounded waits that gave up set it)
     int nfields;                  // Helmholtz: fields in0..in2 -> out0..out2 sharing the operator (1..3)
+    int nodal;                    // quad/hex: coefficients are GLL-Lagrange nodal values
 };
 
 // Field f of a multi-field Helmholtz call.
@@ -990,6 +991,61 @@ __device__ __forceinline__ void helm_metric(const Geo<T, A, NQ, NG> &geo, long l
     }
 }
 
+// Nodal (GLL-Lagrange) coefficients of a quad/hex and the reflection-pair
+// form the contraction tables are built for (see the table builder): along
+// each direction, pair k = 1 .. (N-2)/2 of nodes (k, N-1-k) becomes
+// (x_k + x_{N-1-k}, x_k - x_{N-1-k}) in slots (2k, 2k+1), the end nodes go to
+// slots 0 and 1 and an odd N's middle node to slot N-1.  to_pairs maps nodal
+// input coefficients into that form; otherwise it maps inner products taken
+// against the pair functions back to nodal ones (the inverse transpose, which
+// for these 2x2 blocks is the sum/difference without the factor 1/2).
+// In place on the group's modal block (element stride S), one direction per
+// pass.
+template <int SH, int N, class A, int EPB, int NT, int S>
+__device__ __forceinline__ void nodal_pairs(A *buf, bool to_pairs)
+{
+    if constexpr ((SH == QUAD || SH == HEX) && N > 2) {
+        constexpr int D = dim(SH);
+        constexpr int LINES = D == 2 ? N : N * N;
+        constexpr int K = (N - 2) / 2;
+        for (int dir = 0; dir < D; ++dir) {
+            const int stride = D == 2 ? (dir == 0 ? N : 1) : (dir == 0 ? N * N : dir == 1 ? N : 1);
+            for (int w = threadIdx.x; w < EPB * LINES; w += NT) {
+                const int e = w % EPB, l = w / EPB;
+                int base;
+                if constexpr (D == 2) base = dir == 0 ? l : l * N;
+                else base = dir == 0 ? l : dir == 1 ? (l / N) * N * N + (l % N) : l * N;
+                A *v = buf + e * S + base;
+                A x[N], y[N];
+#pragma unroll
+                for (int r = 0; r < N; ++r) x[r] = v[r * stride];
+                if (to_pairs) {
+                    y[0] = x[0];
+                    y[1] = x[N - 1];
+#pragma unroll
+                    for (int k = 1; k <= K; ++k) {
+                        y[2 * k] = x[k] + x[N - 1 - k];
+                        y[2 * k + 1] = x[k] - x[N - 1 - k];
+                    }
+                    if constexpr (N % 2 == 1) y[N - 1] = x[(N - 1) / 2];
+                } else {
+                    y[0] = x[0];
+                    y[N - 1] = x[1];
+#pragma unroll
+                    for (int k = 1; k <= K; ++k) {
+                        y[k] = x[2 * k] + x[2 * k + 1];
+                        y[N - 1 - k] = x[2 * k] - x[2 * k + 1];
+                    }
+                    if constexpr (N % 2 == 1) y[(N - 1) / 2] = x[N - 1];
+                }
+#pragma unroll
+                for (int r = 0; r < N; ++r) v[r * stride] = y[r];
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // One group of ne (<= EPB) elements starting at e0: the whole operator.
 // tab: the block's tables in shared memory; buf: NBUF * EPB * S values.
 // TP: table accessor for the contractions (STab or PTab); tab: the same
@@ -1010,9 +1066,17 @@ __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename 
     const A *D0 = tab + L.D1, *D1 = tab + L.D2, *D2 = tab + L.D3;
     const Geo<T, A, NQ, NG> geo{reinterpret_cast<const T *>(a.geo), tab + L.wq, a.geo_pp};
 
+    constexpr bool TENSOR = SH == QUAD || SH == HEX;
+    auto to_pairs = [&](A *blk) {
+        if constexpr (TENSOR) { if (a.nodal) nodal_pairs<SH, N, A, EPB, NT, S>(blk, true); }
+    };
+    auto from_pairs = [&](A *blk) {
+        if constexpr (TENSOR) { if (a.nodal) nodal_pairs<SH, N, A, EPB, NT, S>(blk, false); }
+    };
     if constexpr (OP == OP_BWD) {
         gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
         __syncthreads();
+        to_pairs(B0);
         if constexpr (D == 2) {
             MD::bwd(tp, B0, B1, B0, nullptr);
             gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B0);
@@ -1028,6 +1092,7 @@ __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename 
         } else {
             gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
             __syncthreads();
+            to_pairs(B0);
             if constexpr (D == 2) MD::bwd(tp, B0, B1, B0, nullptr);
             else { MD::bwd(tp, B0, B1, B0, B1); P = B1; }
         }
@@ -1039,9 +1104,11 @@ __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename 
         A *O = (P == B0) ? B1 : B0;
         if constexpr (D == 2) {
             MD::iprod(tp, P, O, nullptr, P);
+            from_pairs(P);
             gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, P);
         } else {
             MD::iprod(tp, P, O, P, O);
+            from_pairs(O);
             gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, O);
         }
     } else if constexpr (OP == OP_PHYSDERIV) {
@@ -1098,9 +1165,11 @@ __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename 
         __syncthreads();
         if constexpr (D == 2) {
             MD::iprod(tp, B0, B1, nullptr, B2);
+            from_pairs(B2);
             gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B2);
         } else {
             MD::iprod(tp, B0, B1, B2, B1);
+            from_pairs(B1);
             gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
         }
     } else if constexpr (sizeof(A) == 8) {  // OP_HELM, FP64: point-wise gradient flow
@@ -1108,6 +1177,7 @@ __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename 
         // busy across barriers better than whole pencils)
         gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B1);
         __syncthreads();
+        to_pairs(B1);
         if constexpr (D == 2) MD::bwd(tp, B1, B2, B0, nullptr);
         else MD::bwd(tp, B1, B2, B1, B0);
         // v_i = sum_j G_ij du_j  (G includes W and the chain rule)
@@ -1125,9 +1195,11 @@ __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename 
         __syncthreads();
         if constexpr (D == 2) {
             MD::iprod(tp, B0, B1, nullptr, B2);
+            from_pairs(B2);
             gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B2);
         } else {
             MD::iprod(tp, B0, B1, B2, B1);
+            from_pairs(B1);
             gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
         }
     } else {  // OP_HELM, FP32 / BF16: fused register-blocked pencils
@@ -1136,6 +1208,7 @@ __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename 
             gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B1);
             __syncthreads();
         }
+        to_pairs(B1);
         if constexpr (D == 2) {
             // B1 modes -> B2 t1 -> U = B0, V1 = B1, V2 = B2
             MD::front(tp, B1, B2, nullptr);
@@ -1156,6 +1229,7 @@ __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename 
             HS::t1_first(tp, B0, B2, B1);
             MD::back(tp, B1, B2, B0);
         }
+        from_pairs(B0);
         gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B0);
     }
     __syncthreads();

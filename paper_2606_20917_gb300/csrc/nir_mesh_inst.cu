@@ -108,10 +108,16 @@ __device__ __noinline__ void run_item(const MeshBlk &mb, const MeshItem &m, unsi
         const long long left = mb.a.nelem - e0;
         const int ne = (int)(left < C::EPB ? left : C::EPB);
 #if NIR_PREC != 0
+        // the constant tables hold the modified basis' tables of the variant;
+        // a nodal-basis block reads its own tables from shared memory
         if constexpr (use_ctab(SH, N)) {
-            constexpr TabLayout L = layout(SH, N, N + 1);
-            using CT = CTab<ctab_base<VID>(), L.wq, npts(SH, N + 1)>;
-            run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, CT{0}, tab, buf, e0, ne);
+            if (!mb.a.nodal) {
+                constexpr TabLayout L = layout(SH, N, N + 1);
+                using CT = CTab<ctab_base<VID>(), L.wq, npts(SH, N + 1)>;
+                run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, CT{0}, tab, buf, e0, ne);
+            } else {
+                run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, STab<A>{tab}, tab, buf, e0, ne);
+            }
         } else {
             run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, STab<A>{tab}, tab, buf, e0, ne);
         }

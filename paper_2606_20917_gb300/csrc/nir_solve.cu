@@ -74,7 +74,8 @@ int nir_mesh_build_items(nir_mesh *m, int prec, int gran)
         ps.nt = k.nt;
         ps.smem = std::max(ps.smem, k.smem);
         ps.vid[bi] = k.vid;
-        if (prec != NIR_F64) {  // constant tables of the FP32/BF16 kernel (same for all blocks of a variant)
+        if (prec != NIR_F64 && b->d.basis == NIR_BASIS_MODIFIED) {  // constant tables of the FP32/BF16 kernel
+            // (the modified basis' tables depend on (shape, P) only: shared by the variant's blocks)
             int rc = nir_mesh_tables(m->dim, prec, k.vid, b->tab32_h.data(), (int)b->tab32_h.size(), m->ctx->stream);
             if (rc) return rc;
         }
@@ -171,6 +172,7 @@ int nir_mesh_block_table(nir_mesh *m, int prec, double lambda, const void *in, v
         nirk::KArgs &a = h[bi].a;
         std::memset(&a, 0, sizeof(a));
         a.nfields = 1;
+        a.nodal = b->d.basis == NIR_BASIS_GLL_LAGRANGE;
         a.in0 = (const char *)in + (size_t)m->off[bi] * es;
         a.out0 = (char *)out + (size_t)m->off[bi] * es;
         a.geo = nir_geo_ptr(b, prec, false);
