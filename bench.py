@@ -250,9 +250,12 @@ def run_reference(args, ws, rank):
 
 def workload_config(args, wl):
     E = wl["nodes"].shape[0]
-    return {"workload": args.workload, "shape": wl["shape"], "nelem": E, "P": wl["P"], "Q": wl["Q"],
-            "geometry": "curved (per-point factors)" if wl["deformed"] else "affine",
-            "lambda": 1.0, "precision": args.prec}
+    cfg = {"workload": args.workload, "shape": wl["shape"], "nelem": E, "P": wl["P"], "Q": wl["Q"],
+           "geometry": "curved (per-point factors)" if wl["deformed"] else "affine",
+           "lambda": 1.0, "precision": args.prec}
+    if getattr(args, "basis", "modified") != "modified":
+        cfg["basis"] = "GLL-Lagrange (nodal)"
+    return cfg
 
 
 def cpu_baseline(args, wl, budget_s: float = 15.0):
@@ -286,7 +289,7 @@ def run_nir(args, ws, rank, local):
     wl = W.workload(args.workload)
     shape, P, Q, g = wl["shape"], wl["P"], wl["Q"], wl["gorder"]
     E = wl["nodes"].shape[0]
-    blk = nir.Block(ctx, shape, E, P, deformed=wl["deformed"])
+    blk = nir.Block(ctx, shape, E, P, deformed=wl["deformed"], basis=args.basis)
     blk.set_geometry(g, torch.from_numpy(wl["nodes"]).to(dev))
     if not args.no_tune:
         # set-up, untimed: the library's autotuner picks elements per CTA, grid
@@ -801,6 +804,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-operators", action="store_true", help="skip the per-operator table")
     ap.add_argument("--mode", choices=["apply", "solve", "gsolve", "hybrid", "sweep"], default="apply")
+    ap.add_argument("--basis", choices=["modified", "nodal"], default="modified",
+                    help="apply mode: expansion basis (nodal = GLL-Lagrange, quad/hex)")
     ap.add_argument("--sweep-shapes", default="hex,tet")
     ap.add_argument("--sweep-dofs", default="1e5,1e6,1e7,3e7")
     ap.add_argument("--solve-precs", default="f64,f32,bf16")
