@@ -193,7 +193,8 @@ int nir_helmholtz_host_noalloc(nir_block *blk, int prec, double lambda, const vo
 
 /* Launch tuning of a block's Helmholtz kernel in one precision (what nir_tune
  * sets): variant 0 = default elements per CTA, 1 = half, 2 = double (where it
- * fits in shared memory; otherwise the default); grid = CTAs launched (0: one
+ * fits in shared memory; otherwise the default), 3 = the default group run by
+ * the multi-field kernel (same results, another register allocation); grid = CTAs launched (0: one
  * wave at the kernel's occupancy); pf = 1 to prefetch each group's metric to
  * L2 (FP32/BF16 with per-point factors; ignored elsewhere).  Errors:
  * INVALID_ARG. */

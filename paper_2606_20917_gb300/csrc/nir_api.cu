@@ -105,10 +105,15 @@ int nir_launch_op_range(nir_block *b, int prec, int op, double lambda, const voi
                         cudaStream_t stream, int grid_override)
 {
     if (e_begin < 0 || e_count < 1 || e_begin + e_count > b->d.nelem || (e_begin & 63)) return NIR_ERR_INVALID_ARG;
-    int variant = (op == nirk::OP_HELM && prec >= 0 && prec < 3) ? b->helm_variant[prec] : 0;
+    const bool multi = op == nirk::OP_HELM && in1 != nullptr;  // a multi-field Helmholtz call
+    int variant = (op == nirk::OP_HELM && prec >= 0 && prec < 3 && !multi) ? b->helm_variant[prec] : 0;
     KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, op, variant);
     if (!ki.fn) ki = nir_kinfo(b->d.shape, b->d.P, prec, op, 0);
     if (!ki.fn) return NIR_ERR_UNSUPPORTED;
+    if (multi) {  // the multi-field form of the default variant
+        if (!ki.fn_fields) return NIR_ERR_UNSUPPORTED;
+        ki.fn = ki.fn_fields;
+    }
     int rc = nir_block_ensure_prec(b, prec);
     if (rc) return rc;
     int occ = nir_occupancy(b->ctx, ki);
@@ -675,7 +680,7 @@ extern "C" int nir_helmholtz_host(nir_block *b, int prec, double lambda, const v
 // --------------------------------------------------------------------------- probe / misc
 extern "C" int nir_block_set_tuning(nir_block *b, int prec, int variant, int grid, int pf)
 {
-    if (!b || !valid_prec(prec) || variant < 0 || variant > 2 || grid < 0 || (pf != 0 && pf != 1))
+    if (!b || !valid_prec(prec) || variant < 0 || variant > 3 || grid < 0 || (pf != 0 && pf != 1))
         return NIR_ERR_INVALID_ARG;
     b->helm_variant[prec] = variant;
     b->helm_grid[prec] = grid;

@@ -30,9 +30,13 @@ KInfo make1()
     if constexpr (C::FUSED) {  // FP32/BF16 Helmholtz: bulk-copy staged kernel
         constexpr int stg = STAGE ? ((C::EPB * C::M * (int)sizeof(TT) + 15) / 16) * 16 : 0;
         k.fn = reinterpret_cast<const void *>(&k_helm_tma<NIR_SHAPE, N, N + 1, TT, EPB, STAGE>);
+        if constexpr (EPB == 0 && STAGE)
+            k.fn_fields = reinterpret_cast<const void *>(&k_helm_tma<NIR_SHAPE, N, N + 1, TT, 0, true, true>);
         k.smem = C::SMEM + stg;
     } else {
         k.fn = reinterpret_cast<const void *>(&k_elem<NIR_SHAPE, N, N + 1, TT, OP, EPB>);
+        if constexpr (EPB == 0 && OP == OP_HELM)
+            k.fn_fields = reinterpret_cast<const void *>(&k_elem<NIR_SHAPE, N, N + 1, TT, OP, 0, true>);
         k.smem = C::SMEM;
     }
     k.epb = C::EPB;
@@ -43,7 +47,9 @@ KInfo make1()
 
 // Variant 0: default elements per CTA; 1: half; 2: double (when it fits in
 // 227 KB of shared memory; an FP32/BF16 double group that fits only without
-// its staging buffer loads its coefficients itself).  Only the Helmholtz
+// its staging buffer loads its coefficients itself); 3: the default group run
+// by the multi-field kernel with one field (the compiler allocates its
+// registers differently, which wins at some orders).  Only the Helmholtz
 // operator has variants.
 template <int N, int OP>
 KInfo make(int variant)
@@ -60,6 +66,12 @@ KInfo make(int variant)
         if (variant == 2) {
             if constexpr (fits_unstaged) return make1<N, OP, ed, false>();
             else return make1<N, OP, ed>();
+        }
+        if (variant == 3) {  // default group through the multi-field code: another register allocation
+            KInfo k = make1<N, OP, 0>();
+            if (!k.fn_fields) return KInfo{};
+            k.fn = k.fn_fields;
+            return k;
         }
     }
     if (variant != 0) return KInfo{};

@@ -25,6 +25,7 @@ struct KInfo {
     int epb = 0;               // elements per CTA group
     int nt = 0;                // threads per CTA
     int tabp_bytes = 0;        // size of the table parameter (compute type)
+    const void *fn_fields = nullptr;  // Helmholtz, default variant: the multi-field form
 };
 
 // Provided by the instantiation units (one per shape x precision).

@@ -1002,7 +1002,7 @@ __device__ __forceinline__ void helm_metric(const Geo<T, A, NQ, NG> &geo, long l
 // In place on the group's modal block (element stride S), one direction per
 // pass.
 template <int SH, int N, class A, int EPB, int NT, int S>
-__device__ __forceinline__ void nodal_pairs(A *buf, bool to_pairs)
+__device__ __noinline__ void nodal_pairs(A *buf, bool to_pairs)  // out of line: modified-basis kernels only carry a call
 {
     if constexpr ((SH == QUAD || SH == HEX) && N > 2) {
         constexpr int D = dim(SH);
@@ -1051,9 +1051,12 @@ __device__ __forceinline__ void nodal_pairs(A *buf, bool to_pairs)
 // TP: table accessor for the contractions (STab or PTab); tab: the same
 // tables in shared memory (collocation gathers of PhysDeriv and
 // IProductWRTDerivBase, reference weights).
+// fin/fout: the group's first input and output arrays (a field of a
+// multi-field Helmholtz call; a.in0 / a.out0 otherwise).
 template <int SH, int N, int Q, class T, int OP, int EPB_, int NT_, class TP>
-__device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename CT<T>::type *tab,
-                                          typename CT<T>::type *buf, long long e0, int ne, bool staged = false)
+__device__ __forceinline__ void run_group(const KArgs &a, const void *fin, void *fout, TP tp,
+                                          const typename CT<T>::type *tab, typename CT<T>::type *buf, long long e0,
+                                          int ne, bool staged = false)
 {
     using C = Config<SH, N, Q, T, OP, EPB_, NT_>;
     using A = typename C::A;
@@ -1074,23 +1077,23 @@ __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename 
         if constexpr (TENSOR) { if (a.nodal) nodal_pairs<SH, N, A, EPB, NT, S>(blk, false); }
     };
     if constexpr (OP == OP_BWD) {
-        gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
+        gload<T, A, M, S, NT>(reinterpret_cast<const T *>(fin), e0, ne, B0);
         __syncthreads();
         to_pairs(B0);
         if constexpr (D == 2) {
             MD::bwd(tp, B0, B1, B0, nullptr);
-            gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B0);
+            gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(fout), e0, ne, B0);
         } else {
             MD::bwd(tp, B0, B1, B0, B1);
-            gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
+            gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(fout), e0, ne, B1);
         }
     } else if constexpr (OP == OP_IPROD || OP == OP_MASS) {
         A *P = B0;
         if constexpr (OP == OP_IPROD) {
-            gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
+            gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(fin), e0, ne, B0);
             __syncthreads();
         } else {
-            gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
+            gload<T, A, M, S, NT>(reinterpret_cast<const T *>(fin), e0, ne, B0);
             __syncthreads();
             to_pairs(B0);
             if constexpr (D == 2) MD::bwd(tp, B0, B1, B0, nullptr);
@@ -1105,14 +1108,14 @@ __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename 
         if constexpr (D == 2) {
             MD::iprod(tp, P, O, nullptr, P);
             from_pairs(P);
-            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, P);
+            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(fout), e0, ne, P);
         } else {
             MD::iprod(tp, P, O, P, O);
             from_pairs(O);
-            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, O);
+            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(fout), e0, ne, O);
         }
     } else if constexpr (OP == OP_PHYSDERIV) {
-        gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B0);
+        gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(fin), e0, ne, B0);
         __syncthreads();
         A *Vs[3] = {B1, B2, B3};
         for (int w = threadIdx.x; w < EPB * NQ; w += NT) {
@@ -1132,11 +1135,11 @@ __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename 
             }
         }
         __syncthreads();
-        gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
+        gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(fout), e0, ne, B1);
         gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out1), e0, ne, B2);
         if constexpr (D == 3) gstore<T, A, NQ, S, NT>(reinterpret_cast<T *>(a.out2), e0, ne, B3);
     } else if constexpr (OP == OP_IPROD_DERIV) {
-        gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B1);
+        gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(fin), e0, ne, B1);
         gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in1), e0, ne, B2);
         if constexpr (D == 3) gload<T, A, NQ, S, NT>(reinterpret_cast<const T *>(a.in2), e0, ne, B3);
         __syncthreads();
@@ -1166,16 +1169,16 @@ __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename 
         if constexpr (D == 2) {
             MD::iprod(tp, B0, B1, nullptr, B2);
             from_pairs(B2);
-            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B2);
+            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(fout), e0, ne, B2);
         } else {
             MD::iprod(tp, B0, B1, B2, B1);
             from_pairs(B1);
-            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
+            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(fout), e0, ne, B1);
         }
     } else if constexpr (sizeof(A) == 8) {  // OP_HELM, FP64: point-wise gradient flow
         // (the FP64 pipe is the bound; fine-grained point work items keep it
         // busy across barriers better than whole pencils)
-        gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B1);
+        gload<T, A, M, S, NT>(reinterpret_cast<const T *>(fin), e0, ne, B1);
         __syncthreads();
         to_pairs(B1);
         if constexpr (D == 2) MD::bwd(tp, B1, B2, B0, nullptr);
@@ -1196,16 +1199,16 @@ __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename 
         if constexpr (D == 2) {
             MD::iprod(tp, B0, B1, nullptr, B2);
             from_pairs(B2);
-            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B2);
+            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(fout), e0, ne, B2);
         } else {
             MD::iprod(tp, B0, B1, B2, B1);
             from_pairs(B1);
-            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B1);
+            gstore<T, A, M, S, NT>(reinterpret_cast<T *>(fout), e0, ne, B1);
         }
     } else {  // OP_HELM, FP32 / BF16: fused register-blocked pencils
         const A lam = A(a.lambda);
         if (!staged) {  // otherwise the caller has already put the coefficients in B1
-            gload<T, A, M, S, NT>(reinterpret_cast<const T *>(a.in0), e0, ne, B1);
+            gload<T, A, M, S, NT>(reinterpret_cast<const T *>(fin), e0, ne, B1);
             __syncthreads();
         }
         to_pairs(B1);
@@ -1230,7 +1233,7 @@ __device__ __forceinline__ void run_group(const KArgs &a, TP tp, const typename 
             MD::back(tp, B1, B2, B0);
         }
         from_pairs(B0);
-        gstore<T, A, M, S, NT>(reinterpret_cast<T *>(a.out0), e0, ne, B0);
+        gstore<T, A, M, S, NT>(reinterpret_cast<T *>(fout), e0, ne, B0);
     }
     __syncthreads();
 }
@@ -1296,7 +1299,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 // with plain coalesced loads.
 // STAGE = false: no staging buffer (coefficients loaded by the group itself),
 // for groups whose buffers alone nearly fill shared memory.
-template <int SH, int N, int Q, class T, int EPB_ = 0, bool STAGE = true>
+// MULTI: the multi-field form (1..3 fields per group, a.nfields); the
+// single-field form is a separate instantiation so its code and register
+// allocation do not carry the field loop.
+template <int SH, int N, int Q, class T, int EPB_ = 0, bool STAGE = true, bool MULTI = false>
 __global__ void __launch_bounds__(Config<SH, N, Q, T, OP_HELM, EPB_>::NT)
     k_helm_tma(KArgs a, const __grid_constant__ TabP<typename CT<T>::type, layout(SH, N, Q).total> tp)
 {
@@ -1335,7 +1341,7 @@ __global__ void __launch_bounds__(Config<SH, N, Q, T, OP_HELM, EPB_>::NT)
     };
     // work items: (group g, field f), the fields of a group back to back so
     // the group's metric is read from HBM once and from L2 for later fields
-    const int nf = a.nfields > 1 ? (a.nfields < 3 ? a.nfields : 3) : 1;
+    const int nf = (MULTI && a.nfields > 1) ? (a.nfields < 3 ? a.nfields : 3) : 1;
     auto issue = [&](long long g, int f) -> int {
         if (!STAGE || g >= ngroups) return 0;
         const long long e0 = g * EPB;
@@ -1370,10 +1376,8 @@ __global__ void __launch_bounds__(Config<SH, N, Q, T, OP_HELM, EPB_>::NT)
             __syncthreads();
             if (threadIdx.x == 0)  // stage is free again: the next field, or the next group's first
                 s_next = f + 1 < nf ? issue(g, f + 1) : issue(g + gridDim.x, 0);
-            KArgs af = a;
-            af.in0 = field_in(a, f);
-            af.out0 = field_out(a, f);
-            run_group<SH, N, Q, T, OP_HELM, EPB_, 0>(af, ptab, tab, buf, e0, ne, staged);
+            run_group<SH, N, Q, T, OP_HELM, EPB_, 0>(a, field_in(a, f), field_out(a, f), ptab, tab, buf, e0, ne,
+                                                     staged);
         }
     }
 }
@@ -1381,7 +1385,7 @@ __global__ void __launch_bounds__(Config<SH, N, Q, T, OP_HELM, EPB_>::NT)
 // Persistent single-block kernel: CTAs stride over the element groups.  The
 // tables arrive twice: as a __grid_constant__ parameter (constant bank, used
 // by the contractions) and copied once into shared memory (gathers, weights).
-template <int SH, int N, int Q, class T, int OP, int EPB_ = 0>
+template <int SH, int N, int Q, class T, int OP, int EPB_ = 0, bool MULTI = false>
 __global__ void __launch_bounds__(256)
     k_elem(KArgs a, const __grid_constant__ TabP<typename CT<T>::type, layout(SH, N, Q).total> tp)
 {
@@ -1398,28 +1402,22 @@ __global__ void __launch_bounds__(256)
     // would first load them into register pairs (and the compiler hoists
     // them), so FP64 reads its tables from shared memory instead.
     // Helmholtz fields of a group run back to back (see k_helm_tma)
-    const int nf = (OP == OP_HELM && a.nfields > 1) ? (a.nfields < 3 ? a.nfields : 3) : 1;
+    const int nf = (MULTI && OP == OP_HELM && a.nfields > 1) ? (a.nfields < 3 ? a.nfields : 3) : 1;
     if constexpr (sizeof(A) == 4) {
         const PTab<A, C::TABN> ptab{&tp, 0};
         for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
             const long long e0 = g * EPB;
             const int ne = (int)((a.nelem - e0) < EPB ? (a.nelem - e0) : EPB);
-            for (int f = 0; f < nf; ++f) {
-                KArgs af = a;
-                if (nf > 1) { af.in0 = field_in(a, f); af.out0 = field_out(a, f); }
-                run_group<SH, N, Q, T, OP, EPB_, 0>(af, ptab, tab, buf, e0, ne);
-            }
+            for (int f = 0; f < nf; ++f)
+                run_group<SH, N, Q, T, OP, EPB_, 0>(a, field_in(a, f), field_out(a, f), ptab, tab, buf, e0, ne);
         }
     } else {
         const STab<A> stab{tab};
         for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
             const long long e0 = g * EPB;
             const int ne = (int)((a.nelem - e0) < EPB ? (a.nelem - e0) : EPB);
-            for (int f = 0; f < nf; ++f) {
-                KArgs af = a;
-                if (nf > 1) { af.in0 = field_in(a, f); af.out0 = field_out(a, f); }
-                run_group<SH, N, Q, T, OP, EPB_, 0>(af, stab, tab, buf, e0, ne);
-            }
+            for (int f = 0; f < nf; ++f)
+                run_group<SH, N, Q, T, OP, EPB_, 0>(a, field_in(a, f), field_out(a, f), stab, tab, buf, e0, ne);
         }
     }
 }

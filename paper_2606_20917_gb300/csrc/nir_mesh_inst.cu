@@ -114,15 +114,15 @@ __device__ __noinline__ void run_item(const MeshBlk &mb, const MeshItem &m, unsi
             if (!mb.a.nodal) {
                 constexpr TabLayout L = layout(SH, N, N + 1);
                 using CT = CTab<ctab_base<VID>(), L.wq, npts(SH, N + 1)>;
-                run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, CT{0}, tab, buf, e0, ne);
+                run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, mb.a.in0, mb.a.out0, CT{0}, tab, buf, e0, ne);
             } else {
-                run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, STab<A>{tab}, tab, buf, e0, ne);
+                run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, mb.a.in0, mb.a.out0, STab<A>{tab}, tab, buf, e0, ne);
             }
         } else {
-            run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, STab<A>{tab}, tab, buf, e0, ne);
+            run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, mb.a.in0, mb.a.out0, STab<A>{tab}, tab, buf, e0, ne);
         }
 #else
-        run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, STab<A>{tab}, tab, buf, e0, ne);
+        run_group<SH, N, N + 1, TT, OP_HELM, 0, kMeshNT>(mb.a, mb.a.in0, mb.a.out0, STab<A>{tab}, tab, buf, e0, ne);
 #endif
     }
 }

@@ -500,9 +500,9 @@ extern "C" int nir_tune(nir_mesh *m, const char *cache_path)
             }
             float best = 1e30f;
             int bv = 0, bg = 0, bp = 0;
-            for (int v = 0; v < 3 && !rc; ++v) {
+            for (int v = 0; v < 4 && !rc; ++v) {
                 KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, 5, v);
-                if (!ki.fn || (v > 0 && ki.epb == nir_kinfo(b->d.shape, b->d.P, prec, 5, 0).epb)) continue;
+                if (!ki.fn || ((v == 1 || v == 2) && ki.epb == nir_kinfo(b->d.shape, b->d.P, prec, 5, 0).epb)) continue;
                 int occ = nir_occupancy(ctx, ki);
                 const int npf = (prec != NIR_F64 && b->geo_pp && (ki.epb % 32 == 0 || 32 % ki.epb == 0)) ? 2 : 1;
                 for (int c = 1; c <= std::max(1, occ) && !rc; ++c)

@@ -195,15 +195,19 @@ def test_helmholtz_every_launch_variant(nir, ctx, prec, shape, P):
     g, nodes, blk = setup(nir, ctx, shape, P, E, deformed)
     x = inputs(blk, "helm")
     ref = oracle_op(shape, P, g, nodes, "helm", x, 1.0)
-    for variant in (0, 1, 2):
+    for variant in (0, 1, 2, 3):
         for pf in (0, 1):
             for grid in (0, 152):
                 blk.set_tuning(prec, variant, grid, pf)
                 got = run_op(blk, "helm", prec, x, 1.0)
                 assert rel(got, ref) <= TOL[prec], (variant, pf, grid, rel(got, ref))
-    assert blk.get_tuning(prec) == (2, 152, 1)
+    assert blk.get_tuning(prec) == (3, 152, 1)
+    blk.set_tuning(prec, 0, 0, 0)
+    y0 = run_op(blk, "helm", prec, x, 1.0)
+    blk.set_tuning(prec, 3, 0, 0)
+    assert np.array_equal(run_op(blk, "helm", prec, x, 1.0), y0)   # same arithmetic, other allocation
     with pytest.raises(nir.NirError):
-        blk.set_tuning(prec, 3)
+        blk.set_tuning(prec, 4)
 
 
 @pytest.mark.parametrize("shape", ["quad", "tri", "hex", "prism", "tet"])
