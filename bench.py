@@ -646,7 +646,8 @@ def run_sweep(args, ws, rank, local):
     """Helmholtz throughput against problem size for P = 1..8 on hexahedra and
     tetrahedra (the paper's GPU throughput study, Sec. 4.2): one block per
     (shape, P, size), throughput = DOF / device time of one apply (CUDA events
-    over repeated applies), with the kernel's registers per thread."""
+    over repeated applies, the faster of the two code generations of the
+    default group), with the kernel's registers per thread."""
     import torch
     import paper_2606_20917_gb300 as nir
 
@@ -675,23 +676,29 @@ def run_sweep(args, ws, rank, local):
                 E = nodes.shape[0]
                 blk = nir.Block(ctx, shape, E, P, deformed=deformed)
                 blk.set_geometry(gorder, torch.from_numpy(nodes).to(dev))
-                if prec != "f64":
-                    blk.set_tuning(prec, 0, 0, 1)  # L2 metric prefetch on
                 x = torch.from_numpy(W.coefficients(E, M, seed=0)).to(dev, nir.DTYPE[prec])
                 y = torch.empty_like(x)
-                for _ in range(3):
-                    blk.helmholtz(x, prec=prec, out=y)
                 reps = max(3, min(50, int(2e8 / (E * M))))
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize()
-                a.record(stream)
-                for _ in range(reps):
-                    blk.helmholtz(x, prec=prec, out=y)
-                b.record(stream)
-                torch.cuda.synchronize()
-                t = a.elapsed_time(b) / reps * 1e-3
+                # the two code generations of the default group (variants 0 and 3), L2
+                # metric prefetch on in FP32/BF16; the faster is reported
+                best = None
+                for variant in (0, 3):
+                    blk.set_tuning(prec, variant, 0, 0 if prec == "f64" else 1)
+                    for _ in range(3):
+                        blk.helmholtz(x, prec=prec, out=y)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    a.record(stream)
+                    for _ in range(reps):
+                        blk.helmholtz(x, prec=prec, out=y)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    tv = a.elapsed_time(b) / reps * 1e-3
+                    if best is None or tv < best[0]:
+                        best = (tv, variant, blk.kernel_info(prec, "helm"))
+                t = best[0]
                 rec = {"shape": shape, "P": P, "nelem": E, "dof": E * M, "gdofs": E * M / t / 1e9,
-                       "ms": t * 1e3, **blk.kernel_info(prec, "helm")}
+                       "ms": t * 1e3, "variant": best[1], **best[2]}
                 if prec == "f64":
                     rec["frac_fp64"] = E * helm_flops_per_elem(shape, N, Q) / t / 1e12 / fp64_peak
                 else:
