@@ -19,7 +19,7 @@
  * PhysDeriv of arbitrary point data uses collocation differentiation through
  * the element's own points (Eq. stdderiv) with the same chain rule.
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - H = L + lambda M with lambda > 0 (Eq. weakmatrixhelm; the sign printed
  *     in Eq. weak_helm is not used).
  *   - eta1 = 2(1+xi1)/(-xi2-xi3) - 1 for the tet (Eq. eta-space lacks the -1).
