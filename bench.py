@@ -801,7 +801,7 @@ def run_hybrid(args, ws, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=1000)  # ~0.9 s timed: several clock samples
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["nir", "reference"], default="nir")
     ap.add_argument("--workload", default="hex32_curved_p4")
