@@ -96,9 +96,17 @@ def faces_of(verts: np.ndarray):
     return table
 
 
-def constraints(shape: str, P: int, verts: np.ndarray, dirichlet: bool) -> np.ndarray:
+def _basis_at(shape, P, xi, basis):
+    if basis == "nodal":
+        from oracle import nodal
+        return nodal.eval_basis(shape, P, xi)
+    return orc.eval_basis(shape, P, xi)[0]
+
+
+def constraints(shape: str, P: int, verts: np.ndarray, dirichlet: bool, basis: str = "modified") -> np.ndarray:
     """Rows C with C x = 0 exactly for the conforming (and, with ``dirichlet``,
-    boundary-vanishing) broken expansions x (flattened [E][M])."""
+    boundary-vanishing) broken expansions x (flattened [E][M]) in the modified
+    or the nodal (GLL-Lagrange) basis."""
     d = orc.dim(shape)
     E, M = verts.shape[0], orc.num_modes(shape, P)
     s = _face_samples(d, P)
@@ -109,14 +117,14 @@ def constraints(shape: str, P: int, verts: np.ndarray, dirichlet: bool) -> np.nd
         e1, f1 = owners[0]
         c1 = _face_corners(d, *f1)
         xi1 = _bilinear(s, np.stack([_vertex_xi(d, v) for v in c1]))
-        B1, _ = orc.eval_basis(shape, P, xi1)
+        B1 = _basis_at(shape, P, xi1, basis)
         if len(owners) == 2:
             e2, f2 = owners[1]
             c2 = _face_corners(d, *f2)
             # element 2's reference corners listed in element 1's corner order
             pos2 = {int(verts[e2, v]): v for v in c2}
             xi2 = _bilinear(s, np.stack([_vertex_xi(d, pos2[int(verts[e1, v])]) for v in c1]))
-            B2, _ = orc.eval_basis(shape, P, xi2)
+            B2 = _basis_at(shape, P, xi2, basis)
             R = np.zeros((s.shape[0], E * M))
             R[:, e1 * M:(e1 + 1) * M] = B1
             R[:, e2 * M:(e2 + 1) * M] -= B2
@@ -130,10 +138,10 @@ def constraints(shape: str, P: int, verts: np.ndarray, dirichlet: bool) -> np.nd
     return np.concatenate(rows, axis=0)
 
 
-def conforming_basis(shape: str, P: int, verts: np.ndarray, dirichlet: bool) -> np.ndarray:
+def conforming_basis(shape: str, P: int, verts: np.ndarray, dirichlet: bool, basis: str = "modified") -> np.ndarray:
     """Orthonormal basis Z [E*M][n] of the conforming (homogeneous-Dirichlet)
     space, as the numerical null space of ``constraints``."""
-    C = constraints(shape, P, verts, dirichlet)
+    C = constraints(shape, P, verts, dirichlet, basis)
     if C.shape[0] == 0:
         return np.eye(C.shape[1])
     return sla.null_space(C, rcond=1e-9)
@@ -144,32 +152,45 @@ def block_matrix(mats: np.ndarray) -> np.ndarray:
     return sla.block_diag(*mats)
 
 
-def mass_matrices(shape, P, Q, gorder, nodes) -> np.ndarray:
-    """Dense elemental mass matrices B^T diag(W_e) B, [E][M][M]."""
+def _ops(basis):
+    """(mass matrices, Helmholtz matrices, IProductWRTBase) of the chosen basis."""
+    if basis == "nodal":
+        from oracle import nodal
+        return nodal.mass_matrices, nodal.helmholtz_matrices, nodal.iprod
+    return _mass_modified, orc.helmholtz_matrix, orc.iprod
+
+
+def _mass_modified(shape, P, Q, gorder, nodes) -> np.ndarray:
     B, _ = orc.ref_basis(shape, P, Q)
     W, _, _ = orc.geom_factors(shape, Q, gorder, nodes)
     return np.einsum("nm,en,nk->emk", B, W, B)
 
 
-def project(shape, P, Q, gorder, nodes, verts, g_phys) -> np.ndarray:
+def mass_matrices(shape, P, Q, gorder, nodes, basis: str = "modified") -> np.ndarray:
+    """Dense elemental mass matrices B^T diag(W_e) B, [E][M][M]."""
+    return _ops(basis)[0](shape, P, Q, gorder, nodes)
+
+
+def project(shape, P, Q, gorder, nodes, verts, g_phys, basis: str = "modified") -> np.ndarray:
     """L2 projection onto the conforming space of values g at the quadrature
     points [E][Nq]; returns the local coefficients [E][M]."""
-    Z = conforming_basis(shape, P, verts, dirichlet=False)
-    Mb = block_matrix(mass_matrices(shape, P, Q, gorder, nodes))
-    rhs = orc.iprod(shape, P, Q, gorder, nodes, g_phys).ravel()
+    Z = conforming_basis(shape, P, verts, dirichlet=False, basis=basis)
+    Mb = block_matrix(mass_matrices(shape, P, Q, gorder, nodes, basis))
+    rhs = _ops(basis)[2](shape, P, Q, gorder, nodes, g_phys).ravel()
     y = np.linalg.solve(Z.T @ Mb @ Z, Z.T @ rhs)
     return (Z @ y).reshape(nodes.shape[0], -1)
 
 
-def dirichlet_solve(shape, P, Q, gorder, nodes, verts, lam, f_phys, g_phys):
+def dirichlet_solve(shape, P, Q, gorder, nodes, verts, lam, f_phys, g_phys, basis: str = "modified"):
     """Global (L + lambda M) u = f, u = g on the boundary (g through its L2
     projection).  Returns (u, u_p): local coefficients [E][M] of the solution
     and of the lift."""
     E = nodes.shape[0]
-    u_p = project(shape, P, Q, gorder, nodes, verts, g_phys)
-    H = block_matrix(orc.helmholtz_matrix(shape, P, Q, gorder, nodes, lam))
-    b = orc.iprod(shape, P, Q, gorder, nodes, f_phys).ravel()
-    Z0 = conforming_basis(shape, P, verts, dirichlet=True)
+    _, helm, iprod = _ops(basis)
+    u_p = project(shape, P, Q, gorder, nodes, verts, g_phys, basis)
+    H = block_matrix(helm(shape, P, Q, gorder, nodes, lam))
+    b = iprod(shape, P, Q, gorder, nodes, f_phys).ravel()
+    Z0 = conforming_basis(shape, P, verts, dirichlet=True, basis=basis)
     A = Z0.T @ H @ Z0
     w = sla.cho_solve(sla.cho_factor(A), Z0.T @ (b - H @ u_p.ravel()))
     return (u_p.ravel() + Z0 @ w).reshape(E, -1), u_p

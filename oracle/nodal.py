@@ -82,6 +82,16 @@ def _dx(dB, Lam):
     return np.einsum("enil,inm->elnm", Lam, dB)
 
 
+def eval_basis(shape: str, P: int, xi):
+    """Nodal basis at arbitrary reference points xi [n][d] -> [n][M]."""
+    xi = np.asarray(xi, dtype=np.float64)
+    z = gll_nodes(P + 1)
+    L = [lagrange_1d(z, xi[:, c])[0] for c in range(xi.shape[1])]
+    if xi.shape[1] == 2:
+        return np.einsum("np,nq->npq", L[0], L[1]).reshape(xi.shape[0], -1)
+    return np.einsum("np,nq,nr->npqr", L[0], L[1], L[2]).reshape(xi.shape[0], -1)
+
+
 def bwd(shape, P, Q, coeff):
     B, _ = ref_basis(shape, P, Q)
     return np.asarray(coeff) @ B.T

@@ -111,3 +111,20 @@ def test_spectral_convergence_curved_hex():
     for a, b in zip(errs, errs[1:]):
         assert b < a / 2.0, errs
     assert errs[-1] < errs[0] / 30.0, errs
+
+
+@pytest.mark.parametrize("shape,n,P", [("quad", 3, 3), ("hex", 2, 3)])
+def test_nodal_space_dimension_and_quadratic_solve(shape, n, P):
+    """The same closed-form dimensions and exact quadratic recovery in the
+    nodal (GLL-Lagrange) basis."""
+    d = 2 if shape == "quad" else 3
+    nodes, verts, g = _mesh(shape, n, 1, 0.0, rotate=True, seed=5)
+    assert cf.conforming_basis(shape, P, verts, False, "nodal").shape[1] == (n * P + 1) ** d
+    assert cf.conforming_basis(shape, P, verts, True, "nodal").shape[1] == (n * P - 1) ** d
+    from oracle import nodal as nd
+    Q, lam = P + 2, 0.75
+    X = _xq(shape, Q, g, nodes)
+    u = X[..., 0] ** 2 + X[..., 0] * X[..., 1] - 0.5 * X[..., 1] + (X[..., 2] ** 2 if d == 3 else 0.0)
+    lap = 2.0 + (2.0 if d == 3 else 0.0)
+    sol, _ = cf.dirichlet_solve(shape, P, Q, g, nodes, verts, lam, -lap + lam * u, u, basis="nodal")
+    assert np.abs(nd.bwd(shape, P, Q, sol) - u).max() < 1e-10
