@@ -268,9 +268,10 @@ int nir_cg_solve(nir_mesh *mesh, double lambda, const double *b, double *x, cons
  * The elemental operators above act on broken (element-local) expansions; the
  * paper's solve leaves assembly out (Sec. 2.1).  An assembly object joins the
  * elements of conforming blocks into the continuous spectral/hp space of the
- * modified basis: a global vector x_g maps to element coefficients by
- * x_loc = A x_g (every local mode takes +-1 times one global dof; the sign
- * accounts for the orientation of shared edges and faces), and element
+ * modified or the GLL-Lagrange basis: a global vector x_g maps to element
+ * coefficients by x_loc = A x_g (every local mode takes +-1 times one global
+ * dof; the index and, for the modified basis, the sign account for the
+ * orientation of shared edges and faces), and element
  * results are summed back by y_g = A^T y_loc.  The assembled Helmholtz
  * operator is A^T H A (H = L + lambda M elementwise), the assembled mass
  * operator A^T M A.
@@ -285,24 +286,25 @@ typedef struct nir_asm nir_asm;
 enum { NIR_ASM_HELMHOLTZ = 0, NIR_ASM_MASS = 1 };
 
 /* Build the global numbering of conforming blocks of one shape (NIR_QUAD or
- * NIR_HEX), one P and the modified basis.  vertex_ids[b]: HOST int64 array [nelem_b][2^d] of the
+ * NIR_HEX), one P and one basis (NIR_BASIS_MODIFIED or
+ * NIR_BASIS_GLL_LAGRANGE; the Lagrange numbering has all signs +1).  vertex_ids[b]: HOST int64 array [nelem_b][2^d] of the
  * global vertex ids of block b's elements, local vertex v = a + 2b (+ 4c) at
  * reference coordinates xi = (-1+2a, -1+2b(, -1+2c)) -- the corners of the
  * geometry lattice of nir_block_set_geometry.  Elements may see shared faces
  * in any orientation.  The object keeps pointers to the blocks, which must
  * outlive it.  Errors: INVALID_ARG (null pointers, a face held by more than
- * two elements), UNSUPPORTED (other shapes, mixed shapes or orders),
+ * two elements), UNSUPPORTED (other shapes, mixed shapes, orders or bases),
  * TOO_LARGE (2^31 or more dofs), NO_MEMORY, CUDA. */
 int nir_asm_create(nir_ctx *ctx, nir_block *const *blocks, const int64_t *const *vertex_ids, int nblocks,
                    nir_asm **out);
 void nir_asm_destroy(nir_asm *a);
 /* The numbering alone, on the host (no GPU needed): nblocks blocks of nelem[b]
- * elements of `shape` (NIR_QUAD / NIR_HEX) and degree P with vertex ids as for
- * nir_asm_create.  map_out: HOST int64 [sum_b nelem[b] * M] receiving
+ * elements of `shape` (NIR_QUAD / NIR_HEX), degree P and basis (NIR_BASIS_*)
+ * with vertex ids as for nir_asm_create.  map_out: HOST int64 [sum_b nelem[b] * M] receiving
  * s (g + 1) per local dof (may be NULL); n_global, n_free as for
  * nir_asm_num_dofs.  nir_asm_create uses exactly this numbering. */
-int nir_c0_numbering(int shape, int P, int nblocks, const int64_t *nelem, const int64_t *const *vertex_ids,
-                     int64_t *map_out, int64_t *n_global, int64_t *n_free);
+int nir_c0_numbering(int shape, int P, int basis, int nblocks, const int64_t *nelem,
+                     const int64_t *const *vertex_ids, int64_t *map_out, int64_t *n_global, int64_t *n_free);
 /* Sizes: global dofs, free (non-boundary) dofs, local dofs; NULL outputs skipped. */
 int nir_asm_num_dofs(const nir_asm *a, int64_t *n_global, int64_t *n_free, int64_t *n_local);
 /* HOST copy of the map: map_out[i] = s (g + 1) for local dof i, s = +-1. */

@@ -371,7 +371,8 @@ ASM_OPS = {"helmholtz": 0, "mass": 1}
 
 
 class Assembly:
-    """Conforming C0 assembly of quad or hex blocks (global vectors: free dofs
+    """Conforming C0 assembly of quad or hex blocks of one order and one basis
+    (modified or GLL-Lagrange; global vectors: free dofs
     first, then boundary dofs; local vectors: the blocks' [E][M] arrays
     concatenated)."""
 

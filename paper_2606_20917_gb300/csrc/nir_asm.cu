@@ -3,21 +3,24 @@
 // The paper applies its operators element by element (Sec. 2.1: the weak
 // Helmholtz matrix is built from elemental B, W, Lambda) and leaves the global
 // system out; this unit joins the elemental expansions into a continuous one,
-// the standard spectral/hp construction of the modified C0 basis.
+// the standard spectral/hp construction of a C0 basis (modified or
+// GLL-Lagrange).
 //
-// Global numbering from vertex connectivity.  Every mode of the modified basis
-// belongs to one mesh entity: the tensor index (p, q, r) gives each direction
-// the role "vertex at -1" (index 0), "vertex at +1" (1) or "bubble" (>= 2).
-// No bubble: a vertex mode; one: an edge mode of 1-D bubble index p - 2;
+// Global numbering from vertex connectivity.  Every mode belongs to one mesh
+// entity: each direction of the tensor index (p, q, r) plays the role "vertex
+// at -1", "vertex at +1" or "bubble".  Modified basis: index 0, 1, and >= 2
+// (bubble p - 2); GLL-Lagrange basis: node 0, node N - 1, and the interior
+// nodes 1..N-2 (bubble p - 1).  No bubble: a vertex mode; one: an edge mode;
 // two (3-D): a face mode; all: an interior mode.  Shared entities are keyed by
 // the sorted global ids of their vertices and seen from a canonical frame:
 //   - an edge runs from its smaller to its larger vertex id; a local edge
-//     running the other way sees bubble p with sign (-1)^p (psi_p(-z) =
-//     (-1)^p psi_p(z) for the modified basis bubbles);
+//     running the other way reflects its bubbles: sign (-1)^p for the
+//     modified basis (psi_p(-z) = (-1)^p psi_p(z)), node order reversed for
+//     the Lagrange basis (l_{N-1-j}(-z) = l_j(z) on the symmetric GLL nodes);
 //   - a face's origin is its smallest-id corner, its first axis points to the
 //     origin's neighbour with the smaller id.  A local face whose axes are
 //     swapped relative to that frame exchanges the two mode indices, and each
-//     local axis running against the frame flips sign (-1)^p.
+//     local axis running against the frame reflects that direction as above.
 // Faces (2-D: edges) owned by one element are the boundary.  Free dofs are
 // numbered first (element order, entity order vertices, edges, faces, then
 // interior), boundary dofs after them, so vectors of the outer solve hold the
@@ -390,10 +393,11 @@ void asm_free(nir_asm *a)
 
 // The global numbering (host only): map[i] = s (g + 1) for every local dof of
 // the blocks' elements (nelem[b] elements of M modes each, in block order).
-int c0_numbering(int d, int P, const std::vector<long long> &nelem, const int64_t *const *verts,
+int c0_numbering(int d, int P, int basis, const std::vector<long long> &nelem, const int64_t *const *verts,
                  std::vector<int> &map, long long &nglob, long long &nfree)
 {
     const int N = P + 1, nv = 1 << d;
+    const bool nodal = basis == NIR_BASIS_GLL_LAGRANGE;
     const int M = d == 2 ? N * N : N * N * N;
     const int nb1 = P - 1;  // bubbles per direction
     std::unordered_map<EKey, int, EKeyHash> index;
@@ -536,18 +540,31 @@ int c0_numbering(int d, int P, const std::vector<long long> &nelem, const int64_
                 int idx[3] = {0, 0, 0};
                 if (d == 2) { idx[0] = m / N; idx[1] = m % N; }
                 else { idx[0] = m / (N * N); idx[1] = (m / N) % N; idx[2] = m % N; }
-                int nbub = 0, bub[3], fixd[3], nf = 0;
+                // role per direction: vertex bit (vb) or bubble index (bb)
+                int nbub = 0, bub[3], fixd[3], nf = 0, vb[3] = {0, 0, 0}, bb[3] = {0, 0, 0};
                 for (int k = 0; k < d; ++k) {
-                    if (idx[k] >= 2) bub[nbub++] = k;
-                    else fixd[nf++] = k;
+                    const bool lo = idx[k] == 0, hi = nodal ? idx[k] == N - 1 : idx[k] == 1;
+                    if (lo || hi) {
+                        vb[k] = hi;
+                        fixd[nf++] = k;
+                    } else {
+                        bb[k] = idx[k] - (nodal ? 1 : 2);
+                        bub[nbub++] = k;
+                    }
                 }
                 long long g = 0;
                 int sgn = 1;
+                // a bubble seen from the reflected direction
+                auto reflect = [&](int b) {
+                    if (nodal) return nb1 - 1 - b;
+                    if (b & 1) sgn = -sgn;
+                    return b;
+                };
                 if (nbub == 0) {
-                    g = ents[ee[vnum(idx, d)]].first;
+                    g = ents[ee[vnum(vb, d)]].first;
                 } else if (nbub == 1) {
                     const int dd = bub[0];
-                    int bits[3] = {idx[0] & 1, idx[1] & 1, idx[2] & 1};
+                    int bits[3] = {vb[0], vb[1], vb[2]};
                     // edge number within direction dd: the other bits in increasing direction order
                     int o = 0, sh = 0;
                     for (int q = 0; q < d; ++q)
@@ -556,10 +573,10 @@ int c0_numbering(int d, int P, const std::vector<long long> &nelem, const int64_
                     const long long a0 = vg[vnum(bits, d)];
                     bits[dd] = 1;
                     const long long a1 = vg[vnum(bits, d)];
-                    g = ents[ee[nv + dd * (nv / 2) + o]].first + (idx[dd] - 2);
-                    if (a0 > a1 && (idx[dd] & 1)) sgn = -1;
+                    const int b = a0 > a1 ? reflect(bb[dd]) : bb[dd];
+                    g = ents[ee[nv + dd * (nv / 2) + o]].first + b;
                 } else if (nbub == 2 && d == 3) {
-                    const int f = fixd[0], side = idx[f];
+                    const int f = fixd[0], side = vb[f];
                     const int u = bub[0], v = bub[1];
                     long long c[2][2];
                     for (int s = 0; s < 2; ++s)
@@ -575,14 +592,13 @@ int c0_numbering(int d, int P, const std::vector<long long> &nelem, const int64_
                         for (int t = 0; t < 2; ++t)
                             if (c[s][t] < c[s0][t0]) { s0 = s; t0 = t; }
                     const bool transposed = c[1 - s0][t0] > c[s0][1 - t0];
-                    const int pu = idx[u], pv = idx[v];
-                    if (s0 && (pu & 1)) sgn = -sgn;
-                    if (t0 && (pv & 1)) sgn = -sgn;
-                    const int fa = transposed ? pv : pu, fb = transposed ? pu : pv;
-                    g = ents[ee[nv + nedge + 2 * f + side]].first + (long long)(fa - 2) * nb1 + (fb - 2);
+                    const int bu = s0 ? reflect(bb[u]) : bb[u];
+                    const int bv = t0 ? reflect(bb[v]) : bb[v];
+                    const int fa = transposed ? bv : bu, fb = transposed ? bu : bv;
+                    g = ents[ee[nv + nedge + 2 * f + side]].first + (long long)fa * nb1 + fb;
                 } else {
                     long long r = 0;
-                    for (int k = 0; k < d; ++k) r = r * nb1 + (idx[k] - 2);
+                    for (int k = 0; k < d; ++k) r = r * nb1 + bb[k];
                     g = interior_first[(size_t)e] + r;
                 }
                 map[(size_t)li] = sgn * (int)(g + 1);
@@ -597,7 +613,7 @@ int asm_number(nir_asm *a, const int64_t *const *verts)
 {
     std::vector<long long> nelem;
     for (nir_block *b : a->blocks) nelem.push_back(b->d.nelem);
-    int rc = c0_numbering(a->dim, a->P, nelem, verts, a->map_h, a->nglob, a->nfree);
+    int rc = c0_numbering(a->dim, a->P, a->blocks[0]->d.basis, nelem, verts, a->map_h, a->nglob, a->nfree);
     if (rc) return rc;
     // transpose: copies of every global dof in local order
     std::vector<int> rowptr((size_t)a->nglob + 1, 0), pos((size_t)a->nloc);
@@ -635,7 +651,7 @@ extern "C" int nir_asm_create(nir_ctx *ctx, nir_block *const *blocks, const int6
     for (int i = 0; i < nblocks; ++i) {
         if (!blocks[i] || !vertex_ids[i] || blocks[i]->ctx != ctx) return NIR_ERR_INVALID_ARG;
         if (blocks[i]->d.shape != shape || blocks[i]->d.P != blocks[0]->d.P) return NIR_ERR_UNSUPPORTED;
-        if (blocks[i]->d.basis != NIR_BASIS_MODIFIED) return NIR_ERR_UNSUPPORTED;
+        if (blocks[i]->d.basis != blocks[0]->d.basis) return NIR_ERR_UNSUPPORTED;
     }
     if (blocks[0]->d.P < 1) return NIR_ERR_UNSUPPORTED;
     NIR_CUDA_TRY(cudaSetDevice(ctx->device));
@@ -667,10 +683,11 @@ extern "C" int nir_asm_create(nir_ctx *ctx, nir_block *const *blocks, const int6
     return NIR_OK;
 }
 
-extern "C" int nir_c0_numbering(int shape, int P, int nblocks, const int64_t *nelem, const int64_t *const *vertex_ids,
-                                int64_t *map_out, int64_t *n_global, int64_t *n_free)
+extern "C" int nir_c0_numbering(int shape, int P, int basis, int nblocks, const int64_t *nelem,
+                                const int64_t *const *vertex_ids, int64_t *map_out, int64_t *n_global, int64_t *n_free)
 {
     if ((shape != NIR_QUAD && shape != NIR_HEX)) return NIR_ERR_UNSUPPORTED;
+    if (basis != NIR_BASIS_MODIFIED && basis != NIR_BASIS_GLL_LAGRANGE) return NIR_ERR_INVALID_ARG;
     if (P < 1 || P > 8 || nblocks < 1 || !nelem || !vertex_ids) return NIR_ERR_INVALID_ARG;
     std::vector<long long> ne;
     for (int b = 0; b < nblocks; ++b) {
@@ -679,7 +696,7 @@ extern "C" int nir_c0_numbering(int shape, int P, int nblocks, const int64_t *ne
     }
     std::vector<int> map;
     long long ng = 0, nf = 0;
-    int rc = c0_numbering(shape == NIR_HEX ? 3 : 2, P, ne, vertex_ids, map, ng, nf);
+    int rc = c0_numbering(shape == NIR_HEX ? 3 : 2, P, basis, ne, vertex_ids, map, ng, nf);
     if (rc) return rc;
     if (map_out)
         for (size_t i = 0; i < map.size(); ++i) map_out[i] = map[i];

@@ -128,3 +128,22 @@ def test_nodal_space_dimension_and_quadratic_solve(shape, n, P):
     lap = 2.0 + (2.0 if d == 3 else 0.0)
     sol, _ = cf.dirichlet_solve(shape, P, Q, g, nodes, verts, lam, -lap + lam * u, u, basis="nodal")
     assert np.abs(nd.bwd(shape, P, Q, sol) - u).max() < 1e-10
+
+
+@pytest.mark.parametrize("shape,n,P,g", [("quad", 3, 4, 1), ("hex", 2, 3, 2)])
+def test_nodal_and_modified_solutions_coincide(shape, n, P, g):
+    """Both bases span the same conforming space, so the Galerkin solutions of
+    one Dirichlet problem are the same function: equal at every quadrature
+    point, on a curved mesh in rotated frames."""
+    from oracle import nodal as nd
+    d = 2 if shape == "quad" else 3
+    nodes = W.quad_grid(n, n) if d == 2 else W.hex_grid(n, g, amp=0.05)
+    nodes, verts, _ = W.rotate_elements(nodes, W.grid_vertices(n, d), g, seed=11)
+    Q, lam = P + 2, 1.5
+    X = _xq(shape, Q, g, nodes)
+    u = np.prod(np.sin(np.pi * X), axis=-1)
+    f = (d * np.pi ** 2 + lam) * u
+    sn, _ = cf.dirichlet_solve(shape, P, Q, g, nodes, verts, lam, f, u, basis="nodal")
+    sm, _ = cf.dirichlet_solve(shape, P, Q, g, nodes, verts, lam, f, u)
+    vn, vm = nd.bwd(shape, P, Q, sn), orc.bwd(shape, P, Q, sm)
+    assert np.abs(vn - vm).max() <= 1e-10 * np.abs(vm).max()

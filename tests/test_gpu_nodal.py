@@ -3,13 +3,16 @@ nodal oracle (``oracle/nodal.py``, itself pinned to the modified-basis oracle
 by the change of basis): every modal operator in FP64 at P = 1..8, the FP32
 and BF16 Helmholtz (fused kernel with bulk-copy staging), several launch
 variants, multi-field calls, the hybrid mesh in both launch forms, the full
-benchmark mesh on sampled elements, and the unsupported combinations."""
+benchmark mesh on sampled elements, the conforming C0 assembly and Dirichlet
+solve against the numbering-free oracle of ``oracle/conforming.py`` in the
+nodal basis, and the unsupported combinations."""
 import numpy as np
 import pytest
 import torch
 
 import oracle as orc
 import workloads as W
+from oracle import conforming as cf
 from oracle import nodal as nd
 
 pytestmark = pytest.mark.gpu
@@ -126,11 +129,55 @@ def test_full_benchmark_mesh_nodal_sampled(nir, ctx):
         assert rel(y[ids], ref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("shape,n,P,g", [("quad", 3, 4, 1), ("hex", 2, 4, 2), ("hex", 2, 5, 2)])
+@pytest.mark.parametrize("inner", ["f64", "f32"])
+def test_nodal_assembly_and_dirichlet_solve(nir, ctx, shape, n, P, g, inner):
+    """Rotated local frames (every edge and face orientation): the gathered
+    space is the oracle's conforming nodal space, and the Dirichlet Helmholtz
+    solve through the nodal kernels equals the oracle's global solution."""
+    d = 2 if shape == "quad" else 3
+    lam = 1.5
+    nodes = W.quad_grid(n, n) if d == 2 else W.hex_grid(n, g, amp=0.05)
+    nodes, verts, _ = W.rotate_elements(nodes, W.grid_vertices(n, d), g, seed=7 * P)
+    nodes = np.ascontiguousarray(nodes)
+    E, Q = nodes.shape[0], P + 2
+    cut = E // 2
+    blocks = []
+    for a, b in ((0, cut), (cut, E)):
+        blk = nir.Block(ctx, shape, b - a, P, deformed=True, basis="nodal")
+        blk.set_geometry(g, torch.from_numpy(np.ascontiguousarray(nodes[a:b])).cuda())
+        blocks.append(blk)
+    asm = nir.Assembly(ctx, blocks, [verts[:cut], verts[cut:]])
+    assert (asm.n_global, asm.n_free) == ((n * P + 1) ** d, (n * P - 1) ** d)
+    assert (asm.local_map() > 0).all()
+    Z = cf.conforming_basis(shape, P, verts, dirichlet=False, basis="nodal")
+    xl = asm.gather(torch.from_numpy(W.coefficients(1, asm.n_global, seed=3)[0]).cuda()).cpu().numpy()
+    assert np.linalg.norm(xl - Z @ (Z.T @ xl)) <= 1e-12 * np.linalg.norm(xl)
+    X = orc.geom_factors(shape, Q, g, nodes, with_x=True)[2]
+    u = np.prod(np.sin(np.pi * X), axis=-1)
+    f = (d * np.pi ** 2 + lam) * u
+    sol, lift = cf.dirichlet_solve(shape, P, Q, g, nodes, verts, lam, f, u, basis="nodal")
+    parts = [blocks[0].iproduct_wrt_base(torch.from_numpy(np.ascontiguousarray(f[:cut])).cuda()),
+             blocks[1].iproduct_wrt_base(torch.from_numpy(np.ascontiguousarray(f[cut:])).cuda())]
+    b = asm.assemble(torch.cat([p.view(-1) for p in parts]))
+    x = asm.pick(torch.from_numpy(lift.ravel()).cuda())
+    xb = x[asm.n_free:].clone()
+    x[:asm.n_free] = 0.0
+    rc, st = asm.cg_solve(b, x, lam=lam, inner_prec=inner, tol=1e-12, max_inner=5000)
+    assert rc == 0, st
+    assert torch.equal(x[asm.n_free:], xb)
+    got = asm.gather(x).cpu().numpy().reshape(sol.shape)
+    assert np.linalg.norm(got - sol) <= 1e-9 * np.linalg.norm(sol)
+
+
 def test_unsupported_combinations(nir, ctx):
     with pytest.raises(nir.NirError) as e:
         nir.Block(ctx, "tet", 4, 3, basis="nodal")
     assert e.value.code == -2
     g, nodes, blk = block(nir, ctx, "hex", 2, 8)
-    with pytest.raises(nir.NirError) as e:
-        nir.Assembly(ctx, [blk], [W.grid_vertices(2, 3)])
+    mod = nir.Block(ctx, "hex", 8, 2, deformed=True)
+    mod.set_geometry(g, torch.from_numpy(np.ascontiguousarray(nodes)).cuda())
+    verts = W.grid_vertices(2, 3)
+    with pytest.raises(nir.NirError) as e:           # one assembly, two bases
+        nir.Assembly(ctx, [blk, mod], [verts, verts + 100])
     assert e.value.code == -2
