@@ -102,16 +102,21 @@ KERNEL_SOURCES = ("paper_2606_20917_gb300/csrc/nir_kernels.cuh", "paper_2606_209
                   "paper_2606_20917_gb300/csrc/nir_layout.h")
 
 
-def kernel_sources_sha256() -> str:
+# the threading-over-elements Helmholtz kernel (tuning variant 4)
+TOE_SOURCES = ("paper_2606_20917_gb300/csrc/nir_toe.cuh", "paper_2606_20917_gb300/csrc/nir_toe.cu",
+               "paper_2606_20917_gb300/csrc/nir_layout.h")
+
+
+def kernel_sources_sha256(sources=KERNEL_SOURCES) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def profiled_traffic(name: str):
+def profiled_traffic(name: str, sources=KERNEL_SOURCES):
     """DRAM bytes per launch from the committed ncu summary profiles/<name>.md,
     or None when the kernel sources changed since that capture."""
     import re
@@ -121,7 +126,7 @@ def profiled_traffic(name: str):
     txt = open(path).read()
     t = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", txt)
     h = re.search(r"kernel_sources_sha256:\s*([0-9a-f]{64})", txt)
-    if not t or not h or h.group(1) != kernel_sources_sha256():
+    if not t or not h or h.group(1) != kernel_sources_sha256(sources):
         return None
     return int(t.group(1))
 
@@ -296,6 +301,11 @@ def run_nir(args, ws, rank, local):
         # size and metric-prefetch policy for this block on this GPU (a cache
         # file, when given, is read back instead of re-timing)
         nir.Mesh(ctx, [blk]).tune(args.tune_cache)
+    toe = args.strategy == "elements"
+    if toe:  # the paper's other GPU strategy: one thread per element (tuning variant 4)
+        blk.set_tuning(args.prec, 4, 0, 0)
+    prof = (f"helm_toe_{args.workload}_{args.prec}", TOE_SOURCES) if toe else \
+        (f"helm_{args.workload}_{args.prec}", KERNEL_SOURCES)
     M = blk.M
     dt_t = nir.DTYPE[args.prec]
     u = torch.from_numpy(W.coefficients(E, M, seed=0)).to(dev, dt_t)
@@ -349,7 +359,7 @@ def run_nir(args, ws, rank, local):
         fp64 = ctx.probe_fp64_peak()
         roof = {"bound": "alu", "achieved": flops / avg_launch_s / 1e12, "peak": fp64, "unit": "TFLOP/s",
                 "frac": flops / avg_launch_s / 1e12 / fp64,
-                "traffic": profiled_traffic(f"helm_{args.workload}_{args.prec}"),
+                "traffic": profiled_traffic(*prof),
                 "peak_source": "FP64 FMA throughput measured in this run by nir_probe_fp64_peak "
                                "(register-resident DFMA chains); nominal GB300 FP64 is 1.25 TFLOP/s",
                 "flops_per_elem": flops // E,
@@ -358,7 +368,7 @@ def run_nir(args, ws, rank, local):
         gbs = work_bytes / avg_launch_s / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                "traffic": profiled_traffic(f"helm_{args.workload}_{args.prec}"),
+                "traffic": profiled_traffic(*prof),
                 "bytes_per_elem": work_bytes // E,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "_fallback" not in peaks else "fallback 6.8 TB/s"}
     # three fields sharing the operator in one launch (after the timed region)
@@ -403,6 +413,7 @@ def run_nir(args, ws, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
             "config": dict(workload_config(args, wl), tuned=not args.no_tune,
+                           strategy="threading over elements" if toe else "element groups per CTA",
                            l2=f"no flush: {work_bytes / 2**20:.0f} MiB streamed per step > 129 MiB L2"),
             "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk.summary(),
             "multi_field": fields,
@@ -647,7 +658,8 @@ def run_sweep(args, ws, rank, local):
     tetrahedra (the paper's GPU throughput study, Sec. 4.2): one block per
     (shape, P, size), throughput = DOF / device time of one apply (CUDA events
     over repeated applies, the faster of the two code generations of the
-    default group), with the kernel's registers per thread."""
+    default group), with the kernel's registers per thread; and the same for
+    the paper's other strategy, threading over elements (key "toe")."""
     import torch
     import paper_2606_20917_gb300 as nir
 
@@ -681,9 +693,7 @@ def run_sweep(args, ws, rank, local):
                 reps = max(3, min(50, int(2e8 / (E * M))))
                 # the two code generations of the default group (variants 0 and 3), L2
                 # metric prefetch on in FP32/BF16; the faster is reported
-                best = None
-                for variant in (0, 3):
-                    blk.set_tuning(prec, variant, 0, 0 if prec == "f64" else 1)
+                def time_apply():
                     for _ in range(3):
                         blk.helmholtz(x, prec=prec, out=y)
                     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -693,16 +703,30 @@ def run_sweep(args, ws, rank, local):
                         blk.helmholtz(x, prec=prec, out=y)
                     b.record(stream)
                     torch.cuda.synchronize()
-                    tv = a.elapsed_time(b) / reps * 1e-3
+                    return a.elapsed_time(b) / reps * 1e-3
+
+                best = None
+                for variant in (0, 3):
+                    blk.set_tuning(prec, variant, 0, 0 if prec == "f64" else 1)
+                    tv = time_apply()
                     if best is None or tv < best[0]:
                         best = (tv, variant, blk.kernel_info(prec, "helm"))
                 t = best[0]
                 rec = {"shape": shape, "P": P, "nelem": E, "dof": E * M, "gdofs": E * M / t / 1e9,
                        "ms": t * 1e3, "variant": best[1], **best[2]}
-                if prec == "f64":
-                    rec["frac_fp64"] = E * helm_flops_per_elem(shape, N, Q) / t / 1e12 / fp64_peak
-                else:
-                    rec["frac_hbm"] = E * helm_bytes_per_elem(shape, N, Q, wb, deformed) / t / 1e9 / peaks["hbm_gbs"]
+
+                def frac(tt):
+                    if prec == "f64":
+                        return {"frac_fp64": E * helm_flops_per_elem(shape, N, Q) / tt / 1e12 / fp64_peak}
+                    return {"frac_hbm": E * helm_bytes_per_elem(shape, N, Q, wb, deformed) / tt / 1e9
+                            / peaks["hbm_gbs"]}
+                rec.update(frac(t))
+                if not args.sweep_no_toe:
+                    # the other strategy: threading over elements (one thread per element)
+                    blk.set_tuning(prec, 4, 0, 0)
+                    tt = time_apply()
+                    rec["toe"] = {"gdofs": E * M / tt / 1e9, "ms": tt * 1e3, **blk.kernel_info(prec, "helm"),
+                                  **frac(tt)}
                 recs.append(rec)
                 del blk, x, y
                 torch.cuda.empty_cache()
@@ -815,6 +839,9 @@ def main():
                     help="apply mode: expansion basis (nodal = GLL-Lagrange, quad/hex)")
     ap.add_argument("--sweep-shapes", default="hex,tet")
     ap.add_argument("--sweep-dofs", default="1e5,1e6,1e7,3e7")
+    ap.add_argument("--sweep-no-toe", action="store_true", help="sweep the default strategy only")
+    ap.add_argument("--strategy", choices=["groups", "elements"], default="groups",
+                    help="apply mode: the default kernels (element groups per CTA) or threading over elements")
     ap.add_argument("--solve-precs", default="f64,f32,bf16")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--inner-tol", type=float, default=1e-3)

@@ -194,10 +194,19 @@ int nir_helmholtz_host_noalloc(nir_block *blk, int prec, double lambda, const vo
 /* Launch tuning of a block's Helmholtz kernel in one precision (what nir_tune
  * sets): variant 0 = default elements per CTA, 1 = half, 2 = double (where it
  * fits in shared memory; otherwise the default), 3 = the default group run by
- * the multi-field kernel (same results, another register allocation); grid = CTAs launched (0: one
- * wave at the kernel's occupancy); pf = 1 to prefetch each group's metric to
- * L2 (FP32/BF16 with per-point factors; ignored elsewhere).  Errors:
- * INVALID_ARG. */
+ * the multi-field kernel (same results, another register allocation); grid =
+ * CTAs launched (0: one wave at the kernel's occupancy); pf = 1 to prefetch
+ * each group's metric to L2 (FP32/BF16 with per-point factors; ignored
+ * elsewhere).
+ * Variant 4 selects the other threading strategy of Sec. 3.3, threading over
+ * elements: one thread per element runs all stages, its intermediate tensors
+ * in library-owned global scratch of 5 Q^d values per thread of the grid
+ * (allocated by this call, freed with the block; single-field Helmholtz
+ * only, modified basis only; the autotuner never picks it).  grid = CTAs of
+ * 128 threads (0: one wave at its occupancy).  A block's launches share that
+ * scratch: calls on one block must not overlap on the GPU.
+ * Errors: INVALID_ARG; with variant 4 also UNSUPPORTED (nodal basis),
+ * TOO_LARGE (2^31 or more scratch values), NO_MEMORY, CUDA. */
 int nir_block_set_tuning(nir_block *blk, int prec, int variant, int grid, int pf);
 int nir_block_get_tuning(const nir_block *blk, int prec, int *variant, int *grid, int *pf);
 

@@ -183,7 +183,8 @@ class Block:
             self.h = None
 
     def set_tuning(self, prec: str, variant: int = 0, grid: int = 0, pf: int = 0):
-        """Force the Helmholtz launch tuning in one precision (see nir_block_set_tuning)."""
+        """Force the Helmholtz launch tuning in one precision (see nir_block_set_tuning;
+        variant 4 = the threading-over-elements kernel, grid in CTAs of 128 threads)."""
         _chk(_lib.nir_block_set_tuning(self.h, PREC[prec], int(variant), int(grid), int(pf)), "set_tuning")
 
     def get_tuning(self, prec: str):

@@ -1,7 +1,8 @@
 """Build libnir.so in-tree for sm_103a (nvcc, one process per translation unit).
 
-The elemental-operator kernels are instantiated by ``csrc/nir_inst.cu``
-compiled once per (shape, precision) so the units compile in parallel.
+The elemental-operator kernels are instantiated by ``csrc/nir_inst.cu`` and the
+threading-over-elements Helmholtz kernels by ``csrc/nir_toe.cu``, each compiled
+once per (shape, precision) so the units compile in parallel.
 Usage: ``python paper_2606_20917_gb300/build.py [--force] [--jobs N]``.
 """
 from __future__ import annotations
@@ -35,6 +36,10 @@ def _units():
     for s in range(5):
         for p in range(3):
             units.append((os.path.join(CSRC, "nir_inst.cu"), f"inst_s{s}_p{p}.o",
+                          [f"-DNIR_SHAPE={s}", f"-DNIR_PREC={p}"]))
+    for s in range(5):
+        for p in range(3):
+            units.append((os.path.join(CSRC, "nir_toe.cu"), f"toe_s{s}_p{p}.o",
                           [f"-DNIR_SHAPE={s}", f"-DNIR_PREC={p}"]))
     for d in (2, 3):
         for p in range(3):

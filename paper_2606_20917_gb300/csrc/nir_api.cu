@@ -14,6 +14,7 @@
 #include "nir_internal.h"
 #include "nir_kernels.cuh"
 #include "nir_layout.h"
+#include "nir_toe.cuh"
 
 // --------------------------------------------------------------------------- registry
 #define NIR_DECL(s, p) KInfo nir_kinfo_s##s##_p##p(int P, int op, int variant);
@@ -33,6 +34,27 @@ KInfo nir_kinfo(int shape, int P, int prec, int op, int variant)
         {nir_kinfo_s4_p0, nir_kinfo_s4_p1, nir_kinfo_s4_p2}};
     if (shape < 0 || shape > 4 || prec < 0 || prec > 2) return KInfo{};
     return tab[shape][prec](P, op, variant);
+}
+
+#define NIR_TDECL(s, p) KInfo nir_toe_kinfo_s##s##_p##p(int P);
+NIR_TDECL(0, 0) NIR_TDECL(0, 1) NIR_TDECL(0, 2)
+NIR_TDECL(1, 0) NIR_TDECL(1, 1) NIR_TDECL(1, 2)
+NIR_TDECL(2, 0) NIR_TDECL(2, 1) NIR_TDECL(2, 2)
+NIR_TDECL(3, 0) NIR_TDECL(3, 1) NIR_TDECL(3, 2)
+NIR_TDECL(4, 0) NIR_TDECL(4, 1) NIR_TDECL(4, 2)
+#undef NIR_TDECL
+
+KInfo nir_toe_kinfo(int shape, int P, int prec)
+{
+    typedef KInfo (*F)(int);
+    static const F tab[5][3] = {
+        {nir_toe_kinfo_s0_p0, nir_toe_kinfo_s0_p1, nir_toe_kinfo_s0_p2},
+        {nir_toe_kinfo_s1_p0, nir_toe_kinfo_s1_p1, nir_toe_kinfo_s1_p2},
+        {nir_toe_kinfo_s2_p0, nir_toe_kinfo_s2_p1, nir_toe_kinfo_s2_p2},
+        {nir_toe_kinfo_s3_p0, nir_toe_kinfo_s3_p1, nir_toe_kinfo_s3_p2},
+        {nir_toe_kinfo_s4_p0, nir_toe_kinfo_s4_p1, nir_toe_kinfo_s4_p2}};
+    if (shape < 0 || shape > 4 || prec < 0 || prec > 2) return KInfo{};
+    return tab[shape][prec](P);
 }
 
 size_t nir_prec_size(int prec) { return prec == NIR_F64 ? 8 : prec == NIR_F32 ? 4 : 2; }
@@ -97,6 +119,82 @@ const void *nir_geo_ptr(nir_block *b, int prec, bool lam)
 
 const void *nir_tab_ptr(nir_block *b, int prec) { return prec == NIR_F64 ? (const void *)b->tab64 : (const void *)b->tab32; }
 
+// --------------------------------------------------------------------------- threading over elements
+int nir_toe_prepare(nir_block *b, int prec, int grid)
+{
+    if (b->d.basis != NIR_BASIS_MODIFIED) return NIR_ERR_UNSUPPORTED;
+    KInfo ki = nir_toe_kinfo(b->d.shape, b->d.P, prec);
+    if (!ki.fn) return NIR_ERR_UNSUPPORTED;
+    const int occ = nir_occupancy(b->ctx, ki);  // also sets the kernel's shared-memory limit
+    if (occ < 0) return NIR_ERR_CUDA;
+    long long g = grid > 0 ? grid : (long long)occ * b->ctx->num_sms;
+    g = std::min<long long>(g, (b->d.nelem + ki.nt - 1) / ki.nt);  // no CTA without an element
+    const long long values = 5LL * b->NQ * g * ki.nt;  // scratch arrays x points x threads
+    if (values >= (1LL << 31)) return NIR_ERR_TOO_LARGE;  // the kernel indexes its scratch in 32 bits
+    const size_t bytes = (size_t)values * (prec == NIR_F64 ? 8 : 4);
+    if (bytes > b->toe_bytes) {
+        NIR_CUDA_TRY(cudaStreamSynchronize(b->ctx->stream));
+        if (b->toe_scr) cudaFree(b->toe_scr);
+        b->toe_scr = nullptr;
+        b->toe_bytes = 0;
+        if (cudaMalloc(&b->toe_scr, bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return NIR_ERR_NO_MEMORY;
+        }
+        b->toe_bytes = bytes;
+        // graphs captured with the old scratch (mesh, host pipeline, assembly) must be recaptured
+        b->geo_version++;
+    }
+    b->toe_grid[prec] = (int)g;
+    return NIR_OK;
+}
+
+void nir_toe_release(nir_block *b)
+{
+    for (int p = 0; p < 3; ++p)
+        if (b->helm_variant[p] == NIR_VARIANT_TOE) return;
+    if (!b->toe_scr) return;
+    cudaStreamSynchronize(b->ctx->stream);
+    cudaFree(b->toe_scr);
+    b->toe_scr = nullptr;
+    b->toe_bytes = 0;
+    b->geo_version++;  // as in nir_toe_prepare: graphs holding the scratch are out of date
+}
+
+namespace {
+
+constexpr long long kToeThreads = nirt::kThreads;
+
+// Helmholtz of elements [e_begin, e_begin + e_count) by the threading-over-
+// elements kernel; grid and scratch as prepared by nir_toe_prepare.
+int toe_launch(nir_block *b, int prec, double lambda, const void *in, void *out, long long e_begin,
+               long long e_count, cudaStream_t stream)
+{
+    KInfo ki = nir_toe_kinfo(b->d.shape, b->d.P, prec);
+    const long long g = std::min<long long>(b->toe_grid[prec], (e_count + kToeThreads - 1) / kToeThreads);
+    if (!ki.fn || g < 1 || !b->toe_scr || (size_t)(5LL * b->NQ * g * ki.nt) * (prec == NIR_F64 ? 8 : 4) > b->toe_bytes)
+        return NIR_ERR_STATE;
+    const size_t es = nir_prec_size(prec);
+    nirt::ToeArgs a;
+    a.in = (const char *)in + (size_t)e_begin * b->M * es;
+    a.out = (char *)out + (size_t)e_begin * b->M * es;
+    const size_t geo_off = b->geo_pp ? (size_t)e_begin * b->NQ * b->ng : (size_t)e_begin * b->ng;
+    a.geo = (const char *)nir_geo_ptr(b, prec, false) + geo_off * es;
+    a.tab = nir_tab_ptr(b, prec);
+    a.scr = b->toe_scr;
+    a.nelem = e_count;
+    a.lambda = lambda;
+    a.geo_pp = b->geo_pp;
+    void *args[] = {&a};
+    if (cudaLaunchKernel(ki.fn, dim3((unsigned)g), dim3(ki.nt), args, (size_t)ki.smem, stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return NIR_ERR_CUDA;
+    }
+    return NIR_OK;
+}
+
+}  // namespace
+
 // Launch one operator over elements [e_begin, e_begin + e_count) of a block.
 // Pointers are the block's full arrays; e_begin must be a multiple of 64 so
 // the 32-element interleaved factors stay aligned.
@@ -107,6 +205,11 @@ int nir_launch_op_range(nir_block *b, int prec, int op, double lambda, const voi
     if (e_begin < 0 || e_count < 1 || e_begin + e_count > b->d.nelem || (e_begin & 63)) return NIR_ERR_INVALID_ARG;
     const bool multi = op == nirk::OP_HELM && in1 != nullptr;  // a multi-field Helmholtz call
     int variant = (op == nirk::OP_HELM && prec >= 0 && prec < 3 && !multi) ? b->helm_variant[prec] : 0;
+    if (variant == NIR_VARIANT_TOE) {
+        int rc = nir_block_ensure_prec(b, prec);
+        if (rc) return rc;
+        return toe_launch(b, prec, lambda, in0, out0, e_begin, e_count, stream);
+    }
     KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, op, variant);
     if (!ki.fn) ki = nir_kinfo(b->d.shape, b->d.P, prec, op, 0);
     if (!ki.fn) return NIR_ERR_UNSUPPORTED;
@@ -274,6 +377,7 @@ extern "C" void nir_block_destroy(nir_block *b)
     if (b->L16) cudaFree(b->L16);
     if (b->stage_in) cudaFree(b->stage_in);
     if (b->stage_out) cudaFree(b->stage_out);
+    if (b->toe_scr) cudaFree(b->toe_scr);
     if (b->copy_in) {
         cudaStreamDestroy(b->copy_in);
         cudaStreamDestroy(b->copy_out);
@@ -533,12 +637,15 @@ int host_pipeline(nir_block *b, int prec, double lambda, const void *h_in, void 
     // each and the waves in between are split evenly over the other chunks.
     std::vector<long long> bounds{0};
     {
-        KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, nirk::OP_HELM, b->helm_variant[prec]);
+        const bool toe = b->helm_variant[prec] == NIR_VARIANT_TOE;
+        KInfo ki = toe ? nir_toe_kinfo(b->d.shape, b->d.P, prec)
+                       : nir_kinfo(b->d.shape, b->d.P, prec, nirk::OP_HELM, b->helm_variant[prec]);
         if (!ki.fn) ki = nir_kinfo(b->d.shape, b->d.P, prec, nirk::OP_HELM, 0);
         const int occ = ki.fn ? nir_occupancy(b->ctx, ki) : -1;
         long long wave = E;
         if (occ > 0) {
-            const long long grid = b->helm_grid[prec] > 0 ? b->helm_grid[prec] : (long long)occ * b->ctx->num_sms;
+            long long grid = b->helm_grid[prec] > 0 ? b->helm_grid[prec] : (long long)occ * b->ctx->num_sms;
+            if (toe) grid = b->toe_grid[prec];
             wave = ((grid * ki.epb + 63) / 64) * 64;
         }
         const long long waves = (E + wave - 1) / wave;
@@ -680,8 +787,13 @@ extern "C" int nir_helmholtz_host(nir_block *b, int prec, double lambda, const v
 // --------------------------------------------------------------------------- probe / misc
 extern "C" int nir_block_set_tuning(nir_block *b, int prec, int variant, int grid, int pf)
 {
-    if (!b || !valid_prec(prec) || variant < 0 || variant > 3 || grid < 0 || (pf != 0 && pf != 1))
+    if (!b || !valid_prec(prec) || variant < 0 || variant > NIR_VARIANT_TOE || grid < 0 || (pf != 0 && pf != 1))
         return NIR_ERR_INVALID_ARG;
+    if (variant == NIR_VARIANT_TOE) {
+        NIR_CUDA_TRY(cudaSetDevice(b->ctx->device));
+        int rc = nir_toe_prepare(b, prec, grid);
+        if (rc) return rc;
+    }
     b->helm_variant[prec] = variant;
     b->helm_grid[prec] = grid;
     b->helm_pf[prec] = pf;
@@ -702,7 +814,8 @@ extern "C" int nir_block_kernel_info(const nir_block *b, int prec, int op, int *
 {
     if (!b || !valid_prec(prec) || op < 0 || op > 5) return NIR_ERR_INVALID_ARG;
     const int variant = op == nirk::OP_HELM ? b->helm_variant[prec] : 0;
-    KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, op, variant);
+    KInfo ki = variant == NIR_VARIANT_TOE ? nir_toe_kinfo(b->d.shape, b->d.P, prec)
+                                          : nir_kinfo(b->d.shape, b->d.P, prec, op, variant);
     if (!ki.fn) ki = nir_kinfo(b->d.shape, b->d.P, prec, op, 0);
     if (!ki.fn) return NIR_ERR_UNSUPPORTED;
     cudaFuncAttributes fa;

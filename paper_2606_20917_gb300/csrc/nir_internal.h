@@ -30,6 +30,9 @@ struct KInfo {
 
 // Provided by the instantiation units (one per shape x precision).
 KInfo nir_kinfo(int shape, int P, int prec, int op, int variant);
+// The threading-over-elements Helmholtz kernel (Helmholtz variant 4).
+KInfo nir_toe_kinfo(int shape, int P, int prec);
+#define NIR_VARIANT_TOE 4
 
 struct nir_ctx {
     int device = 0;
@@ -54,8 +57,11 @@ struct nir_block {
     int helm_variant[3] = {0, 0, 0};          // tuned elements-per-CTA variant per precision
     int helm_grid[3] = {0, 0, 0};             // tuned grid size per precision (0: occupancy)
     int helm_pf[3] = {0, 0, 0};               // tuned L2 metric-prefetch policy per precision
+    int toe_grid[3] = {0, 0, 0};              // CTAs of the threading-over-elements kernel per precision
+    void *toe_scr = nullptr;                  // its per-thread scratch (shared by the precisions)
+    size_t toe_bytes = 0;
     bool geo_set = false;
-    unsigned geo_version = 0;                 // bumped by every nir_block_set_geometry
+    unsigned geo_version = 0;                 // bumped by every nir_block_set_geometry (and scratch moves)
     double *G64 = nullptr, *L64 = nullptr;    // metric (ng) and d eta/d x + W (nl)
     float *G32 = nullptr, *L32 = nullptr;
     void *G16 = nullptr, *L16 = nullptr;      // bfloat16 copies
@@ -82,6 +88,12 @@ int nir_launch_op(nir_block *blk, int prec, int op, double lambda, const void *i
 int nir_launch_op_range(nir_block *b, int prec, int op, double lambda, const void *in0, const void *in1,
                         const void *in2, void *out0, void *out1, void *out2, long long e_begin, long long e_count,
                         cudaStream_t stream, int grid_override);
+// Size the threading-over-elements scratch for `grid` CTAs (0: one wave at
+// the kernel's occupancy; at most one CTA per 128 elements) and record the
+// grid; never called during capture.
+int nir_toe_prepare(nir_block *b, int prec, int grid);
+// Free that scratch unless a precision of the block is tuned to use it.
+void nir_toe_release(nir_block *b);
 const void *nir_geo_ptr(nir_block *blk, int prec, bool lam);
 const void *nir_tab_ptr(nir_block *blk, int prec);
 int nir_occupancy(nir_ctx *ctx, const KInfo &ki);

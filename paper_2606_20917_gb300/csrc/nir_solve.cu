@@ -1,6 +1,7 @@
 // nir_solve.cu -- hybrid meshes: the persistent single-launch Helmholtz apply
 // over blocks of different shapes and orders, its CUDA-graph cache and the
-// autotuner (elements-per-CTA variants and grid sizes, JSON cache file).
+// autotuner (elements-per-CTA variants, the threading strategy and grid
+// sizes, JSON cache file).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -489,13 +490,18 @@ extern "C" int nir_tune(nir_mesh *m, const char *cache_path)
         // per-block elements-per-CTA variant and grid size
         for (auto *b : m->blocks) {
             char key[160];
-            std::snprintf(key, sizeof key, "%s|block|%d|%d|%d|%s", gpu.c_str(), b->d.shape, b->d.P, b->d.Q,
-                          pname[prec]);
+            std::snprintf(key, sizeof key, "%s|block|%d|%d|%d|%lld|%s", gpu.c_str(), b->d.shape, b->d.P, b->d.Q,
+                          (long long)b->d.nelem, pname[prec]);
             auto it = kv.find(key);
             if (it != kv.end()) {
                 b->helm_pf[prec] = 0;
                 std::sscanf(it->second.c_str(), "%d,%d,%d", &b->helm_variant[prec], &b->helm_grid[prec],
                             &b->helm_pf[prec]);
+                // a cache entry naming the threading-over-elements kernel gets its
+                // scratch here; an unknown variant falls back to 0
+                int &v = b->helm_variant[prec];
+                if (v == NIR_VARIANT_TOE && nir_toe_prepare(b, prec, b->helm_grid[prec]) != NIR_OK) v = 0;
+                if (v < 0 || v > NIR_VARIANT_TOE) v = 0;
                 continue;
             }
             float best = 1e30f;
@@ -517,9 +523,21 @@ extern "C" int nir_tune(nir_mesh *m, const char *cache_path)
                         if (t < best) { best = t; bv = v; bg = c * ctx->num_sms; bp = pf; }
                     }
             }
+            // the other threading strategy (one thread per element, Sec. 3.3): it
+            // only wins in FP64 on large high-order blocks, so it is timed in FP64
+            if (prec == NIR_F64 && !rc && nir_toe_prepare(b, prec, 0) == NIR_OK) {
+                b->helm_variant[prec] = NIR_VARIANT_TOE;
+                b->helm_grid[prec] = 0;
+                b->helm_pf[prec] = 0;
+                float t = time_ms(st, 5, [&] {
+                    if (!rc) rc = nir_launch_op(b, prec, 5, 1.0, x, nullptr, nullptr, y, nullptr, nullptr, st, 0);
+                });
+                if (t < best) { best = t; bv = NIR_VARIANT_TOE; bg = 0; bp = 0; }
+            }
             b->helm_variant[prec] = bv;
             b->helm_grid[prec] = bg;
             b->helm_pf[prec] = bp;
+            if (bv != NIR_VARIANT_TOE) nir_toe_release(b);
             char val[64];
             std::snprintf(val, sizeof val, "%d,%d,%d", bv, bg, bp);
             kv[key] = val;

@@ -207,7 +207,7 @@ def test_helmholtz_every_launch_variant(nir, ctx, prec, shape, P):
     blk.set_tuning(prec, 3, 0, 0)
     assert np.array_equal(run_op(blk, "helm", prec, x, 1.0), y0)   # same arithmetic, other allocation
     with pytest.raises(nir.NirError):
-        blk.set_tuning(prec, 4)
+        blk.set_tuning(prec, 5)
 
 
 @pytest.mark.parametrize("shape", ["quad", "tri", "hex", "prism", "tet"])
