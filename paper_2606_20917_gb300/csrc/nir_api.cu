@@ -133,7 +133,8 @@ int nir_toe_prepare(nir_block *b, int prec, int grid)
     if (values >= (1LL << 31)) return NIR_ERR_TOO_LARGE;  // the kernel indexes its scratch in 32 bits
     const size_t bytes = (size_t)values * (prec == NIR_F64 ? 8 : 4);
     if (bytes > b->toe_bytes) {
-        NIR_CUDA_TRY(cudaStreamSynchronize(b->ctx->stream));
+        // launches on other streams (a mesh's concurrent block branches) may still use it
+        NIR_CUDA_TRY(cudaDeviceSynchronize());
         if (b->toe_scr) cudaFree(b->toe_scr);
         b->toe_scr = nullptr;
         b->toe_bytes = 0;
@@ -154,7 +155,7 @@ void nir_toe_release(nir_block *b)
     for (int p = 0; p < 3; ++p)
         if (b->helm_variant[p] == NIR_VARIANT_TOE) return;
     if (!b->toe_scr) return;
-    cudaStreamSynchronize(b->ctx->stream);
+    cudaDeviceSynchronize();
     cudaFree(b->toe_scr);
     b->toe_scr = nullptr;
     b->toe_bytes = 0;
