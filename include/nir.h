@@ -202,9 +202,11 @@ int nir_helmholtz_host_noalloc(nir_block *blk, int prec, double lambda, const vo
  * elements: one thread per element runs all stages, its intermediate tensors
  * in library-owned global scratch of 5 Q^d values per thread of the grid
  * (allocated by this call, freed with the block; single-field Helmholtz
- * only, modified basis only; the autotuner never picks it).  grid = CTAs of
- * 128 threads (0: one wave at its occupancy).  A block's launches share that
- * scratch: calls on one block must not overlap on the GPU.
+ * only, modified basis only; the autotuner times it in FP64, where its
+ * results equal the other variants' bit for bit).  grid = CTAs of 128
+ * threads (0: one wave at its occupancy), at most one CTA per 128 elements.
+ * A block's launches share that scratch: calls on one block must not overlap
+ * on the GPU.
  * Errors: INVALID_ARG; with variant 4 also UNSUPPORTED (nodal basis),
  * TOO_LARGE (2^31 or more scratch values), NO_MEMORY, CUDA. */
 int nir_block_set_tuning(nir_block *blk, int prec, int variant, int grid, int pf);
@@ -296,8 +298,9 @@ enum { NIR_ASM_HELMHOLTZ = 0, NIR_ASM_MASS = 1 };
 
 /* Build the global numbering of conforming blocks of one shape (NIR_QUAD or
  * NIR_HEX), one P and one basis (NIR_BASIS_MODIFIED or
- * NIR_BASIS_GLL_LAGRANGE; the Lagrange numbering has all signs +1).  vertex_ids[b]: HOST int64 array [nelem_b][2^d] of the
- * global vertex ids of block b's elements, local vertex v = a + 2b (+ 4c) at
+ * NIR_BASIS_GLL_LAGRANGE; the Lagrange numbering has all signs +1).
+ * vertex_ids[b]: HOST int64 array [nelem_b][2^d] of the global vertex ids of
+ * block b's elements, local vertex v = a + 2b (+ 4c) at
  * reference coordinates xi = (-1+2a, -1+2b(, -1+2c)) -- the corners of the
  * geometry lattice of nir_block_set_geometry.  Elements may see shared faces
  * in any orientation.  The object keeps pointers to the blocks, which must
