@@ -180,7 +180,9 @@ int toe_launch(nir_block *b, int prec, double lambda, const void *in, void *out,
     a.in = (const char *)in + (size_t)e_begin * b->M * es;
     a.out = (char *)out + (size_t)e_begin * b->M * es;
     const size_t geo_off = b->geo_pp ? (size_t)e_begin * b->NQ * b->ng : (size_t)e_begin * b->ng;
-    a.geo = (const char *)nir_geo_ptr(b, prec, false) + geo_off * es;
+    const void *g0 = nir_geo_ptr(b, prec, false);
+    if (!g0) return NIR_ERR_STATE;  // geometry not set (the entry points check this first)
+    a.geo = (const char *)g0 + geo_off * es;
     a.tab = nir_tab_ptr(b, prec);
     a.scr = b->toe_scr;
     a.nelem = e_count;
