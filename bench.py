@@ -263,8 +263,10 @@ def workload_config(args, wl):
     return cfg
 
 
-def cpu_baseline(args, wl, budget_s: float = 15.0):
-    """Oracle timed on a bounded seeded sample (rank 0, N = 1 only)."""
+def cpu_baseline(args, wl, budget_s: float = 15.0, y_gpu=None):
+    """Oracle timed on a bounded seeded sample (rank 0, N = 1 only).  With the
+    GPU result y_gpu [E][M] (FP64), also its error against the oracle on that
+    sample."""
     import oracle
     shape, P, Q, g = wl["shape"], wl["P"], wl["Q"], wl["gorder"]
     M = oracle.num_modes(shape, P)
@@ -274,13 +276,137 @@ def cpu_baseline(args, wl, budget_s: float = 15.0):
     while True:
         ids = W.sample_elements(E, k, seed=0)
         t0 = time.perf_counter()
-        oracle.helmholtz(shape, P, Q, g, np.ascontiguousarray(wl["nodes"][ids]), 1.0, u_all[ids])
+        y_or = oracle.helmholtz(shape, P, Q, g, np.ascontiguousarray(wl["nodes"][ids]), 1.0, u_all[ids])
         dt = time.perf_counter() - t0
         if dt > budget_s / 4 or k >= E:
             break
         k = min(E, int(k * max(2.0, budget_s / 4 / max(dt, 1e-3))))
-    return {"value": k * M / dt / 1e9, "unit": "GDOF/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{k} seeded elements of {E}, one dense-matrix Helmholtz apply each"}
+    out = {"value": k * M / dt / 1e9, "unit": "GDOF/s", "cores": oracle.threads(), "kind": "oracle",
+           "sample": f"{k} seeded elements of {E}, one dense-matrix Helmholtz apply each"}
+    if y_gpu is not None:
+        out["gpu_rel_error_on_sample"] = rel_err(y_gpu[ids], y_or)
+    return out
+
+
+def time_calls(fn, stream, reps: int) -> float:
+    """Seconds per call: CUDA events on the launching stream around `reps`
+    calls, after 3 untimed ones."""
+    import torch
+    for _ in range(3):
+        fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps * 1e-3
+
+
+def roofline_entry(prec, flops, nbytes, sec, fp64_peak, peaks):
+    """FP64: FP64-pipe bound (flops / measured DFMA peak); FP32/BF16: HBM bound
+    (algorithmic bytes / measured copy bandwidth)."""
+    if prec == "f64":
+        ach = flops / sec / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak}
+    ach = nbytes / sec / 1e9
+    pk = peaks.get("hbm_gbs", 6800.0)
+    return {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk}
+
+
+CONFIG_WORKLOADS = ("quad8x8_p4", "tet20_kuhn_p4", "prism40x40x20_p4")
+
+
+def config_table(nir, ctx, dev, stream, peaks, fp64_peak, args):
+    """FP64 and FP32 Helmholtz apply rates, roofline fractions and sampled
+    errors against the oracle on the other workloads: the 8x8 quad mesh, the
+    Kuhn-split tet mesh, the prism mesh and the ~150k-element hybrid mesh (one
+    graph launch per apply).  Each is tuned first (set-up, untimed)."""
+    import torch
+    import oracle
+    out = {}
+    for name in CONFIG_WORKLOADS:
+        wl = W.workload(name)
+        shape, P, Q, g = wl["shape"], wl["P"], wl["Q"], wl["gorder"]
+        E = wl["nodes"].shape[0]
+        blk = nir.Block(ctx, shape, E, P, deformed=wl["deformed"])
+        blk.set_geometry(g, torch.from_numpy(wl["nodes"]).to(dev))
+        if not args.no_tune:
+            nir.Mesh(ctx, [blk]).tune(args.tune_cache)
+        u64 = W.coefficients(E, blk.M, seed=0)
+        ids = W.sample_elements(E, 16, seed=5)
+        y_or = oracle.helmholtz(shape, P, Q, g, np.ascontiguousarray(wl["nodes"][ids]), 1.0, u64[ids])
+        rec = {"shape": shape, "nelem": E, "P": P, "Q": Q, "dof": E * blk.M}
+        reps = max(20, min(500, int(4e8 / (E * blk.M))))
+        for prec in ("f64", "f32"):
+            u = torch.from_numpy(u64).to(dev, nir.DTYPE[prec])
+            y = torch.empty_like(u)
+            sec = time_calls(lambda: blk.helmholtz(u, prec=prec, out=y), stream, reps)
+            wb = u.element_size()
+            rec[prec] = {"gdofs": E * blk.M / sec / 1e9, "ms_per_apply": sec * 1e3,
+                         "roofline": roofline_entry(prec, E * helm_flops_per_elem(shape, P + 1, Q),
+                                                    E * helm_bytes_per_elem(shape, P + 1, Q, wb, wl["deformed"]),
+                                                    sec, fp64_peak, peaks),
+                         "rel_error_vs_oracle": rel_err(y.double().cpu().numpy()[ids], y_or)}
+        out[name] = rec
+        del blk, u, y
+    parts = W.hybrid_mesh(seed=0)
+    blocks = []
+    for p in parts:
+        b = nir.Block(ctx, p["shape"], p["nodes"].shape[0], p["P"], deformed=p["deformed"])
+        b.set_geometry(p["gorder"], torch.from_numpy(p["nodes"]).to(dev))
+        blocks.append(b)
+    mesh = nir.Mesh(ctx, blocks)
+    if not args.no_tune:
+        mesh.tune(args.tune_cache)
+    x64 = W.coefficients(1, mesh.ndof, seed=0)[0]
+    samples = []
+    for b, o, p in zip(blocks, mesh.offsets, parts):
+        ids = W.sample_elements(b.nelem, 2, seed=p["P"])
+        ref = oracle.helmholtz(p["shape"], p["P"], p["Q"], p["gorder"], np.ascontiguousarray(p["nodes"][ids]), 1.0,
+                               x64[o:o + b.nelem * b.M].reshape(b.nelem, b.M)[ids])
+        samples.append((o, b, ids, ref))
+    rec = {"nelem": sum(b.nelem for b in blocks), "dof": mesh.ndof, "blocks": len(blocks)}
+    for prec in ("f64", "f32"):
+        x = torch.from_numpy(x64).to(dev, nir.DTYPE[prec])
+        y = torch.empty_like(x)
+        sec = time_calls(lambda: mesh.helmholtz(x, prec=prec, out=y), stream, 20)
+        wb = x.element_size()
+        flops = sum(p["nodes"].shape[0] * helm_flops_per_elem(p["shape"], p["P"] + 1, p["Q"]) for p in parts)
+        nbytes = sum(p["nodes"].shape[0] * helm_bytes_per_elem(p["shape"], p["P"] + 1, p["Q"], wb, p["deformed"])
+                     for p in parts)
+        yh = y.double().cpu().numpy()
+        got = np.concatenate([yh[o:o + b.nelem * b.M].reshape(b.nelem, b.M)[ids].ravel() for o, b, ids, _ in samples])
+        want = np.concatenate([r.ravel() for *_, r in samples])
+        rec[prec] = {"gdofs": mesh.ndof / sec / 1e9, "ms_per_apply": sec * 1e3, "launch": mesh.get_launch(prec),
+                     "roofline": roofline_entry(prec, flops, nbytes, sec, fp64_peak, peaks),
+                     "rel_error_vs_oracle": rel_err(got, want)}
+    out["hybrid150k_p2to8"] = rec
+    return out
+
+
+def solve_section(nir, ctx, dev, args, local):
+    """The P = 6 48^3 curved-hex solve: every solver variant, with wall time,
+    iterations, residual, forward error against the oracle and speed-up over
+    plain FP64 CG."""
+    import torch
+    wl = W.workload("hex48_curved_p6")
+    E = wl["nodes"].shape[0]
+    blk = nir.Block(ctx, wl["shape"], E, wl["P"], deformed=wl["deformed"])
+    blk.set_geometry(wl["gorder"], torch.from_numpy(wl["nodes"]).to(dev))
+    mesh = nir.Mesh(ctx, [blk])
+    if not args.no_tune:
+        mesh.tune(args.tune_cache)
+    results, ndof = solve_compare(nir, mesh, blk, wl, dev, args, 1, local, args.solve_precs.split(","))
+    best = max((k for k, r in results.items() if k != "f64" and r["rc"] == 0), key=lambda k: results[k]["gdofs"],
+               default=None)
+    return {"workload": "hex48_curved_p6", "nelem": E, "P": wl["P"], "Q": wl["Q"], "dof": ndof,
+            "tol": args.tol, "fwd_tol": args.fwd_tol, "inner_tol": args.inner_tol,
+            "solve": "CG on the broken operator, Jacobi preconditioner; rhs B^T W f, "
+                     "f = (3 pi^2 + 1) sin(pi x) sin(pi y) sin(pi z)",
+            "variants": results, "fastest": best,
+            "speedup_vs_fp64_cg": results[best]["speedup_vs_fp64_cg"] if best else None}
 
 
 def run_nir(args, ws, rank, local):
@@ -423,7 +549,12 @@ def run_nir(args, ws, rank, local):
     if extras:
         line["extras"] = extras
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args, wl)
+        line["cpu_baseline"] = cpu_baseline(args, wl, y_gpu=y.double().cpu().numpy() if args.prec == "f64" else None)
+    if ws == 1 and not args.no_configs:
+        fp64_pk = roof["peak"] if args.prec == "f64" else ctx.probe_fp64_peak()
+        line["configs"] = config_table(nir, ctx, dev, stream, peaks, fp64_pk, args)
+    if ws == 1 and not args.no_solve:
+        line["solve"] = solve_section(nir, ctx, dev, args, local)
     print(json.dumps(line), flush=True)
 
 
@@ -475,6 +606,87 @@ def operator_table(blk, prec, dev, stream, wl, ctx, peaks, fp64_peak):
     return res
 
 
+# Solver variants compared on the P = 6 workload: name -> (operator precision
+# inside CG, inner-solver vector precision).  "f64" is plain FP64 CG.
+SOLVE_VARIANTS = {
+    "f64": ("f64", "f64"),
+    "f32": ("f32", "f64"),        # FP32 operator, FP64 inner vectors and dots
+    "f32_vec32": ("f32", "f32"),  # FP32 operator, FP32 inner vectors, compensated dots
+    "bf16": ("bf16", "f64"),      # BF16 storage operator, FP64 inner vectors
+}
+
+
+def rel_err(a, b) -> float:
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def oracle_solve_sample(wl, ids, lam):
+    """The oracle's own solution on sampled elements: right-hand side
+    b = B^T W f with f = (3 pi^2 + lam) sin(pi x) sin(pi y) sin(pi z) at the
+    oracle's quadrature points (its own geometry), then the per-element dense
+    Cholesky solve of the broken operator."""
+    import oracle
+    shape, P, Q, g = wl["shape"], wl["P"], wl["Q"], wl["gorder"]
+    nodes = np.ascontiguousarray(wl["nodes"][ids])
+    _, _, X = oracle.geom_factors(shape, Q, g, nodes, with_x=True)
+    s = np.sin(np.pi * X)
+    f = (3 * np.pi ** 2 + lam) * s[..., 0] * s[..., 1] * s[..., 2]
+    bs = oracle.iprod(shape, P, Q, g, nodes, f)
+    return oracle.helmholtz_solve(shape, P, Q, g, nodes, lam, bs)
+
+
+def solve_compare(nir, mesh, blk, wl, dev, args, ws, local, variants, sample=8):
+    """Time each solver variant once (after a loose warm-up solve that captures
+    its iteration graphs and builds the preconditioner) on the manufactured
+    right-hand side, to relative residual args.tol and forward tolerance
+    args.fwd_tol; report its error against the oracle's per-element Cholesky
+    solution on a seeded sample of elements."""
+    import torch
+    lam = 1.0
+    E, M = blk.nelem, blk.M
+    eta, xi = blk.points()
+    f = manufactured_rhs_points(wl, xi, lam, dev)
+    b = blk.iproduct_wrt_base(f).reshape(-1).contiguous()
+    del f
+    ids = W.sample_elements(E, sample, seed=11)
+    x_or = oracle_solve_sample(wl, ids, lam) if ws == 1 or int(os.environ.get("RANK", "0")) == 0 else None
+    results, xs = {}, {}
+    for name in variants:
+        inner, vec = SOLVE_VARIANTS[name]
+        kw = dict(lam=lam, inner_prec=inner, inner_vectors=vec, tol=args.tol, fwd_tol=args.fwd_tol, max_outer=60,
+                  max_inner=args.max_inner if inner != "bf16" else min(args.max_inner, 3000),
+                  inner_tol=args.inner_tol)
+        mesh.cg_solve(b, torch.zeros_like(b), **dict(kw, tol=1e-2, fwd_tol=0.0))
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        barrier(ws)
+        with ClockSampler(local) as clk, ProfileRegion(args.profile_region):
+            t0 = time.perf_counter()
+            rc, st = mesh.cg_solve(b, x, **kw)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        dt = max_over_ranks(ws, dt, dev)
+        r = dict(rc=rc, operator=inner, inner_vectors=vec if inner != "f64" else "f64", wall_seconds=dt,
+                 gdofs=ws * b.numel() / dt / 1e9, outer=st["outer"], inner_total=st["inner_total"],
+                 rel_residual=st["rel_residual"], rel_correction=st["rel_correction"], clocks=clk.summary())
+        if x_or is not None:
+            r["fwd_error_vs_oracle"] = rel_err(x.view(E, M)[torch.from_numpy(ids).to(dev)].cpu().numpy(), x_or)
+            r["oracle_sample"] = f"{len(ids)} seeded elements of {E}: oracle b = B^T W f and dense Cholesky"
+        results[name] = r
+        xs[name] = x
+    if "f64" in xs:
+        ref = xs["f64"]
+        for name, x in xs.items():
+            if name != "f64":
+                results[name]["rel_diff_vs_fp64_cg"] = float(torch.linalg.norm(x - ref) / torch.linalg.norm(ref))
+    base = results.get("f64")
+    ok = base is not None and base["rc"] == 0
+    for name, r in results.items():
+        if name != "f64":
+            r["speedup_vs_fp64_cg"] = (base["wall_seconds"] / r["wall_seconds"]) if (ok and r["rc"] == 0) else None
+    return results, b.numel()
+
+
 def run_solve(args, ws, rank, local):
     """Helmholtz solve on the P = 6 curved-hex workload: plain FP64 CG versus CG
     with the operator in FP32 / BF16 inside FP64 iterative refinement."""
@@ -491,41 +703,19 @@ def run_solve(args, ws, rank, local):
     mesh = nir.Mesh(ctx, [blk])
     if not args.no_tune:
         mesh.tune(args.tune_cache)  # set-up, untimed
-    # right-hand side b = B^T W f for f = (3 pi^2 + lambda) sin(pi x) sin(pi y) sin(pi z)
-    eta, xi = blk.points()
-    lam = 1.0
-    f = manufactured_rhs_points(wl, xi, lam, dev)
-    b = blk.iproduct_wrt_base(f).reshape(-1).contiguous()
-    results = {}
-    for inner in args.solve_precs.split(","):
-        x = torch.zeros_like(b)
-        # warm-up solve (graph capture, preconditioner), then the timed solve
-        mesh.cg_solve(b, torch.zeros_like(b), lam=lam, inner_prec=inner, tol=args.tol, max_outer=60,
-                      max_inner=args.max_inner, inner_tol=args.inner_tol)
-        torch.cuda.synchronize()
-        barrier(ws)
-        with ClockSampler(local) as clk, ProfileRegion(args.profile_region):
-            t0 = time.perf_counter()
-            rc, st = mesh.cg_solve(b, x, lam=lam, inner_prec=inner, tol=args.tol, max_outer=60,
-                                   max_inner=args.max_inner, inner_tol=args.inner_tol)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-        dt = max_over_ranks(ws, dt, dev)
-        results[inner] = dict(rc=rc, wall_seconds=dt, gdofs=ws * b.numel() / dt / 1e9, clocks=clk.summary(),
-                              outer=st["outer"], inner_total=st["inner_total"], rel_residual=st["rel_residual"])
+    results, ndof = solve_compare(nir, mesh, blk, wl, dev, args, ws, local, args.solve_precs.split(","))
     if rank != 0:
         return
     best = max((r for k, r in results.items() if k != "f64" and r["rc"] == 0), key=lambda r: r["gdofs"],
                default=None)
-    base = results.get("f64")
-    line = {"metric": "Helmholtz solve GDOF/s to relative residual %g" % args.tol,
+    line = {"metric": "Helmholtz solve GDOF/s to relative residual %g, forward tolerance %g" % (args.tol, args.fwd_tol),
             "value": best["gdofs"] if best else None, "unit": "GDOF/s", "n_gpus": ws, "steps": 1,
             "warmup": 1, "ms_per_step": best["wall_seconds"] * 1e3 if best else None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 operator / f64 refinement", "data": "synthetic",
             "config": dict(workload_config(args, wl), solve="CG on the broken operator, Jacobi preconditioner",
                            rhs="B^T W f, f = (3 pi^2 + 1) sin(pi x) sin(pi y) sin(pi z)"),
             "solves": results,
-            "speedup_vs_fp64_cg": (best["gdofs"] / base["gdofs"]) if (best and base and base["rc"] == 0) else None}
+            "speedup_vs_fp64_cg": best.get("speedup_vs_fp64_cg") if best else None}
     print(json.dumps(line), flush=True)
 
 
@@ -611,25 +801,27 @@ def run_gsolve(args, ws, rank, local):
     b = asm.assemble(blk.iproduct_wrt_base(f).reshape(-1))
     umax = float(u.abs().max())
     results = {}
-    for inner in args.solve_precs.split(","):
+    for name in args.solve_precs.split(","):
+        inner, vec = SOLVE_VARIANTS[name]
+        kw = dict(lam=lam, inner_prec=inner, inner_vectors=vec, tol=args.tol, max_outer=60,
+                  max_inner=args.max_inner, inner_tol=args.inner_tol)
         x = up.clone()
         x[:asm.n_free] = 0.0
         xw = x.clone()
-        asm.cg_solve(b, xw, lam=lam, inner_prec=inner, tol=args.tol, max_outer=60, max_inner=args.max_inner,
-                     inner_tol=args.inner_tol)  # warm-up: graph capture, preconditioner
+        asm.cg_solve(b, xw, **dict(kw, tol=1e-2))  # warm-up: graph capture, preconditioner
         del xw
         torch.cuda.synchronize()
         barrier(ws)
         with ClockSampler(local) as clk, ProfileRegion(args.profile_region):
             t0 = time.perf_counter()
-            rc, st = asm.cg_solve(b, x, lam=lam, inner_prec=inner, tol=args.tol, max_outer=60,
-                                  max_inner=args.max_inner, inner_tol=args.inner_tol)
+            rc, st = asm.cg_solve(b, x, **kw)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
         dt = max_over_ranks(ws, dt, dev)
         uq = blk.bwd_trans(asm.gather(x).view(E, blk.M))
         err = float((uq - u).abs().max()) / umax
-        results[inner] = dict(rc=rc, wall_seconds=dt, gdofs=ws * asm.n_free / dt / 1e9,
+        results[name] = dict(rc=rc, operator=inner, inner_vectors=vec, wall_seconds=dt,
+                              gdofs=ws * asm.n_free / dt / 1e9,
                               gdofs_local=ws * E * blk.M / dt / 1e9, clocks=clk.summary(), outer=st["outer"],
                               inner_total=st["inner_total"], rel_residual=st["rel_residual"],
                               max_rel_error_vs_exact=err)
@@ -834,6 +1026,10 @@ def main():
     ap.add_argument("--extras", action="store_true", help="also time the FP32/BF16 applies")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-operators", action="store_true", help="skip the per-operator table")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="apply mode: skip the quad/tet/prism/hybrid apply table")
+    ap.add_argument("--no-solve", action="store_true",
+                    help="apply mode: skip the P = 6 solve comparison")
     ap.add_argument("--mode", choices=["apply", "solve", "gsolve", "hybrid", "sweep"], default="apply")
     ap.add_argument("--basis", choices=["modified", "nodal"], default="modified",
                     help="apply mode: expansion basis (nodal = GLL-Lagrange, quad/hex)")
@@ -842,8 +1038,11 @@ def main():
     ap.add_argument("--sweep-no-toe", action="store_true", help="sweep the default strategy only")
     ap.add_argument("--strategy", choices=["groups", "elements"], default="groups",
                     help="apply mode: the default kernels (element groups per CTA) or threading over elements")
-    ap.add_argument("--solve-precs", default="f64,f32,bf16")
+    ap.add_argument("--solve-precs", default="f64,f32,f32_vec32,bf16",
+                    help="solver variants: " + ",".join(SOLVE_VARIANTS))
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--fwd-tol", type=float, default=1e-10,
+                    help="solves: also stop only when the last correction |dx| <= fwd_tol |x|")
     ap.add_argument("--inner-tol", type=float, default=1e-3)
     ap.add_argument("--max-inner", type=int, default=20000)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner set-up")

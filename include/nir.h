@@ -253,23 +253,54 @@ typedef struct {
     double tol;            /* target ||b - H x|| / ||b|| (FP64 residual) */
     int max_outer;         /* refinement sweeps (ignored for plain FP64 CG) */
     int max_inner;         /* CG iterations per sweep (total for plain CG) */
-    double inner_tol;      /* relative residual reduction per refinement sweep */
+    double inner_tol;      /* relative residual reduction per refinement sweep
+                              (plain CG: per polishing sweep, see fwd_tol;
+                              0 there means 1e-3) */
     int jacobi;            /* 1: diagonal (Jacobi) preconditioner */
+    int inner_vectors;     /* storage and arithmetic of the inner solver's
+                              vectors (correction, residual, preconditioned
+                              residual, search direction) and of its dot
+                              products: NIR_F64 (0, the default when the struct
+                              is zero-initialised): FP64 vectors, FP64 updates
+                              and dots; the operator reads an FP32/BF16 copy of
+                              the search direction and returns H p in its own
+                              type.  NIR_F32: FP32 vectors and updates, dots of
+                              exact FP32 products with compensated summation,
+                              per-thread partials summed in FP64 (faster on
+                              GB300, whose FP64 rate is a small fraction of
+                              FP32).  Ignored for plain FP64 CG. */
+    double fwd_tol;        /* > 0: also require the last correction to be
+                              small, ||dx|| <= fwd_tol ||x||, which bounds the
+                              forward error ||x - H^-1 b|| / ||x|| (the error
+                              left after a correction is a fraction of that
+                              correction).  Mixed precision: dx is the last
+                              refinement sweep's update.  Plain FP64 CG: once
+                              the residual meets tol, CG continues in
+                              polishing sweeps that each cut the residual by
+                              inner_tol, and dx is one sweep's update.
+                              0: stop on the residual alone. */
 } nir_cg_opts;
 
 typedef struct {
-    int outer;             /* refinement sweeps done */
+    int outer;             /* refinement (plain CG: restart/polishing) sweeps */
     int inner_total;       /* operator applies in the inner solver */
     double rel_residual;   /* final ||b - H x|| / ||b|| in FP64 */
     double seconds;        /* wall time of the solve */
+    double rel_correction; /* ||dx|| / ||x|| of the last sweep's update (the
+                              forward-error estimate of fwd_tol; 0 when no
+                              sweep measured it) */
 } nir_cg_stats;
 
 /* Solve (L + lambda M) x = b on the mesh's broken (element-block-diagonal)
  * operator.  b, x: DEVICE FP64 [ndof]; x holds the initial guess on entry.
  * Plain CG when inner_prec == NIR_F64; otherwise CG in inner_prec on the
- * defect equation inside FP64 iterative refinement.  Residuals, dot products
- * and the refinement update are FP64 on the GPU.  Synchronous.  Errors:
- * INVALID_ARG, NOT_CONVERGED, NONFINITE, CUDA, NO_MEMORY. */
+ * defect equation inside FP64 iterative refinement: r = b - H x in FP64,
+ * solve H_lo d = r / |r| to inner_tol, x += |r| d, until |r| / |b| <= tol (and
+ * the correction meets fwd_tol when set).  The refinement residual, the
+ * update of x and (with inner_vectors = NIR_F64) the inner CG's residuals,
+ * search directions and dot products are FP64 on the GPU.  Synchronous.
+ * Errors: INVALID_ARG, NOT_CONVERGED (iteration or sweep cap, stalled
+ * refinement, CG breakdown), NONFINITE, CUDA, NO_MEMORY. */
 int nir_cg_solve(nir_mesh *mesh, double lambda, const double *b, double *x, const nir_cg_opts *opts,
                  nir_cg_stats *stats);
 

@@ -42,12 +42,23 @@ BASIS = {"modified": 0, "nodal": 1}
 
 class CGOpts(C.Structure):
     _fields_ = [("inner_prec", C.c_int), ("tol", C.c_double), ("max_outer", C.c_int),
-                ("max_inner", C.c_int), ("inner_tol", C.c_double), ("jacobi", C.c_int)]
+                ("max_inner", C.c_int), ("inner_tol", C.c_double), ("jacobi", C.c_int),
+                ("inner_vectors", C.c_int), ("fwd_tol", C.c_double)]
 
 
 class CGStats(C.Structure):
     _fields_ = [("outer", C.c_int), ("inner_total", C.c_int), ("rel_residual", C.c_double),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("rel_correction", C.c_double)]
+
+
+def _cg_opts(inner_prec, tol, max_outer, max_inner, inner_tol, jacobi, inner_vectors, fwd_tol):
+    return CGOpts(PREC[inner_prec], float(tol), int(max_outer), int(max_inner), float(inner_tol), int(jacobi),
+                  PREC[inner_vectors], float(fwd_tol))
+
+
+def _cg_stats(s):
+    return dict(outer=s.outer, inner_total=s.inner_total, rel_residual=s.rel_residual, seconds=s.seconds,
+                rel_correction=s.rel_correction)
 
 
 _SIGS = {
@@ -357,15 +368,17 @@ class Mesh:
         return {0: "persistent", 1: "blocks"}[v.value]
 
     def cg_solve(self, b, x, lam=1.0, inner_prec="f32", tol=1e-10, max_outer=50, max_inner=2000,
-                 inner_tol=1e-4, jacobi=True):
+                 inner_tol=1e-4, jacobi=True, inner_vectors="f64", fwd_tol=0.0):
+        """Returns (status code, stats dict); x is updated in place.  inner_vectors:
+        "f64" (FP64 inner vectors and dots) or "f32"; fwd_tol > 0 also requires the
+        last correction |dx| <= fwd_tol |x| (see nir_cg_opts)."""
         for t in (b, x):
             if t.dtype != torch.float64 or not t.is_cuda or t.numel() != self.ndof:
                 raise ValueError("b and x must be FP64 CUDA vectors of the mesh's dofs")
-        o = CGOpts(PREC[inner_prec], float(tol), int(max_outer), int(max_inner), float(inner_tol), int(jacobi))
+        o = _cg_opts(inner_prec, tol, max_outer, max_inner, inner_tol, jacobi, inner_vectors, fwd_tol)
         s = CGStats()
         rc = _lib.nir_cg_solve(self.h, float(lam), _ptr(b), _ptr(x), C.byref(o), C.byref(s))
-        return rc, dict(outer=s.outer, inner_total=s.inner_total, rel_residual=s.rel_residual,
-                        seconds=s.seconds)
+        return rc, _cg_stats(s)
 
 
 ASM_OPS = {"helmholtz": 0, "mass": 1}
@@ -447,13 +460,12 @@ class Assembly:
         return out
 
     def cg_solve(self, b, x, op="helmholtz", lam=1.0, fix_boundary=True, inner_prec="f32", tol=1e-10,
-                 max_outer=50, max_inner=5000, inner_tol=1e-3, jacobi=True):
-        """Returns (status code, stats dict); x is updated in place."""
+                 max_outer=50, max_inner=5000, inner_tol=1e-3, jacobi=True, inner_vectors="f64", fwd_tol=0.0):
+        """Returns (status code, stats dict); x is updated in place (options as Mesh.cg_solve)."""
         self._vec(b, self.n_global, "f64", "b")
         self._vec(x, self.n_global, "f64", "x")
-        o = CGOpts(PREC[inner_prec], float(tol), int(max_outer), int(max_inner), float(inner_tol), int(jacobi))
+        o = _cg_opts(inner_prec, tol, max_outer, max_inner, inner_tol, jacobi, inner_vectors, fwd_tol)
         s = CGStats()
         rc = _lib.nir_asm_cg_solve(self.h, ASM_OPS[op], float(lam), int(bool(fix_boundary)), _ptr(b), _ptr(x),
                                    C.byref(o), C.byref(s))
-        return rc, dict(outer=s.outer, inner_total=s.inner_total, rel_residual=s.rel_residual,
-                        seconds=s.seconds)
+        return rc, _cg_stats(s)

@@ -812,7 +812,7 @@ extern "C" int nir_asm_cg_solve(nir_asm *a, int op, double lambda, int fix_bound
     }
     if (op == NIR_ASM_MASS) lambda = 0.0;
     if (a->ops[op][fix_boundary]->n() == 0) {  // every dof held: nothing to solve
-        if (stats) *stats = nir_cg_stats{0, 0, 0.0, 0.0};
+        if (stats) *stats = nir_cg_stats{0, 0, 0.0, 0.0, 0.0};
         return NIR_OK;
     }
     return nir_cg_run(*a->ops[op][fix_boundary], a->cg[op][fix_boundary], lambda, b, x, o, stats);

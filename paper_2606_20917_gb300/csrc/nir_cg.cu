@@ -7,8 +7,14 @@
 // paragraph); the solver itself is not described there.  Mixed precision:
 //   r = b - H64 x                      (FP64 operator, FP64 vectors)
 //   repeat: solve H_lo d = r / |r| by preconditioned CG with the operator in
-//           FP32 (or BF16 storage), FP32 vectors and FP64 dot products;
-//           x += |r| d;  r = b - H64 x   until |r| / |b| <= tol.
+//           FP32 (or BF16 storage) and FP64 vectors and dot products (or, as
+//           an option, FP32 vectors with FP64-accurate dots);
+//           x += |r| d;  r = b - H64 x   until |r| / |b| <= tol and, when a
+//           forward tolerance is set, |r| |d| <= fwd_tol |x|.
+// The last test is the forward-error criterion: the error of x before a sweep
+// is what that sweep's correction estimates, and the error after it is a
+// fraction of it (the inner solve's accuracy), so a small correction bounds
+// the forward error of the result.
 // The Jacobi preconditioner's diagonal comes from the operator (for the mesh
 // operator by probing: it is block diagonal per element with the same mode
 // numbering in every element of a block, so applying it to the vector that is
@@ -365,18 +371,50 @@ __global__ void k_residual(double *r, const double *b, const double *Ax, long lo
         r[i] = b[i] - Ax[i];
 }
 
-// lo = scale * r (rounded to FP32)
-__global__ void k_scale_to_f32(float *lo, const double *r, double scale, long long n)
+// out = scale * r in the inner solver's vector type (out may be r for FP64)
+template <class V>
+__global__ void k_scale_to(V *out, const double *r, double scale, long long n)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        lo[i] = (float)(scale * r[i]);
+        st_v(out + i, scale * r[i]);
 }
 
 // x += scale * d
-__global__ void k_correct(double *x, const float *d, double scale, long long n)
+template <class V>
+__global__ void k_correct(double *x, const V *d, double scale, long long n)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        x[i] += scale * (double)d[i];
+        x[i] += scale * to_d(d[i]);
+}
+
+// out[0] = |a - b|^2, out[1] = |a|^2 (FP64)
+__global__ void __launch_bounds__(kThreads) k_diff_norms(const double *__restrict__ a, const double *__restrict__ b,
+                                                         long long n, double *part, unsigned *ticket, double *out)
+{
+    const long long S = (long long)gridDim.x * kThreads;
+    double v[2] = {0.0, 0.0};
+    for (long long i0 = blockIdx.x * (long long)kThreads + threadIdx.x; i0 < n; i0 += S * kU) {
+        double av[kU], bv[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const long long i = i0 + k * S, j = i < n ? i : i0;
+            av[k] = a[j];
+            bv[k] = b[j];
+        }
+#pragma unroll
+        for (int k = 0; k < kU; ++k)
+            if (i0 + k * S < n) {
+                const double d = av[k] - bv[k];
+                v[0] += d * d;
+                v[1] += av[k] * av[k];
+            }
+    }
+    block_sum(v);
+    double t[2];
+    if (finish_reduce(v, part, ticket, t)) {
+        out[0] = t[0];
+        out[1] = t[1];
+    }
 }
 
 template <class V>
@@ -431,7 +469,9 @@ struct CGWork {
     long long n = 0;              // unknowns
     long long n_full = 0;         // entries of x (unknowns, then fixed values)
     int grid = 0;                 // CTAs of the vector kernels
+    // x64: plain CG's solution copy, or the FP64 inner solver's correction d
     double *x64 = nullptr, *r64 = nullptr, *z64 = nullptr, *p64 = nullptr, *Ap64 = nullptr;
+    double *xs64 = nullptr;       // plain CG: x before a polishing sweep (allocated on first use)
     float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *d32 = nullptr;
     __nv_bfloat16 *pb16 = nullptr, *Apb16 = nullptr;
     double *dinv64 = nullptr;
@@ -439,22 +479,24 @@ struct CGWork {
     double *part = nullptr;       // 2 * grid partials
     unsigned *ticket = nullptr;
     CGScal *scal = nullptr;
-    double *dots = nullptr;       // scratch scalars
+    double *dots = nullptr;       // scratch scalars: |r|^2, |b|^2, |d|^2 (or |dx|^2), |x|^2
     int *flag = nullptr;
     bool diag_ready = false;
     double diag_lambda = 0.0;
-    // chunk graphs per inner precision (0: FP64 plain, 1: FP32, 2: BF16)
-    cudaGraphExec_t chunk[3] = {nullptr, nullptr, nullptr};
-    double chunk_lambda[3] = {0, 0, 0};
-    void *chunk_op[3] = {nullptr, nullptr, nullptr};   // operator launch bindings of the graphs
-    CgOperator *chunk_owner[3] = {nullptr, nullptr, nullptr};
+    // chunk graphs per inner solver: 0 plain FP64; operator FP32 / BF16 with
+    // FP32 vectors (1 / 2) or with FP64 vectors (3 / 4)
+    static constexpr int kModes = 5;
+    cudaGraphExec_t chunk[kModes] = {};
+    double chunk_lambda[kModes] = {};
+    void *chunk_op[kModes] = {};   // operator launch bindings of the graphs
+    CgOperator *chunk_owner[kModes] = {};
     int chunk_len = 25;
 };
 
 void nir_cg_work_invalidate(CGWork *w)
 {
     if (!w) return;
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < CGWork::kModes; ++i) {
         if (w->chunk[i]) cudaGraphExecDestroy(w->chunk[i]);
         if (w->chunk_op[i] && w->chunk_owner[i]) w->chunk_owner[i]->release(w->chunk_op[i]);
         w->chunk[i] = nullptr;
@@ -468,7 +510,7 @@ void nir_cg_work_free(CGWork *&w)
 {
     if (!w) return;
     nir_cg_work_invalidate(w);
-    void *ptrs[] = {w->x64, w->r64, w->z64, w->p64, w->Ap64, w->r32, w->z32, w->p32, w->Ap32, w->d32, w->pb16,
+    void *ptrs[] = {w->x64, w->xs64, w->r64, w->z64, w->p64, w->Ap64, w->r32, w->z32, w->p32, w->Ap32, w->d32, w->pb16,
                     w->Apb16, w->dinv64, w->dinv32, w->part, w->ticket, w->scal, w->dots, w->flag};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -571,8 +613,10 @@ int capture_chunk(CgOperator &op, CGWork *w, int mode, int prec, double lambda, 
 }
 
 // FP64 true residual r64 = b - H x; returns |r|^2 and |b|^2 on the host.
+// With `extra`, also returns dots[2] and dots[3], which the caller queued on
+// the same stream before this call.
 int residual64(CgOperator &op, CGWork *w, double lambda, const double *b, const double *x, double *rr, double *bb,
-               cudaStream_t st)
+               cudaStream_t st, double *extra = nullptr)
 {
     const long long n = w->n;
     int rc = op.apply64(lambda, x, w->Ap64, st);
@@ -580,11 +624,15 @@ int residual64(CgOperator &op, CGWork *w, double lambda, const double *b, const 
     k_residual<<<vgrid(n), 256, 0, st>>>(w->r64, b, w->Ap64, n);
     k_dot<double><<<w->grid, kThreads, 0, st>>>(w->r64, w->r64, n, w->part, w->ticket + 2, w->dots);
     if (bb) k_dot<double><<<w->grid, kThreads, 0, st>>>(b, b, n, w->part, w->ticket + 2, w->dots + 1);
-    double h[2] = {0, 0};
-    NIR_CUDA_TRY(cudaMemcpyAsync(h, w->dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+    double h[4] = {0, 0, 0, 0};
+    NIR_CUDA_TRY(cudaMemcpyAsync(h, w->dots, sizeof(double) * (extra ? 4 : 2), cudaMemcpyDeviceToHost, st));
     NIR_CUDA_TRY(cudaStreamSynchronize(st));
     *rr = h[0];
     if (bb) *bb = h[1];
+    if (extra) {
+        extra[0] = h[2];
+        extra[1] = h[3];
+    }
     return NIR_OK;
 }
 
@@ -704,6 +752,42 @@ struct MeshOp final : CgOperator {
 
 }  // namespace
 
+namespace {
+
+// Inner solve of one refinement sweep, H_lo d = r64 / rn, in the vector type
+// V (double or float) with the operator in `prec`; d is left in x64 (FP64
+// vectors) or d32 (FP32 vectors).
+template <class V>
+int inner_sweep(CgOperator &op, CGWork *w, int prec, double lambda, double rn, const nir_cg_opts *o, int *iters,
+                int *bad, cudaStream_t st)
+{
+    const long long n = w->n;
+    constexpr bool v64 = std::is_same<V, double>::value;
+    V *d, *r, *z, *p;
+    const V *dinv;
+    if constexpr (v64) {
+        d = w->x64; r = w->r64; z = w->z64; p = w->p64; dinv = w->dinv64;
+    } else {
+        d = w->d32; r = w->r32; z = w->z32; p = w->p32; dinv = w->dinv32;
+    }
+    if (!o->jacobi) dinv = nullptr;
+    k_scale_to<V><<<vgrid(n), 256, 0, st>>>(r, w->r64, 1.0 / rn, n);
+    k_fill<V><<<vgrid(n), 256, 0, st>>>(d, 0.0, n);
+    const double th = o->inner_tol * o->inner_tol;
+    double rr_in = 0.0;
+    const int mode = (prec == NIR_F32 ? 1 : 2) + (v64 ? 2 : 0);
+    if (prec == NIR_F32) {
+        // FP32 vectors: p itself is the operator's input; FP64 vectors: its FP32 copy
+        float *pT = v64 ? w->p32 : reinterpret_cast<float *>(p);
+        return run_pcg<V, float>(op, w, mode, NIR_F32, lambda, d, r, z, p, pT, w->Ap32, dinv, th, o->max_inner, iters,
+                                 &rr_in, bad, st);
+    }
+    return run_pcg<V, __nv_bfloat16>(op, w, mode, NIR_BF16, lambda, d, r, z, p, w->pb16, w->Apb16, dinv, th,
+                                     o->max_inner, iters, &rr_in, bad, st);
+}
+
+}  // namespace
+
 int nir_cg_run(CgOperator &op, CGWork *&wref, double lambda, const double *b, double *x, const nir_cg_opts *o,
                nir_cg_stats *stats)
 {
@@ -711,6 +795,10 @@ int nir_cg_run(CgOperator &op, CGWork *&wref, double lambda, const double *b, do
     if (!(o->tol > 0.0) || o->max_inner < 1 || !std::isfinite(lambda)) return NIR_ERR_INVALID_ARG;
     if (o->inner_prec != NIR_F64 && o->inner_prec != NIR_F32 && o->inner_prec != NIR_BF16) return NIR_ERR_INVALID_ARG;
     if (o->inner_prec != NIR_F64 && (o->max_outer < 1 || !(o->inner_tol > 0.0) || !(o->inner_tol < 1.0)))
+        return NIR_ERR_INVALID_ARG;
+    if (o->inner_vectors != NIR_F64 && o->inner_vectors != NIR_F32) return NIR_ERR_INVALID_ARG;
+    if (!(o->fwd_tol >= 0.0) || !std::isfinite(o->fwd_tol)) return NIR_ERR_INVALID_ARG;
+    if (o->inner_prec == NIR_F64 && o->fwd_tol > 0.0 && !(o->inner_tol >= 0.0 && o->inner_tol < 1.0))
         return NIR_ERR_INVALID_ARG;
     NIR_CUDA_TRY(cudaSetDevice(op.context()->device));
     const auto t0 = std::chrono::steady_clock::now();
@@ -727,8 +815,11 @@ int nir_cg_run(CgOperator &op, CGWork *&wref, double lambda, const double *b, do
     rc = residual64(op, w, lambda, b, x, &rr, &bb, st);
     if (rc) return rc;
     if (!std::isfinite(rr) || !std::isfinite(bb)) return NIR_ERR_NONFINITE;
-    nir_cg_stats s{0, 0, 0.0, 0.0};
+    nir_cg_stats s{0, 0, 0.0, 0.0, 0.0};
     const double bn = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
+    const bool fwd = o->fwd_tol > 0.0;
+    double corr = fwd ? HUGE_VAL : 0.0;   // last sweep's |dx| / |x|
+    auto met = [&] { return std::sqrt(rr) / bn <= o->tol && (!fwd || corr <= o->fwd_tol); };
     int status = NIR_OK;
     if (o->inner_prec == NIR_F64) {
         // plain preconditioned CG, FP64 throughout, on an internal copy of x (the
@@ -753,39 +844,72 @@ int nir_cg_run(CgOperator &op, CGWork *&wref, double lambda, const double *b, do
             if (std::sqrt(rr) / bn <= o->tol) break;
             if (s.inner_total >= o->max_inner || rr >= prev) { status = NIR_ERR_NOT_CONVERGED; break; }
         }
+        // Polishing for the forward tolerance: CG continues from the true
+        // residual, cutting it by inner_tol per sweep, and each sweep's update
+        // |x_after - x_before| is the correction that fwd_tol bounds.
+        if (!status && fwd) {
+            if (!w->xs64 && cudaMalloc(&w->xs64, sizeof(double) * n) != cudaSuccess) return NIR_ERR_NO_MEMORY;
+            const double red = o->inner_tol > 0.0 ? o->inner_tol : 1e-3;
+            double corr_prev = HUGE_VAL;
+            for (int sweep = 0; !met(); ++sweep) {
+                if (sweep >= 50 || s.inner_total >= o->max_inner) { status = NIR_ERR_NOT_CONVERGED; break; }
+                NIR_CUDA_TRY(cudaMemcpyAsync(w->xs64, w->x64, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+                int iters = 0, bad = 0;
+                double rr_it = 0.0;
+                rc = run_pcg<double, double>(op, w, 0, NIR_F64, lambda, w->x64, w->r64, w->z64, w->p64, w->p64,
+                                             w->Ap64, o->jacobi ? w->dinv64 : nullptr, red * red * rr,
+                                             o->max_inner - s.inner_total, &iters, &rr_it, &bad, st);
+                if (rc) return rc;
+                s.inner_total += iters;
+                s.outer += 1;
+                k_diff_norms<<<w->grid, kThreads, 0, st>>>(w->x64, w->xs64, n, w->part, w->ticket + 2, w->dots + 2);
+                const double prev = rr;
+                double e[2] = {0, 0};
+                rc = residual64(op, w, lambda, b, w->x64, &rr, nullptr, st, e);
+                if (rc) return rc;
+                if (bad == 2 || !std::isfinite(rr) || !std::isfinite(e[0])) { status = NIR_ERR_NONFINITE; break; }
+                corr = e[1] > 0.0 ? std::sqrt(e[0] / e[1]) : 0.0;
+                if (bad == 1) { status = NIR_ERR_NOT_CONVERGED; break; }
+                if (!met() && rr >= prev && corr >= corr_prev) { status = NIR_ERR_NOT_CONVERGED; break; }
+                corr_prev = corr;
+            }
+        }
         NIR_CUDA_TRY(cudaMemcpyAsync(x, w->x64, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     } else {
-        const int mode = o->inner_prec == NIR_F32 ? 1 : 2;
-        while (std::sqrt(rr) / bn > o->tol && s.outer < o->max_outer) {
+        const bool v64 = o->inner_vectors == NIR_F64;
+        double corr_prev = HUGE_VAL;
+        while (!met() && s.outer < o->max_outer) {
             const double rn = std::sqrt(rr);
-            k_scale_to_f32<<<vgrid(n), 256, 0, st>>>(w->r32, w->r64, 1.0 / rn, n);
-            k_fill<float><<<vgrid(n), 256, 0, st>>>(w->d32, 0.0, n);
             int iters = 0, bad = 0;
-            double rr_in = 0.0;
-            const double th = o->inner_tol * o->inner_tol;
-            if (mode == 1)
-                rc = run_pcg<float, float>(op, w, 1, NIR_F32, lambda, w->d32, w->r32, w->z32, w->p32, w->p32,
-                                           w->Ap32, o->jacobi ? w->dinv32 : nullptr, th, o->max_inner, &iters,
-                                           &rr_in, &bad, st);
-            else
-                rc = run_pcg<float, __nv_bfloat16>(op, w, 2, NIR_BF16, lambda, w->d32, w->r32, w->z32, w->p32,
-                                                   w->pb16, w->Apb16, o->jacobi ? w->dinv32 : nullptr, th,
-                                                   o->max_inner, &iters, &rr_in, &bad, st);
+            rc = v64 ? inner_sweep<double>(op, w, o->inner_prec, lambda, rn, o, &iters, &bad, st)
+                     : inner_sweep<float>(op, w, o->inner_prec, lambda, rn, o, &iters, &bad, st);
             if (rc) return rc;
             s.inner_total += iters;
             s.outer += 1;
             if (bad == 2) { status = NIR_ERR_NONFINITE; break; }
-            k_correct<<<vgrid(n), 256, 0, st>>>(x, w->d32, rn, n);
+            if (v64) {
+                k_correct<double><<<vgrid(n), 256, 0, st>>>(x, w->x64, rn, n);
+                k_dot<double><<<w->grid, kThreads, 0, st>>>(w->x64, w->x64, n, w->part, w->ticket + 2, w->dots + 2);
+            } else {
+                k_correct<float><<<vgrid(n), 256, 0, st>>>(x, w->d32, rn, n);
+                k_dot<float><<<w->grid, kThreads, 0, st>>>(w->d32, w->d32, n, w->part, w->ticket + 2, w->dots + 2);
+            }
+            k_dot<double><<<w->grid, kThreads, 0, st>>>(x, x, n, w->part, w->ticket + 2, w->dots + 3);
             const double prev = rr;
-            rc = residual64(op, w, lambda, b, x, &rr, nullptr, st);
+            double e[2] = {0, 0};
+            rc = residual64(op, w, lambda, b, x, &rr, nullptr, st, e);
             if (rc) return rc;
-            if (!std::isfinite(rr)) { status = NIR_ERR_NONFINITE; break; }
-            if (rr >= prev) { status = NIR_ERR_NOT_CONVERGED; break; }  // refinement stalled
+            if (!std::isfinite(rr) || !std::isfinite(e[0])) { status = NIR_ERR_NONFINITE; break; }
+            corr = e[1] > 0.0 ? rn * std::sqrt(e[0] / e[1]) : 0.0;
+            // refinement stalled: neither the residual nor the correction shrinks
+            if (!met() && rr >= prev && corr >= corr_prev) { status = NIR_ERR_NOT_CONVERGED; break; }
+            corr_prev = corr;
         }
-        if (!status && std::sqrt(rr) / bn > o->tol) status = NIR_ERR_NOT_CONVERGED;
+        if (!status && !met()) status = NIR_ERR_NOT_CONVERGED;
     }
     NIR_CUDA_TRY(cudaStreamSynchronize(st));
     s.rel_residual = std::sqrt(rr) / bn;
+    s.rel_correction = std::isfinite(corr) ? corr : 0.0;
     s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = s;
     return status;

@@ -1,6 +1,7 @@
 """GPU tests of the hybrid mesh (one persistent launch, CUDA graphs,
 autotuner) and of the conjugate-gradient Helmholtz solve with FP64 iterative
 refinement, against the FP64 oracle (per-element operator and dense Cholesky)."""
+import ctypes as C
 import json
 import os
 
@@ -100,11 +101,9 @@ def hex_problem(nir, ctx, n=4, P=3, amp=0.05):
     return mesh, nodes, b, x_ref
 
 
-def kappa(nodes, P):
-    """Condition number of the block-diagonal operator (all element matrices)."""
-    H = oracle.helmholtz_matrix("hex", P, P + 2, 2, nodes, 1.0)
-    ev = np.concatenate([np.linalg.eigvalsh(h) for h in H])
-    return ev.max() / ev.min()
+# The solve's accuracy target: 1e-10 relative error of the final solution
+# against the oracle's (per-element dense Cholesky of the broken operator).
+FWD = 1e-10
 
 
 @pytest.mark.parametrize("jacobi", [True, False])
@@ -112,32 +111,54 @@ def test_fp64_cg_matches_dense_cholesky(nir, ctx, jacobi):
     mesh, nodes, b, x_ref = hex_problem(nir, ctx)
     bt = torch.from_numpy(b.ravel()).cuda()
     x = torch.zeros_like(bt)
-    rc, st = mesh.cg_solve(bt, x, inner_prec="f64", tol=1e-12, max_inner=20000, jacobi=jacobi)
+    rc, st = mesh.cg_solve(bt, x, inner_prec="f64", tol=1e-10, fwd_tol=FWD, max_inner=20000, jacobi=jacobi)
     assert rc == 0, st
-    assert st["rel_residual"] <= 1e-12
-    # forward error is bounded by kappa times the relative residual
-    assert rel(x.cpu().numpy(), x_ref.ravel()) <= 2 * kappa(nodes, 3) * st["rel_residual"] + 1e-14
+    assert st["rel_residual"] <= 1e-10 and st["rel_correction"] <= FWD, st
+    assert rel(x.cpu().numpy(), x_ref.ravel()) <= FWD
 
 
+@pytest.mark.parametrize("vectors", ["f64", "f32"])
 @pytest.mark.parametrize("inner", ["f32", "bf16"])
-def test_mixed_refinement_reaches_fp64_accuracy(nir, ctx, inner):
+def test_mixed_refinement_reaches_fp64_accuracy(nir, ctx, inner, vectors):
     mesh, nodes, b, x_ref = hex_problem(nir, ctx)
     bt = torch.from_numpy(b.ravel()).cuda()
     x = torch.zeros_like(bt)
-    rc, st = mesh.cg_solve(bt, x, inner_prec=inner, tol=1e-10, max_outer=60, max_inner=5000, inner_tol=1e-3)
+    rc, st = mesh.cg_solve(bt, x, inner_prec=inner, inner_vectors=vectors, tol=1e-10, fwd_tol=FWD, max_outer=60,
+                           max_inner=5000, inner_tol=1e-3)
     if inner == "f32":
         assert rc == 0, st
     if rc == 0:
-        assert st["rel_residual"] <= 1e-10
-        xf = torch.zeros_like(bt)
-        rc64, st64 = mesh.cg_solve(bt, xf, inner_prec="f64", tol=1e-10, max_inner=20000)
-        assert rc64 == 0
-        e_mixed = rel(x.cpu().numpy(), x_ref.ravel())
-        e_fp64 = rel(xf.cpu().numpy(), x_ref.ravel())
-        bound = 2 * kappa(nodes, 3) * 1e-10
-        assert e_mixed <= bound and e_fp64 <= bound, (e_mixed, e_fp64, bound)
+        assert st["rel_residual"] <= 1e-10 and st["rel_correction"] <= FWD, st
+        assert rel(x.cpu().numpy(), x_ref.ravel()) <= FWD, (rel(x.cpu().numpy(), x_ref.ravel()), st)
     else:
         assert rc == -4, (rc, st)   # refinement stalls: reported, not hidden
+
+
+def test_forward_criterion_adds_sweeps(nir, ctx):
+    """The residual alone can stop refinement while the correction is still
+    large; fwd_tol keeps refining until the correction meets it."""
+    mesh, nodes, b, x_ref = hex_problem(nir, ctx)
+    bt = torch.from_numpy(b.ravel()).cuda()
+    x1, x2 = torch.zeros_like(bt), torch.zeros_like(bt)
+    rc1, st1 = mesh.cg_solve(bt, x1, inner_prec="f32", tol=1e-6, max_outer=60, max_inner=5000, inner_tol=1e-3)
+    rc2, st2 = mesh.cg_solve(bt, x2, inner_prec="f32", tol=1e-6, fwd_tol=FWD, max_outer=60, max_inner=5000,
+                             inner_tol=1e-3)
+    assert rc1 == 0 and rc2 == 0, (st1, st2)
+    assert st2["outer"] > st1["outer"] and st2["rel_correction"] <= FWD
+    assert rel(x2.cpu().numpy(), x_ref.ravel()) <= FWD < rel(x1.cpu().numpy(), x_ref.ravel())
+
+
+def test_cg_options_rejected(nir, ctx):
+    mesh, nodes, b, x_ref = hex_problem(nir, ctx, n=2, P=2)
+    bt = torch.from_numpy(b.ravel()).cuda()
+    x = torch.zeros_like(bt)
+    L = nir.lib()
+    for kw in (dict(inner_vectors="bf16"), dict(fwd_tol=-1.0), dict(fwd_tol=float("nan"))):
+        o = nir._cg_opts(**{**dict(inner_prec="f32", tol=1e-10, max_outer=10, max_inner=100, inner_tol=1e-3,
+                                   jacobi=1, inner_vectors="f64", fwd_tol=0.0), **kw})
+        s = nir.CGStats()
+        assert L.nir_cg_solve(mesh.h, 1.0, C.c_void_p(bt.data_ptr()), C.c_void_p(x.data_ptr()), C.byref(o),
+                              C.byref(s)) == -1, kw
 
 
 def test_cg_on_hybrid_mesh(nir, ctx):
@@ -145,7 +166,8 @@ def test_cg_on_hybrid_mesh(nir, ctx):
     mesh, blocks = build_mesh(nir, ctx, parts)
     b = torch.from_numpy(W.coefficients(1, mesh.ndof, seed=9)[0]).cuda()
     x = torch.zeros_like(b)
-    rc, st = mesh.cg_solve(b, x, inner_prec="f32", tol=1e-10, max_outer=60, max_inner=5000, inner_tol=1e-3)
+    rc, st = mesh.cg_solve(b, x, inner_prec="f32", tol=1e-10, fwd_tol=FWD, max_outer=60, max_inner=5000,
+                           inner_tol=1e-3)
     assert rc == 0 and st["rel_residual"] <= 1e-10, st
     # check against the per-element dense solve on a few elements of every block
     xh = x.cpu().numpy()
@@ -155,7 +177,7 @@ def test_cg_on_hybrid_mesh(nir, ctx):
         n = blk.nelem * blk.M
         xr = oracle.helmholtz_solve(p["shape"], p["P"], p["Q"], p["gorder"], p["nodes"][ids], 1.0,
                                     bh[o:o + n].reshape(blk.nelem, blk.M)[ids])
-        assert rel(xh[o:o + n].reshape(blk.nelem, blk.M)[ids], xr) <= 1e-5
+        assert rel(xh[o:o + n].reshape(blk.nelem, blk.M)[ids], xr) <= FWD, (p["shape"], p["P"])
 
 
 def test_cg_failure_reporting(nir, ctx):
@@ -242,10 +264,14 @@ def test_full_hybrid_mesh_sampled(nir, ctx):
             assert rel(y[o:o + n].reshape(b.nelem, b.M)[ids], ref) <= tol, (prec, p["shape"], p["P"])
 
 
-def test_full_p6_solve_sampled(nir, ctx):
-    """Mixed-precision solve of the full 48^3 P6 curved mesh to 1e-10; the
-    broken operator is block diagonal, so each element's exact solution is
-    the oracle's dense per-element solve."""
+@pytest.mark.parametrize("inner,vectors", [("f32", "f64"), ("f32", "f32"), ("f64", "f64")])
+def test_full_p6_solve_sampled(nir, ctx, inner, vectors):
+    """Solve of the full 48^3 P6 curved mesh (110 592 elements, 37.9 M DOF) to
+    relative residual 1e-10 and forward tolerance 1e-10: FP32 operator inside FP64
+    refinement with FP64 or FP32 inner vectors, and plain FP64 CG.  The broken
+    operator is block diagonal, so each element's exact solution is the
+    oracle's dense per-element Cholesky solve; the sampled elements must match
+    it to 1e-10."""
     wl = W.workload("hex48_curved_p6")
     nodes = wl["nodes"]
     E = nodes.shape[0]
@@ -255,12 +281,12 @@ def test_full_p6_solve_sampled(nir, ctx):
     b = W.coefficients(E, blk.M, seed=3)
     bt = torch.from_numpy(b.ravel()).cuda()
     x = torch.zeros_like(bt)
-    rc, st = mesh.cg_solve(bt, x, inner_prec="f32", tol=1e-10, max_outer=60, max_inner=20000, inner_tol=1e-3)
-    assert rc == 0 and st["rel_residual"] <= 1e-10, st
+    rc, st = mesh.cg_solve(bt, x, inner_prec=inner, inner_vectors=vectors, tol=1e-10, fwd_tol=FWD, max_outer=60,
+                           max_inner=20000, inner_tol=1e-3)
+    assert rc == 0 and st["rel_residual"] <= 1e-10 and st["rel_correction"] <= FWD, st
     ids = W.sample_elements(E, 6, seed=4)
     xr = oracle.helmholtz_solve("hex", 6, 8, 6, nodes[ids], 1.0, b[ids])
-    H = oracle.helmholtz_matrix("hex", 6, 8, 6, nodes[ids], 1.0)
-    kap = max(np.linalg.cond(h) for h in H)
     xs = x.cpu().numpy().reshape(E, blk.M)[ids]
-    # global residual 1e-10 bounds each sampled element's error by kappa
-    assert rel(xs, xr) <= 10 * kap * 1e-10, (rel(xs, xr), kap)
+    assert rel(xs, xr) <= FWD, (rel(xs, xr), st)
+    for i in range(len(ids)):
+        assert rel(xs[i], xr[i]) <= FWD, (i, rel(xs[i], xr[i]))
