@@ -106,6 +106,15 @@ void nir_ctx_destroy(nir_ctx *ctx);
  * wait that runs out sets a device error word and the kernel returns.
  * Returns NIR_ERR_CUDA (and clears the word) if one was set. */
 int nir_ctx_check(nir_ctx *ctx);
+/* Failure-path self-test of the bounded wait (the paper has no counterpart:
+ * this exercises the library's own failure detection).  Launches on the
+ * context stream one CTA that waits on an mbarrier nothing arrives on and with
+ * no copy in flight, with a wait limit of limit_cycles SM clock cycles
+ * (1 .. 2^31; every staged kernel uses 2^31).  The wait runs out, the kernel
+ * sets the context's device error word and returns; the next nir_ctx_check
+ * reports NIR_ERR_CUDA and clears the word.  Asynchronous.  Errors:
+ * INVALID_ARG, CUDA. */
+int nir_ctx_selftest_wait(nir_ctx *ctx, int64_t limit_cycles);
 
 /* Create a block; builds the FP64 basis/quadrature tables (Eqs. basis matrix,
  * bwdsumfachex, bwdsumfactet, stdderiv) and uploads them.  Errors:
@@ -135,6 +144,26 @@ int nir_block_points(const nir_block *blk, double *eta_out, double *xi_out);
  * Synchronises the context stream.  Errors: INVALID_ARG, GEOMETRY (some
  * det J <= 0 or non-finite), NO_MEMORY, CUDA. */
 int nir_block_set_geometry(nir_block *blk, int gorder, const double *nodes);
+
+/* Geometry given as geometric factors, the form of the paper's statement of
+ * the problem (Sec. 2.1: the weights matrix W = diag(w |J|) and, in
+ * Eq. physderiv, Lambda(d xi/d x)), for callers that already hold them.
+ * DEVICE FP64 arrays, caller-owned, read during the call only:
+ *   per_element = 0: dxi_dx [E][Nq][d][d], jac [E][Nq] -- at every
+ *                    quadrature point (point order as for physical values);
+ *   per_element = 1: dxi_dx [E][d][d], jac [E] -- constant over each
+ *                    element (an affine element map), any shape.
+ * dxi_dx[.][i][l] = d xi_i / d x_l of the standard element (the collapsed
+ * coordinates' chain rule d eta/d xi is applied by the library); jac = |J| =
+ * det(d x/d xi) > 0.  The library forms W = w |J| (w: quadrature weights with
+ * the collapse factors), d eta/d x and G = W (d eta/d x)(d eta/d x)^T in FP64
+ * on the GPU, exactly as nir_block_set_geometry does from the element maps,
+ * and derives FP32/BF16 copies on first use.  An undeformed quad/hex block
+ * stores one set of factors per element and takes only per_element = 1.
+ * Synchronises the context stream.  Errors: INVALID_ARG (null or aliased
+ * pointers, per_element not 0/1, per-point factors for an undeformed quad/hex
+ * block), GEOMETRY (some jac <= 0 or non-finite), NO_MEMORY, CUDA. */
+int nir_block_set_geometric_factors(nir_block *blk, int per_element, const double *dxi_dx, const double *jac);
 
 /* BwdTrans u = B u_hat (Eqs. bwdstd, bwdsumfachex, bwdsumfactet).
  * coeff [E][M] -> phys [E][Nq]. */
@@ -184,8 +213,11 @@ int nir_helmholtz_host(nir_block *blk, int prec, double lambda, const void *h_in
  *     block's low-precision factors; TOO_LARGE when E*M*sizeof exceeds
  *     NIR_NOALLOC_MAX_VECTOR_BYTES (nothing is launched); CUDA.
  *   - The first call on a device looks up the array's device address with
- *     cudaGetSymbolAddress (with that device current); make that first call
- *     before any stream capture.
+ *     cudaGetSymbolAddress (with that device current) and keeps it for the
+ *     life of the process; make that first call before any stream capture,
+ *     and do not reset the device (cudaDeviceReset) after it.
+ *   - On any error after the input copy was queued the call still waits for
+ *     the stream before returning, so h_in and h_out are free on return.
  *   - Every call shares the one array and leaves its last contents there;
  *     calls whose work overlaps on the GPU (other threads or streams) race
  *     on it, so serialise them. */
@@ -206,8 +238,11 @@ int nir_helmholtz_host_noalloc(nir_block *blk, int prec, double lambda, const vo
  * results equal the other variants' bit for bit).  grid = CTAs of 128
  * threads (0: one wave at its occupancy), at most one CTA per 128 elements.
  * A block's launches share that scratch: calls on one block must not overlap
- * on the GPU.
- * Errors: INVALID_ARG; with variant 4 also UNSUPPORTED (nodal basis),
+ * on the GPU.  Leaving variant 4 in the last precision that used it frees the
+ * scratch.  Selecting or leaving variant 4 allocates or frees device memory
+ * and synchronises the device, so it must not overlap a stream capture on
+ * this device; while the context stream is capturing it returns STATE.
+ * Errors: INVALID_ARG, STATE; with variant 4 also UNSUPPORTED (nodal basis),
  * TOO_LARGE (2^31 or more scratch values), NO_MEMORY, CUDA. */
 int nir_block_set_tuning(nir_block *blk, int prec, int variant, int grid, int pf);
 int nir_block_get_tuning(const nir_block *blk, int prec, int *variant, int *grid, int *pf);
@@ -378,6 +413,11 @@ int nir_asm_cg_solve(nir_asm *a, int op, double lambda, int fix_boundary, const 
 /* Measure the FP64 FMA throughput of the device (TFLOP/s) with a register-
  * resident DFMA loop; used as the FP64 roofline ceiling. Synchronous. */
 int nir_probe_fp64_peak(nir_ctx *ctx, double *tflops);
+/* Measure the FP64 tensor-core (DMMA, mma.sync m8n8k4 f64) throughput of the
+ * device (TFLOP/s) with register-resident accumulator chains; compared with
+ * nir_probe_fp64_peak it tells whether FP64 contractions would gain from the
+ * tensor pipe.  Synchronous. */
+int nir_probe_fp64_mma_peak(nir_ctx *ctx, double *tflops);
 
 const char *nir_strerror(int code);
 /* Library version string. */

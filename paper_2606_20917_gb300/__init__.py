@@ -70,6 +70,7 @@ _SIGS = {
     "nir_block_num_points": [_vp, C.POINTER(_i64)],
     "nir_block_points": [_vp, _vp, _vp],
     "nir_block_set_geometry": [_vp, _i, _vp],
+    "nir_block_set_geometric_factors": [_vp, _i, _vp, _vp],
     "nir_bwd_trans": [_vp, _i, _vp, _vp],
     "nir_iproduct_wrt_base": [_vp, _i, _vp, _vp],
     "nir_phys_deriv": [_vp, _i, _vp, _vp, _vp, _vp],
@@ -89,6 +90,8 @@ _SIGS = {
     "nir_mesh_get_launch": [_vp, _i, C.POINTER(_i)],
     "nir_cg_solve": [_vp, _d, _vp, _vp, C.POINTER(CGOpts), C.POINTER(CGStats)],
     "nir_probe_fp64_peak": [_vp, C.POINTER(_d)],
+    "nir_probe_fp64_mma_peak": [_vp, C.POINTER(_d)],
+    "nir_ctx_selftest_wait": [_vp, _i64],
     "nir_asm_create": [_vp, C.POINTER(_vp), C.POINTER(_vp), _i, C.POINTER(_vp)],
     "nir_asm_num_dofs": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)],
     "nir_asm_local_map": [_vp, _vp],
@@ -161,6 +164,17 @@ class Context:
         _chk(_lib.nir_probe_fp64_peak(self.h, C.byref(v)), "nir_probe_fp64_peak")
         return v.value
 
+    def probe_fp64_mma_peak(self) -> float:
+        """FP64 tensor-core (DMMA) throughput in TFLOP/s."""
+        v = _d()
+        _chk(_lib.nir_probe_fp64_mma_peak(self.h, C.byref(v)), "nir_probe_fp64_mma_peak")
+        return v.value
+
+    def selftest_wait(self, limit_cycles: int):
+        """Launch the bounded-wait self-test (see nir_ctx_selftest_wait); the
+        next check() raises NIR_ERR_CUDA."""
+        _chk(_lib.nir_ctx_selftest_wait(self.h, int(limit_cycles)), "nir_ctx_selftest_wait")
+
     def __del__(self):
         h = getattr(self, "h", None)
         if h:
@@ -229,6 +243,17 @@ class Block:
         if nodes.numel() != self.nelem * npe * self.dim:
             raise ValueError(f"nodes must be [{self.nelem}][{npe}][{self.dim}]")
         _chk(_lib.nir_block_set_geometry(self.h, int(gorder), _ptr(nodes)), "nir_block_set_geometry")
+
+    def set_geometric_factors(self, dxi_dx: torch.Tensor, jac: torch.Tensor, per_element: bool = False):
+        """Geometry from d xi/d x and |J| (FP64 CUDA tensors): per point
+        [E][Nq][d][d] and [E][Nq], or per element [E][d][d] and [E]."""
+        dxi_dx = self._dev(dxi_dx, torch.float64, "dxi_dx")
+        jac = self._dev(jac, torch.float64, "jac")
+        units = self.nelem * (1 if per_element else self.NQ)
+        if dxi_dx.numel() != units * self.dim * self.dim or jac.numel() != units:
+            raise ValueError(f"dxi_dx must hold {units} x {self.dim} x {self.dim} values and jac {units}")
+        _chk(_lib.nir_block_set_geometric_factors(self.h, int(bool(per_element)), _ptr(dxi_dx), _ptr(jac)),
+             "nir_block_set_geometric_factors")
 
     # -- helpers
     def _dev(self, t, dtype, name):

@@ -438,12 +438,17 @@ extern "C" int nir_block_points(const nir_block *b, double *eta, double *xi)
     return NIR_OK;
 }
 
-extern "C" int nir_block_set_geometry(nir_block *b, int gorder, const double *nodes)
+namespace {
+
+// Shared by both geometry entry points: host tables (points, weights, lattice
+// Lagrange tables for an element map), the FP64 factor arrays, one kernel
+// launch (from the element map when nodes != null, else from the caller's
+// d xi/d x and |J|), the determinant check and the reset of derived copies.
+int set_geometry_impl(nir_block *b, int gorder, const double *nodes, int per_elem, const double *dxi_dx,
+                      const double *jac)
 {
-    if (!b || !nodes) return NIR_ERR_INVALID_ARG;
-    const int shape = b->d.shape, Q = b->d.Q, d = b->dim;
+    const int shape = b->d.shape, Q = b->d.Q;
     const bool tensor = (shape == NIR_QUAD || shape == NIR_HEX);
-    if (tensor ? (gorder < 1 || gorder > 12) : gorder != 1) return NIR_ERR_INVALID_ARG;
     NIR_CUDA_TRY(cudaSetDevice(b->ctx->device));
     cudaStream_t st = b->ctx->stream;
     // host tables: per-direction points, weights, lattice Lagrange tables
@@ -455,7 +460,7 @@ extern "C" int nir_block_set_geometry(nir_block *b, int gorder, const double *no
     double *hz = host.data(), *hw = hz + 3 * Q, *hL = hw + b->NQ, *hdL = hL + (Q + 1) * g1;
     std::memcpy(hz, z.data(), sizeof(double) * 3 * Q);
     std::memcpy(hw, b->tab_h.data() + L.wq, sizeof(double) * b->NQ);
-    if (tensor) {
+    if (tensor && nodes) {
         std::vector<double> zz(Q + 1);
         for (int q = 0; q < Q; ++q) zz[q] = z[q];
         zz[Q] = 0.0;  // element centre, for per-element factors
@@ -497,7 +502,10 @@ extern "C" int nir_block_set_geometry(nir_block *b, int gorder, const double *no
         ga.Q = Q;
         ga.g = gorder;
         ga.pp = b->geo_pp;
-        rc = nir_geom_launch(ga, st);
+        ga.dxi_dx = dxi_dx;
+        ga.jac = jac;
+        ga.per_elem = per_elem;
+        rc = nodes ? nir_geom_launch(ga, st) : nir_geom_factors_launch(ga, st);
     }
     int herr = 0;
     if (!rc && (cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -516,8 +524,28 @@ extern "C" int nir_block_set_geometry(nir_block *b, int gorder, const double *no
         return NIR_ERR_GEOMETRY;
     }
     b->geo_set = true;
-    (void)d;
     return NIR_OK;
+}
+
+}  // namespace
+
+extern "C" int nir_block_set_geometry(nir_block *b, int gorder, const double *nodes)
+{
+    if (!b || !nodes) return NIR_ERR_INVALID_ARG;
+    const int shape = b->d.shape;
+    const bool tensor = (shape == NIR_QUAD || shape == NIR_HEX);
+    if (tensor ? (gorder < 1 || gorder > 12) : gorder != 1) return NIR_ERR_INVALID_ARG;
+    return set_geometry_impl(b, gorder, nodes, 0, nullptr, nullptr);
+}
+
+extern "C" int nir_block_set_geometric_factors(nir_block *b, int per_element, const double *dxi_dx,
+                                               const double *jac)
+{
+    if (!b || !dxi_dx || !jac || (const void *)dxi_dx == (const void *)jac) return NIR_ERR_INVALID_ARG;
+    if (per_element != 0 && per_element != 1) return NIR_ERR_INVALID_ARG;
+    // an undeformed quad/hex block keeps one set of factors per element
+    if (!b->geo_pp && !per_element) return NIR_ERR_INVALID_ARG;
+    return set_geometry_impl(b, 1, nullptr, per_element, dxi_dx, jac);
 }
 
 // --------------------------------------------------------------------------- operators
@@ -792,14 +820,23 @@ extern "C" int nir_block_set_tuning(nir_block *b, int prec, int variant, int gri
 {
     if (!b || !valid_prec(prec) || variant < 0 || variant > NIR_VARIANT_TOE || grid < 0 || (pf != 0 && pf != 1))
         return NIR_ERR_INVALID_ARG;
-    if (variant == NIR_VARIANT_TOE) {
+    // choosing or leaving the threading-over-elements kernel may allocate or
+    // free its scratch, which synchronises the device: not inside a capture
+    const bool touches_scratch = variant == NIR_VARIANT_TOE || b->helm_variant[prec] == NIR_VARIANT_TOE;
+    if (touches_scratch) {
         NIR_CUDA_TRY(cudaSetDevice(b->ctx->device));
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        NIR_CUDA_TRY(cudaStreamIsCapturing(b->ctx->stream, &cs));
+        if (cs != cudaStreamCaptureStatusNone) return NIR_ERR_STATE;
+    }
+    if (variant == NIR_VARIANT_TOE) {
         int rc = nir_toe_prepare(b, prec, grid);
         if (rc) return rc;
     }
     b->helm_variant[prec] = variant;
     b->helm_grid[prec] = grid;
     b->helm_pf[prec] = pf;
+    if (variant != NIR_VARIANT_TOE) nir_toe_release(b);  // frees the scratch once no precision uses it
     return NIR_OK;
 }
 
@@ -827,6 +864,71 @@ extern "C" int nir_block_kernel_info(const nir_block *b, int prec, int op, int *
     if (smem_bytes) *smem_bytes = ki.smem + (int)fa.sharedSizeBytes;
     if (threads) *threads = ki.nt;
     if (elems_per_cta) *elems_per_cta = ki.epb;
+    return NIR_OK;
+}
+
+namespace {
+
+// One CTA waits on an mbarrier that nothing arrives on and that has no copy in
+// flight, with a wait limit of `limit` cycles: the wait runs out, sets the
+// error word and the CTA returns -- the path every staged kernel takes when a
+// bulk copy never completes.
+__global__ void k_wait_selftest(int *err, long long limit)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) nirk::mbar_init(&bar, 1);
+    __syncthreads();
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) s_fail = 0;
+    __syncthreads();
+    if (!nirk::mbar_wait(&bar, 0u, err, limit)) atomicExch(&s_fail, 1);
+    __syncthreads();
+    if (s_fail) return;
+}
+
+}  // namespace
+
+extern "C" int nir_ctx_selftest_wait(nir_ctx *ctx, int64_t limit_cycles)
+{
+    if (!ctx || limit_cycles < 1 || limit_cycles > (1LL << 31)) return NIR_ERR_INVALID_ARG;
+    NIR_CUDA_TRY(cudaSetDevice(ctx->device));
+    k_wait_selftest<<<1, 32, 0, ctx->stream>>>(ctx->derr, (long long)limit_cycles);
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        (void)cudaGetLastError();
+        return NIR_ERR_CUDA;
+    }
+    return NIR_OK;
+}
+
+extern "C" int nir_probe_fp64_mma_peak(nir_ctx *ctx, double *tflops)
+{
+    if (!ctx || !tflops) return NIR_ERR_INVALID_ARG;
+    NIR_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    double *sink = nullptr;
+    NIR_CUDA_TRY(cudaMalloc(&sink, sizeof(double) * 65536));
+    const int grid = ctx->num_sms * 8, iters = 2048;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = nir_probe_mma_launch(sink, grid, iters / 8, st);  // warm-up
+    float best = 1e30f;
+    for (int rep = 0; rep < 3 && !rc; ++rep) {
+        cudaEventRecord(e0, st);
+        rc = nir_probe_mma_launch(sink, grid, iters, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = NIR_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (rc) return rc;
+    // m8n8k4: 8 x 8 x 4 multiply-adds per warp instruction, 8 chains per warp
+    const double flops = 2.0 * 256.0 * 8.0 * iters * (double)grid * (256.0 / 32.0);
+    *tflops = flops / (best * 1e-3) / 1e12;
     return NIR_OK;
 }
 

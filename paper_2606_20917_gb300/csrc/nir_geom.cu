@@ -1,5 +1,7 @@
 // nir_geom.cu -- FP64 geometric factors on the GPU, precision conversion of
-// the factors, and the FP64 FMA throughput probe.
+// the factors, and the FP64 FMA throughput probe.  The factors come either
+// from the element maps (k_geometry) or from the caller's d xi/d x and |J|
+// (k_geometry_from_factors); both finish through store_factors.
 //
 // Per point (or once per element for undeformed quad/hex blocks) the kernel
 // forms the Jacobian J = dx/dxi of the element map, W = w |J| (the weights
@@ -43,35 +45,105 @@ __device__ void vertex_grads(int shape, const double *xi, double G[6][3], int &n
     }
 }
 
-__global__ void k_geometry(GeoArgs a)
+// Collapsed (eta) and standard-element (xi) coordinates of point n, and its
+// per-direction indices ii.
+__device__ void point_coords(const GeoArgs &a, int n, double eta[3], double xi[3], int ii[3])
+{
+    const int d = dim(a.shape), Q = a.Q;
+    ii[0] = n % Q;
+    ii[1] = (n / Q) % Q;
+    ii[2] = n / (Q * Q);
+    eta[0] = eta[1] = eta[2] = 0.0;
+    xi[0] = xi[1] = xi[2] = 0.0;
+    for (int c = 0; c < d; ++c) eta[c] = a.z[c * Q + ii[c]];
+    // collapsed coordinates -> standard element (Eq. eta-space and its inverse)
+    if (a.shape == TRI) {
+        xi[0] = 0.5 * (1.0 + eta[0]) * (1.0 - eta[1]) - 1.0;
+        xi[1] = eta[1];
+    } else if (a.shape == PRISM) {
+        xi[0] = 0.5 * (1.0 + eta[0]) * (1.0 - eta[2]) - 1.0;
+        xi[1] = eta[1];
+        xi[2] = eta[2];
+    } else if (a.shape == TET) {
+        xi[0] = 0.25 * (1.0 + eta[0]) * (1.0 - eta[1]) * (1.0 - eta[2]) - 1.0;
+        xi[1] = 0.5 * (1.0 + eta[1]) * (1.0 - eta[2]) - 1.0;
+        xi[2] = eta[2];
+    } else {
+        for (int c = 0; c < d; ++c) xi[c] = eta[c];
+    }
+}
+
+// From Ji[i][l] = d xi_i / d x_l and det = |J| at point n of element e: the
+// collapsed factors d eta/d xi, d eta/d x = (d eta/d xi)(d xi/d x), W = w|J|
+// (|J| alone for per-element factors) and G = W (d eta/d x)(d eta/d x)^T,
+// stored in the library's layouts (per point interleaved by 32 elements, or
+// per element).  A det that is not positive and finite raises the error flag.
+__device__ void store_factors(const GeoArgs &a, long long e, int n, const double eta[3], const double Ji[3][3],
+                              double det)
 {
     const int d = dim(a.shape);
     const int NQ = npts(a.shape, a.Q);
     const int ng = ngeo(a.shape), nl = nlam(a.shape);
+    if (!(det > 0.0) || !isfinite(det)) atomicExch(a.err, 1);
+    // A[j][i] = d eta_j / d xi_i
+    double A[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    if (a.shape == TRI) {
+        A[0][0] = 2.0 / (1.0 - eta[1]);
+        A[0][1] = (1.0 + eta[0]) / (1.0 - eta[1]);
+    } else if (a.shape == PRISM) {
+        A[0][0] = 2.0 / (1.0 - eta[2]);
+        A[0][2] = (1.0 + eta[0]) / (1.0 - eta[2]);
+    } else if (a.shape == TET) {
+        const double s = (1.0 - eta[1]) * (1.0 - eta[2]);
+        A[0][0] = 4.0 / s;
+        A[0][1] = A[0][2] = 2.0 * (1.0 + eta[0]) / s;
+        A[1][1] = 2.0 / (1.0 - eta[2]);
+        A[1][2] = (1.0 + eta[1]) / (1.0 - eta[2]);
+    }
+    double Lm[3][3];
+    for (int j = 0; j < d; ++j)
+        for (int l = 0; l < d; ++l) {
+            double s = 0.0;
+            for (int i = 0; i < d; ++i) s = fma(A[j][i], Ji[i][l], s);
+            Lm[j][l] = s;
+        }
+    const double W = (a.pp ? a.wq[n] : 1.0) * det;
+    double gv[7];
+    int c = 0;
+    for (int i = 0; i < d; ++i)
+        for (int j = i; j < d; ++j) {
+            double s = 0.0;
+            for (int l = 0; l < d; ++l) s = fma(Lm[i][l], Lm[j][l], s);
+            gv[c++] = W * s;
+        }
+    gv[c] = W;
+    if (a.pp) {
+        const long long base = (e >> 5) * NQ + n;
+        for (int q = 0; q < ng; ++q) a.G[((base * ng + q) << 5) + (e & 31)] = gv[q];
+        for (int j = 0; j < d; ++j)
+            for (int l = 0; l < d; ++l) a.Lam[((base * nl + j * d + l) << 5) + (e & 31)] = Lm[j][l];
+        a.Lam[((base * nl + nl - 1) << 5) + (e & 31)] = W;
+    } else {
+        for (int q = 0; q < ng; ++q) a.G[e * ng + q] = gv[q];
+        for (int j = 0; j < d; ++j)
+            for (int l = 0; l < d; ++l) a.Lam[e * nl + j * d + l] = Lm[j][l];
+        a.Lam[e * nl + nl - 1] = W;
+    }
+}
+
+__global__ void k_geometry(GeoArgs a)
+{
+    const int d = dim(a.shape);
+    const int NQ = npts(a.shape, a.Q);
     const long long total = a.pp ? a.nelem * NQ : a.nelem;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const long long e = a.pp ? t / NQ : t;
         const int n = a.pp ? (int)(t - e * NQ) : 0;
         const int Q = a.Q;
-        const int ii[3] = {n % Q, (n / Q) % Q, n / (Q * Q)};
-        double eta[3] = {0, 0, 0}, xi[3] = {0, 0, 0};
-        for (int c = 0; c < d; ++c) eta[c] = a.z[c * Q + ii[c]];
-        // collapsed coordinates -> standard element (Eq. eta-space and its inverse)
-        if (a.shape == TRI) {
-            xi[0] = 0.5 * (1.0 + eta[0]) * (1.0 - eta[1]) - 1.0;
-            xi[1] = eta[1];
-        } else if (a.shape == PRISM) {
-            xi[0] = 0.5 * (1.0 + eta[0]) * (1.0 - eta[2]) - 1.0;
-            xi[1] = eta[1];
-            xi[2] = eta[2];
-        } else if (a.shape == TET) {
-            xi[0] = 0.25 * (1.0 + eta[0]) * (1.0 - eta[1]) * (1.0 - eta[2]) - 1.0;
-            xi[1] = 0.5 * (1.0 + eta[1]) * (1.0 - eta[2]) - 1.0;
-            xi[2] = eta[2];
-        } else {
-            for (int c = 0; c < d; ++c) xi[c] = eta[c];
-        }
+        int ii[3];
+        double eta[3], xi[3];
+        point_coords(a, n, eta, xi, ii);
         // J[l][i] = d x_l / d xi_i
         double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         if (a.shape == QUAD || a.shape == HEX) {
@@ -107,7 +179,7 @@ __global__ void k_geometry(GeoArgs a)
                     for (int i = 0; i < d; ++i) J[l][i] = fma(X[v * d + l], Gv[v][i], J[l][i]);
         }
         // determinant and inverse (Ji[i][l] = d xi_i / d x_l)
-        double det, Ji[3][3];
+        double det, Ji[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         if (d == 2) {
             det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
             Ji[0][0] = J[1][1] / det; Ji[0][1] = -J[0][1] / det;
@@ -128,51 +200,32 @@ __global__ void k_geometry(GeoArgs a)
             Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * r;
             Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * r;
         }
-        if (!(det > 0.0) || !isfinite(det)) atomicExch(a.err, 1);
-        // A[j][i] = d eta_j / d xi_i
-        double A[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-        if (a.shape == TRI) {
-            A[0][0] = 2.0 / (1.0 - eta[1]);
-            A[0][1] = (1.0 + eta[0]) / (1.0 - eta[1]);
-        } else if (a.shape == PRISM) {
-            A[0][0] = 2.0 / (1.0 - eta[2]);
-            A[0][2] = (1.0 + eta[0]) / (1.0 - eta[2]);
-        } else if (a.shape == TET) {
-            const double s = (1.0 - eta[1]) * (1.0 - eta[2]);
-            A[0][0] = 4.0 / s;
-            A[0][1] = A[0][2] = 2.0 * (1.0 + eta[0]) / s;
-            A[1][1] = 2.0 / (1.0 - eta[2]);
-            A[1][2] = (1.0 + eta[1]) / (1.0 - eta[2]);
-        }
-        double Lm[3][3];
-        for (int j = 0; j < d; ++j)
-            for (int l = 0; l < d; ++l) {
-                double s = 0.0;
-                for (int i = 0; i < d; ++i) s = fma(A[j][i], Ji[i][l], s);
-                Lm[j][l] = s;
-            }
-        const double W = (a.pp ? a.wq[n] : 1.0) * det;
-        double gv[7];
-        int c = 0;
+        store_factors(a, e, n, eta, Ji, det);
+    }
+}
+
+// Factors given by the caller (Sec. 2.1: Lambda = d xi/d x and |J|), per
+// point [E][NQ][d][d] / [E][NQ], or constant over each element [E][d][d] /
+// [E] (per_elem).  The block's layout decides the units written: every
+// point (a.pp) or every element.
+__global__ void k_geometry_from_factors(GeoArgs a)
+{
+    const int d = dim(a.shape);
+    const int NQ = npts(a.shape, a.Q);
+    const long long total = a.pp ? a.nelem * NQ : a.nelem;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long e = a.pp ? t / NQ : t;
+        const int n = a.pp ? (int)(t - e * NQ) : 0;
+        int ii[3];
+        double eta[3], xi[3];
+        point_coords(a, n, eta, xi, ii);
+        const long long u = a.per_elem ? e : e * NQ + n;
+        const double *L = a.dxi_dx + u * d * d;
+        double Ji[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         for (int i = 0; i < d; ++i)
-            for (int j = i; j < d; ++j) {
-                double s = 0.0;
-                for (int l = 0; l < d; ++l) s = fma(Lm[i][l], Lm[j][l], s);
-                gv[c++] = W * s;
-            }
-        gv[c] = W;
-        if (a.pp) {
-            const long long base = (e >> 5) * NQ + n;
-            for (int q = 0; q < ng; ++q) a.G[((base * ng + q) << 5) + (e & 31)] = gv[q];
-            for (int j = 0; j < d; ++j)
-                for (int l = 0; l < d; ++l) a.Lam[((base * nl + j * d + l) << 5) + (e & 31)] = Lm[j][l];
-            a.Lam[((base * nl + nl - 1) << 5) + (e & 31)] = W;
-        } else {
-            for (int q = 0; q < ng; ++q) a.G[e * ng + q] = gv[q];
-            for (int j = 0; j < d; ++j)
-                for (int l = 0; l < d; ++l) a.Lam[e * nl + j * d + l] = Lm[j][l];
-            a.Lam[e * nl + nl - 1] = W;
-        }
+            for (int l = 0; l < d; ++l) Ji[i][l] = L[i * d + l];
+        store_factors(a, e, n, eta, Ji, a.jac[u]);
     }
 }
 
@@ -204,7 +257,39 @@ __global__ void __launch_bounds__(256) k_dfma_probe(double *sink, int iters, dou
     if (s == -1.2345) sink[blockIdx.x] = s;  // never true; keeps the chains live
 }
 
+// Register-resident FP64 tensor-core (DMMA) chains: mma.sync m8n8k4 with FP64
+// operands and accumulators, 8 independent accumulator pairs per thread.  Its
+// rate next to the DFMA probe's decides whether FP64 contractions gain
+// anything from the tensor pipe on this GPU.
+__global__ void __launch_bounds__(256) k_dmma_probe(double *sink, int iters, double a, double b)
+{
+    double c[8][2];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        c[k][0] = 1e-3 * (threadIdx.x + k);
+        c[k][1] = 2e-3 * (threadIdx.x + k);
+    }
+    const double av = a * (1.0 + 1e-3 * (threadIdx.x & 31)), bv = b;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                         : "+d"(c[k][0]), "+d"(c[k][1])
+                         : "d"(av), "d"(bv));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += c[k][0] + c[k][1];
+    if (s == -1.2345) sink[blockIdx.x] = s;  // never true; keeps the chains live
+}
+
 }  // namespace nirk
+
+int nir_probe_mma_launch(double *sink, int grid, int iters, cudaStream_t st)
+{
+    nirk::k_dmma_probe<<<grid, 256, 0, st>>>(sink, iters, 0.25, 1e-3);
+    return cudaPeekAtLastError() == cudaSuccess ? NIR_OK : (cudaGetLastError(), NIR_ERR_CUDA);
+}
 
 int nir_geom_launch(const nirk::GeoArgs &a, cudaStream_t st)
 {
@@ -212,6 +297,15 @@ int nir_geom_launch(const nirk::GeoArgs &a, cudaStream_t st)
     long long blocks = (total + 255) / 256;
     if (blocks > 65535LL * 8) blocks = 65535LL * 8;
     nirk::k_geometry<<<(unsigned)blocks, 256, 0, st>>>(a);
+    return cudaPeekAtLastError() == cudaSuccess ? NIR_OK : (cudaGetLastError(), NIR_ERR_CUDA);
+}
+
+int nir_geom_factors_launch(const nirk::GeoArgs &a, cudaStream_t st)
+{
+    const long long total = a.pp ? a.nelem * nirk::npts(a.shape, a.Q) : a.nelem;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 65535LL * 8) blocks = 65535LL * 8;
+    nirk::k_geometry_from_factors<<<(unsigned)blocks, 256, 0, st>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? NIR_OK : (cudaGetLastError(), NIR_ERR_CUDA);
 }
 

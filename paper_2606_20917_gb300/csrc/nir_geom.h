@@ -14,9 +14,15 @@ struct GeoArgs {
     int *err;
     long long nelem;
     int shape, Q, g, pp;
+    // caller-given factors (nir_geom_factors_launch): d xi/d x and |J|
+    const double *dxi_dx = nullptr;
+    const double *jac = nullptr;
+    int per_elem = 0;
 };
 }  // namespace nirk
 
 int nir_geom_launch(const nirk::GeoArgs &a, cudaStream_t st);
+int nir_geom_factors_launch(const nirk::GeoArgs &a, cudaStream_t st);
 int nir_convert_launch(const double *src, float *d32, void *d16, long long n, cudaStream_t st);
 int nir_probe_launch(double *sink, int grid, int iters, cudaStream_t st);
+int nir_probe_mma_launch(double *sink, int grid, int iters, cudaStream_t st);

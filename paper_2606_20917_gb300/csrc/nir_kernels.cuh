@@ -1269,9 +1269,11 @@ __device__ __forceinline__ void l2_prefetch(const void *src, unsigned bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
-// Wait for phase `parity` of `bar` for at most ~2^31 clock cycles (about a
-// second).  Returns false on timeout after setting the device error word.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *err)
+// Wait for phase `parity` of `bar` for at most `limit` clock cycles (by
+// default 2^31, about a second).  Returns false on timeout after setting the
+// device error word.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *err,
+                                          long long limit = (1LL << 31))
 {
     const long long t0 = clock64();
     unsigned done = 0;
@@ -1282,7 +1284,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
             : "r"(smem_u32(bar)), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > (1LL << 31)) {
+        if (clock64() - t0 > limit) {
             if (err) atomicExch(err, 1);
             return false;
         }

@@ -70,8 +70,9 @@ extern "C" int nir_helmholtz_host_noalloc(nir_block *b, int prec, double lambda,
     cudaStream_t st = b->ctx->stream;
     NIR_CUDA_TRY(cudaMemcpyAsync(d_in, h_in, bytes, cudaMemcpyHostToDevice, st));
     rc = nir_launch_op(b, prec, nirk::OP_HELM, lambda, d_in, nullptr, nullptr, d_out, nullptr, nullptr, st, 0);
-    if (rc) return rc;
-    NIR_CUDA_TRY(cudaMemcpyAsync(h_out, d_out, bytes, cudaMemcpyDeviceToHost, st));
-    NIR_CUDA_TRY(cudaStreamSynchronize(st));
-    return NIR_OK;
+    if (!rc && cudaMemcpyAsync(h_out, d_out, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = NIR_ERR_CUDA;
+    // once a copy from h_in is queued, return only after the stream has drained
+    // (also on failure), so the caller may reuse h_in and h_out at once
+    if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NIR_ERR_CUDA;
+    return rc;
 }

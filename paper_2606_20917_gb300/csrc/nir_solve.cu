@@ -502,6 +502,7 @@ extern "C" int nir_tune(nir_mesh *m, const char *cache_path)
                 int &v = b->helm_variant[prec];
                 if (v == NIR_VARIANT_TOE && nir_toe_prepare(b, prec, b->helm_grid[prec]) != NIR_OK) v = 0;
                 if (v < 0 || v > NIR_VARIANT_TOE) v = 0;
+                if (v != NIR_VARIANT_TOE) nir_toe_release(b);
                 continue;
             }
             float best = 1e30f;

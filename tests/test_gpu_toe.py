@@ -176,3 +176,50 @@ def test_toe_kernel_info_and_unsupported(nir, ctx):
     assert e.value.code == -2
     with pytest.raises(nir.NirError):
         blk.set_tuning("f64", 5, 0, 0)
+
+
+def free_bytes():
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
+def test_toe_scratch_released_when_no_precision_uses_it(nir, ctx):
+    """Leaving variant 4 frees the threading-over-elements scratch once no
+    precision of the block uses it; the results stay correct."""
+    E, P = 4096, 8
+    g, nodes, blk = block(nir, ctx, "hex", P, E, False)
+    x = W.coefficients(E, blk.M, seed=2)
+    y0 = apply(nir, blk, "f64", x).cpu()
+    base = free_bytes()
+    blk.set_tuning("f64", 4, 0, 0)
+    blk.set_tuning("f32", 4, 0, 0)
+    held = base - free_bytes()
+    expect = 5 * blk.NQ * E * 8   # 5 arrays of Q^3 FP64 values per thread, one thread per element at most
+    assert held >= 0.5 * expect, (held, expect)
+    assert torch.equal(apply(nir, blk, "f64", x).cpu(), y0)   # FP64: the same bits
+    blk.set_tuning("f64", 0, 0, 0)
+    assert base - free_bytes() >= 0.5 * expect               # FP32 still uses it
+    blk.set_tuning("f32", 0, 0, 0)
+    assert abs(base - free_bytes()) < 0.1 * expect           # released
+    assert torch.equal(apply(nir, blk, "f64", x).cpu(), y0)
+
+
+def test_toe_tuning_refused_inside_capture(nir, ctx):
+    """Selecting variant 4 allocates and synchronises: refused (STATE) while
+    the context stream is being captured, with nothing left half-done."""
+    g, nodes, blk = block(nir, ctx, "tet", 3, 64, False)
+    s = torch.cuda.Stream()
+    c2 = nir.Context(0, s)
+    b2 = nir.Block(c2, "tet", 64, 3)
+    b2.set_geometry(g, torch.from_numpy(np.ascontiguousarray(nodes)).cuda())
+    graph = torch.cuda.CUDAGraph()
+    rc = None
+    with torch.cuda.graph(graph, stream=s):
+        rc = nir.lib().nir_block_set_tuning(b2.h, 0, 4, 0, 0)
+        keep = torch.ones(4, device="cuda") * 2   # the capture holds one node
+    del keep
+    assert rc == -8
+    assert b2.get_tuning("f64")[0] == 0
+    b2.set_tuning("f64", 4, 0, 0)   # outside the capture it works
+    x = W.coefficients(64, b2.M, seed=1)
+    assert torch.equal(apply(nir, b2, "f64", x), apply(nir, blk, "f64", x))

@@ -7,7 +7,9 @@ allocation after set-up.  It stages through a fixed device array compiled into
 the library instead of allocated buffers.  This test calls it through the C ABI
 and checks it against the allocating entry point nir_helmholtz_host on two
 calls in a row (the shared array must not leak state from one call into the
-next), plus its size limit.  The file name makes pytest collect it last.
+next), plus its size limit.  Both calls must give exactly the allocating call's bits (the same kernel on
+the same inputs), and the device's free memory must not change across them.
+The file name makes pytest collect it last.
 """
 import ctypes as C
 
@@ -41,31 +43,48 @@ def curved_block(nir, ctx, E, P):
     return blk
 
 
-def rel(a, b):
-    return (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item()
+def free_bytes():
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-6)])
-def test_noalloc_matches_host_entry_point_twice(nir, prec, tol):
+# (precision, Helmholtz tuning variant): the default element-group kernel and
+# the threading-over-elements kernel (variant 4), whose global scratch is
+# prepared by set_tuning, so the no-allocation call only uses it
+CASES = [("f64", 0), ("f32", 0), ("bf16", 0), ("f64", 4), ("f32", 4)]
+
+
+@pytest.mark.parametrize("prec,variant", CASES)
+def test_noalloc_matches_host_entry_point_twice(nir, prec, variant):
     torch.cuda.set_device(0)
     ctx = nir.Context(0)
     blk = curved_block(nir, ctx, 300, 4)
     dt = nir.DTYPE[prec]
+    if variant:
+        blk.set_tuning(prec, variant, 0, 0)
     if prec != "f64":
         # low-precision factors are derived by an allocating call first
         u0 = torch.zeros((blk.nelem, blk.M), dtype=dt, device="cuda")
         blk.helmholtz(u0, prec=prec)
         torch.cuda.synchronize()
     f = nir.lib().nir_helmholtz_host_noalloc
-    for call, seed in enumerate((11, 12)):
-        u = torch.from_numpy(W.coefficients(blk.nelem, blk.M, seed)).to(dt).pin_memory()
-        ref = torch.empty_like(u).pin_memory()
-        out = torch.full_like(u, float("nan")).pin_memory()
+    us = [torch.from_numpy(W.coefficients(blk.nelem, blk.M, seed)).to(dt).pin_memory() for seed in (11, 12)]
+    refs = [torch.empty_like(u).pin_memory() for u in us]
+    outs = [torch.full_like(u, float("nan")).pin_memory() for u in us]
+    # the allocating entry point (its staging buffers) and one no-allocation call
+    # (the first call on a device looks up the fixed array) come before the count
+    for u, ref in zip(us, refs):
         blk.helmholtz_host(u, ref, lam=1.5, prec=prec)
+    warm = torch.empty_like(us[0]).pin_memory()
+    assert f(blk.h, nir.PREC[prec], 1.5, C.c_void_p(us[0].data_ptr()), C.c_void_p(warm.data_ptr())) == 0
+    before = free_bytes()
+    for call, (u, ref, out) in enumerate(zip(us, refs, outs)):
         rc = f(blk.h, nir.PREC[prec], 1.5, C.c_void_p(u.data_ptr()), C.c_void_p(out.data_ptr()))
         assert rc == 0, (call, rc)
-        assert torch.isfinite(out).all()
-        assert rel(out.double(), ref.double()) <= tol, call
+        # the same kernel on the same inputs: the same bits as the allocating call
+        assert torch.equal(out, ref), (call, prec, variant)
+    assert free_bytes() == before, "the no-allocation entry point changed the device's free memory"
+    assert blk.get_tuning(prec)[0] == variant
 
 
 def test_noalloc_rejects_oversize_and_missing_factors(nir):
