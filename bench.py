@@ -223,6 +223,16 @@ def max_over_ranks(ws, v: float, device=None) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(ws, v: float, device=None) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t)
+    return float(t.item())
+
+
 def run_reference(args, ws, rank):
     """The FP64 oracle on a bounded sample of the workload, on the host cores."""
     import oracle
@@ -635,12 +645,31 @@ def oracle_solve_sample(wl, ids, lam):
     return oracle.helmholtz_solve(shape, P, Q, g, nodes, lam, bs)
 
 
-def solve_compare(nir, mesh, blk, wl, dev, args, ws, local, variants, sample=8):
+def dist_allreduce(ws, dev):
+    """Host-array sum over the torchrun ranks for a sharded solve (None at N = 1)."""
+    if ws == 1:
+        return None
+    import torch
+    import torch.distributed as dist
+    on_gpu = dist.get_backend() == "nccl"
+
+    def f(v):
+        t = torch.from_numpy(v.copy())
+        if on_gpu:
+            t = t.to(dev)
+        dist.all_reduce(t)
+        v[:] = t.cpu().numpy()
+    return f
+
+
+def solve_compare(nir, mesh, blk, wl, dev, args, ws, local, variants, sample=8, allreduce=None):
     """Time each solver variant once (after a loose warm-up solve that captures
     its iteration graphs and builds the preconditioner) on the manufactured
     right-hand side, to relative residual args.tol and forward tolerance
     args.fwd_tol; report its error against the oracle's per-element Cholesky
-    solution on a seeded sample of elements."""
+    solution on a seeded sample of elements.  With `allreduce` the mesh is this
+    rank's part of a sharded mesh (wl holds its elements) and the solve sums
+    its scalars over the ranks."""
     import torch
     lam = 1.0
     E, M = blk.nelem, blk.M
@@ -656,6 +685,8 @@ def solve_compare(nir, mesh, blk, wl, dev, args, ws, local, variants, sample=8):
         kw = dict(lam=lam, inner_prec=inner, inner_vectors=vec, tol=args.tol, fwd_tol=args.fwd_tol, max_outer=60,
                   max_inner=args.max_inner if inner != "bf16" else min(args.max_inner, 3000),
                   inner_tol=args.inner_tol)
+        if allreduce is not None:
+            kw["allreduce"] = allreduce
         mesh.cg_solve(b, torch.zeros_like(b), **dict(kw, tol=1e-2, fwd_tol=0.0))
         x = torch.zeros_like(b)
         torch.cuda.synchronize()
@@ -666,8 +697,10 @@ def solve_compare(nir, mesh, blk, wl, dev, args, ws, local, variants, sample=8):
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
         dt = max_over_ranks(ws, dt, dev)
+        # replicas: N copies of the problem; sharded: one problem split over the ranks
+        ndof_all = ws * b.numel() if allreduce is None else int(sum_over_ranks(ws, float(b.numel()), dev))
         r = dict(rc=rc, operator=inner, inner_vectors=vec if inner != "f64" else "f64", wall_seconds=dt,
-                 gdofs=ws * b.numel() / dt / 1e9, outer=st["outer"], inner_total=st["inner_total"],
+                 gdofs=ndof_all / dt / 1e9, outer=st["outer"], inner_total=st["inner_total"],
                  rel_residual=st["rel_residual"], rel_correction=st["rel_correction"], clocks=clk.summary())
         if x_or is not None:
             r["fwd_error_vs_oracle"] = rel_err(x.view(E, M)[torch.from_numpy(ids).to(dev)].cpu().numpy(), x_or)
@@ -689,7 +722,10 @@ def solve_compare(nir, mesh, blk, wl, dev, args, ws, local, variants, sample=8):
 
 def run_solve(args, ws, rank, local):
     """Helmholtz solve on the P = 6 curved-hex workload: plain FP64 CG versus CG
-    with the operator in FP32 / BF16 inside FP64 iterative refinement."""
+    with the operator in FP32 / BF16 inside FP64 iterative refinement.  Under
+    torchrun (N > 1) the mesh is sharded: each rank takes its cost-balanced
+    contiguous element range (nir_partition_elements) and the solve sums its
+    FP64 scalars over the ranks (strong scaling: one problem, N GPUs)."""
     import torch
     import paper_2606_20917_gb300 as nir
 
@@ -697,13 +733,17 @@ def run_solve(args, ws, rank, local):
     dev = torch.device("cuda", local)
     ctx = nir.Context(local, torch.cuda.current_stream())
     wl = W.workload(args.workload)
+    if ws > 1:
+        first = nir.partition_elements([(wl["shape"], wl["P"], wl["nodes"].shape[0])], ws)
+        wl = dict(wl, nodes=np.ascontiguousarray(wl["nodes"][first[rank]:first[rank + 1]]))
     E = wl["nodes"].shape[0]
     blk = nir.Block(ctx, wl["shape"], E, wl["P"], deformed=wl["deformed"])
     blk.set_geometry(wl["gorder"], torch.from_numpy(wl["nodes"]).to(dev))
     mesh = nir.Mesh(ctx, [blk])
     if not args.no_tune:
         mesh.tune(args.tune_cache)  # set-up, untimed
-    results, ndof = solve_compare(nir, mesh, blk, wl, dev, args, ws, local, args.solve_precs.split(","))
+    results, ndof = solve_compare(nir, mesh, blk, wl, dev, args, ws, local, args.solve_precs.split(","),
+                                  allreduce=dist_allreduce(ws, dev))
     if rank != 0:
         return
     best = max((r for k, r in results.items() if k != "f64" and r["rc"] == 0), key=lambda r: r["gdofs"],
@@ -711,9 +751,12 @@ def run_solve(args, ws, rank, local):
     line = {"metric": "Helmholtz solve GDOF/s to relative residual %g, forward tolerance %g" % (args.tol, args.fwd_tol),
             "value": best["gdofs"] if best else None, "unit": "GDOF/s", "n_gpus": ws, "steps": 1,
             "warmup": 1, "ms_per_step": best["wall_seconds"] * 1e3 if best else None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 operator / f64 refinement", "data": "synthetic",
+            "scaling": "strong" if ws > 1 else "weak", "vs_baseline": None,
+            "dtype": "f32 operator / f64 refinement", "data": "synthetic",
             "config": dict(workload_config(args, wl), solve="CG on the broken operator, Jacobi preconditioner",
-                           rhs="B^T W f, f = (3 pi^2 + 1) sin(pi x) sin(pi y) sin(pi z)"),
+                           rhs="B^T W f, f = (3 pi^2 + 1) sin(pi x) sin(pi y) sin(pi z)",
+                           sharding=(f"{ws} ranks, contiguous cost-balanced element ranges, CG scalars summed "
+                                     f"over the ranks") if ws > 1 else "none"),
             "solves": results,
             "speedup_vs_fp64_cg": best.get("speedup_vs_fp64_cg") if best else None}
     print(json.dumps(line), flush=True)

@@ -67,7 +67,8 @@ enum {
     NIR_ERR_NO_MEMORY = -6,     /* device or host allocation failed */
     NIR_ERR_GEOMETRY = -7,      /* non-positive Jacobian determinant */
     NIR_ERR_STATE = -8,         /* geometry not set / object in wrong state */
-    NIR_ERR_TOO_LARGE = -9      /* request exceeds a fixed capacity of the library */
+    NIR_ERR_TOO_LARGE = -9,     /* request exceeds a fixed capacity of the library */
+    NIR_ERR_COMM = -10          /* the caller's cross-rank reduction reported a failure */
 };
 
 typedef struct nir_ctx nir_ctx;
@@ -338,6 +339,45 @@ typedef struct {
  * refinement, CG breakdown), NONFINITE, CUDA, NO_MEMORY. */
 int nir_cg_solve(nir_mesh *mesh, double lambda, const double *b, double *x, const nir_cg_opts *opts,
                  nir_cg_stats *stats);
+
+/* ---------------------------------------------------------------------------
+ * Solves sharded across ranks (one process per GPU).
+ *
+ * The operators are element-local, so a mesh splits into contiguous element
+ * ranges, one per rank, with no exchange in the apply (the paper's CPU runs
+ * split elements across MPI ranks the same way, Sec. 4).  The broken
+ * operator's CG then needs only sums of FP64 scalars over the ranks.
+ * --------------------------------------------------------------------------- */
+
+/* Contiguous element ranges of the concatenation of nblocks blocks (block b:
+ * shape[b], degree P[b], nelem[b] elements, in block order), one per rank,
+ * balanced by the sum-factorised Helmholtz flops per element of each
+ * (shape, P) (the costs the kernels' rooflines use).  first_out[nranks + 1]
+ * (HOST): rank r owns global elements [first_out[r], first_out[r+1]); first
+ * is 0 and last the total.  Host only (no GPU needed).  Errors: INVALID_ARG. */
+int nir_partition_elements(int nblocks, const int *shape, const int *P, const int64_t *nelem, int nranks,
+                           int64_t *first_out);
+
+/* Sum of n FP64 values over all ranks, in place: `values` is a HOST array of
+ * this rank's partial sums on entry and must hold the totals on return, the
+ * same on every rank.  Returns 0 on success; anything else aborts the solve
+ * with NIR_ERR_COMM. */
+typedef int (*nir_allreduce_fn)(double *values, int n, void *user);
+
+/* nir_cg_solve on one rank's part of a sharded mesh: `mesh` holds this rank's
+ * elements (e.g. its range from nir_partition_elements), b and x its entries
+ * (DEVICE FP64 [ndof of this mesh]).  Every rank calls it collectively with
+ * the same options; every dot product (residual norms, CG scalars, the
+ * forward-error norms, the preconditioner check) is this rank's partial sum
+ * passed through `allreduce`, so all ranks take the same iterations and stop
+ * together.  The iterations run without graph capture, with two host round
+ * trips per CG iteration (the partial p.Ap, then r.z and r.r).  A rank that
+ * fails in its own work returns without further reductions: the caller's
+ * reduction must then fail (e.g. a process-group timeout) on the other
+ * ranks.  Results equal the single-rank solve up to the rounding of the
+ * reduction order.  Errors: as nir_cg_solve, plus COMM. */
+int nir_cg_solve_dist(nir_mesh *mesh, double lambda, const double *b, double *x, const nir_cg_opts *opts,
+                      nir_cg_stats *stats, nir_allreduce_fn allreduce, void *user);
 
 /* ---------------------------------------------------------------------------
  * Conforming C0 assembly (quadrilateral and hexahedral blocks).

@@ -92,6 +92,8 @@ _SIGS = {
     "nir_probe_fp64_peak": [_vp, C.POINTER(_d)],
     "nir_probe_fp64_mma_peak": [_vp, C.POINTER(_d)],
     "nir_ctx_selftest_wait": [_vp, _i64],
+    "nir_cg_solve_dist": [_vp, _d, _vp, _vp, C.POINTER(CGOpts), C.POINTER(CGStats), _vp, _vp],
+    "nir_partition_elements": [_i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i64), _i, C.POINTER(_i64)],
     "nir_asm_create": [_vp, C.POINTER(_vp), C.POINTER(_vp), _i, C.POINTER(_vp)],
     "nir_asm_num_dofs": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)],
     "nir_asm_local_map": [_vp, _vp],
@@ -111,6 +113,38 @@ for _name in ("nir_ctx_destroy", "nir_block_destroy", "nir_mesh_destroy", "nir_a
 _lib.nir_strerror.argtypes = [_i]
 _lib.nir_strerror.restype = C.c_char_p
 _lib.nir_version.restype = C.c_char_p
+
+
+# nir_allreduce_fn: int (*)(double *values, int n, void *user)
+ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.POINTER(C.c_double), C.c_int, C.c_void_p)
+
+
+def partition_elements(blocks, nranks: int) -> list[int]:
+    """Contiguous cost-balanced element ranges (nir_partition_elements) of
+    blocks given as (shape, P, nelem) in block order: returns first[nranks + 1];
+    rank r owns global elements [first[r], first[r + 1]).  Host only."""
+    nb = len(blocks)
+    sh = (C.c_int * nb)(*[SHAPES[b[0]] for b in blocks])
+    pp = (C.c_int * nb)(*[int(b[1]) for b in blocks])
+    ne = (_i64 * nb)(*[int(b[2]) for b in blocks])
+    out = (_i64 * (nranks + 1))()
+    _chk(_lib.nir_partition_elements(nb, sh, pp, ne, int(nranks), out), "nir_partition_elements")
+    return list(out)
+
+
+def _allreduce_callback(fn):
+    """Wrap fn(values: numpy float64 array) -> None (in-place sum over ranks)
+    as a nir_allreduce_fn; an exception becomes a non-zero return."""
+    import numpy as np
+
+    def cb(values, n, user):
+        try:
+            arr = np.ctypeslib.as_array(values, shape=(n,))
+            fn(arr)
+            return 0
+        except Exception:  # noqa: BLE001 -- reported to the library as a failed reduction
+            return 1
+    return ALLREDUCE_FN(cb)
 
 
 class NirError(RuntimeError):
@@ -393,16 +427,23 @@ class Mesh:
         return {0: "persistent", 1: "blocks"}[v.value]
 
     def cg_solve(self, b, x, lam=1.0, inner_prec="f32", tol=1e-10, max_outer=50, max_inner=2000,
-                 inner_tol=1e-4, jacobi=True, inner_vectors="f64", fwd_tol=0.0):
+                 inner_tol=1e-4, jacobi=True, inner_vectors="f64", fwd_tol=0.0, allreduce=None):
         """Returns (status code, stats dict); x is updated in place.  inner_vectors:
         "f64" (FP64 inner vectors and dots) or "f32"; fwd_tol > 0 also requires the
-        last correction |dx| <= fwd_tol |x| (see nir_cg_opts)."""
+        last correction |dx| <= fwd_tol |x| (see nir_cg_opts).  allreduce: for a
+        mesh that is one rank's part of a sharded mesh, a callable that sums a
+        float64 numpy array in place over the ranks (nir_cg_solve_dist)."""
         for t in (b, x):
             if t.dtype != torch.float64 or not t.is_cuda or t.numel() != self.ndof:
                 raise ValueError("b and x must be FP64 CUDA vectors of the mesh's dofs")
         o = _cg_opts(inner_prec, tol, max_outer, max_inner, inner_tol, jacobi, inner_vectors, fwd_tol)
         s = CGStats()
-        rc = _lib.nir_cg_solve(self.h, float(lam), _ptr(b), _ptr(x), C.byref(o), C.byref(s))
+        if allreduce is None:
+            rc = _lib.nir_cg_solve(self.h, float(lam), _ptr(b), _ptr(x), C.byref(o), C.byref(s))
+        else:
+            cb = _allreduce_callback(allreduce)   # kept alive for the call
+            rc = _lib.nir_cg_solve_dist(self.h, float(lam), _ptr(b), _ptr(x), C.byref(o), C.byref(s),
+                                        C.cast(cb, _vp), None)
         return rc, _cg_stats(s)
 
 

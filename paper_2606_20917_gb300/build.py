@@ -46,7 +46,7 @@ def _units():
             units.append((os.path.join(CSRC, "nir_mesh_inst.cu"), f"mesh_d{d}_p{p}.o",
                           [f"-DNIR_MESH_DIM={d}", f"-DNIR_PREC={p}"]))
     for src in ("nir_api.cu", "nir_geom.cu", "nir_solve.cu", "nir_cg.cu", "nir_asm.cu", "nir_noalloc.cu",
-                "nir_basis.cpp"):
+                "nir_basis.cpp", "nir_partition.cpp"):
         units.append((os.path.join(CSRC, src), os.path.splitext(src)[0] + ".o", []))
     return units
 

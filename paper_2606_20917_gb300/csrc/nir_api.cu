@@ -973,6 +973,7 @@ extern "C" const char *nir_strerror(int code)
     case NIR_ERR_NOT_CONVERGED: return "solver did not converge";
     case NIR_ERR_NONFINITE: return "non-finite value in solver";
     case NIR_ERR_NO_MEMORY: return "out of memory";
+    case NIR_ERR_COMM: return "cross-rank reduction failed";
     case NIR_ERR_GEOMETRY: return "non-positive or non-finite Jacobian determinant";
     case NIR_ERR_STATE: return "object not ready (geometry not set?)";
     case NIR_ERR_TOO_LARGE: return "request exceeds the library's fixed no-allocation scratch capacity";

@@ -45,9 +45,14 @@ namespace {
 using nirv::st_v;
 using nirv::to_d;
 
+// Device-side CG scalars.  With `defer` set (a solve sharded across ranks)
+// the reduction kernels only publish this rank's partial sums (pAp; rzn and
+// rr) and the host, after summing them over the ranks, writes alpha and beta
+// back; `done` then stays 0 and the host ends the loop.
 struct CGScal {
     double rz, pAp, alpha, beta, rr, thresh;
-    int done, bad, iters, pad;
+    int done, bad, iters, defer;
+    double rzn;
 };
 
 constexpr int kThreads = 256;
@@ -175,6 +180,7 @@ __global__ void __launch_bounds__(kThreads) k_alpha(const V *__restrict__ p, con
     double t[1];
     if (finish_reduce(v, part, ticket, t)) {
         s->pAp = t[0];
+        if (s->defer) return;
         if (!isfinite(t[0])) { s->bad = 2; s->done = 1; }
         else if (!(t[0] > 0.0)) { s->bad = 1; s->done = 1; }
         else s->alpha = s->rz / t[0];
@@ -243,6 +249,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(V) == 8 ? 3 : 4) k_update(V *
     block_sum(v);
     double t[2];
     if (finish_reduce(v, part, ticket, t)) {
+        if (s->defer) {
+            s->rzn = t[0];
+            s->rr = t[1];
+            return;
+        }
         s->beta = t[0] / s->rz;
         s->rz = t[0];
         s->rr = t[1];
@@ -290,7 +301,8 @@ __global__ void __launch_bounds__(kThreads) k_pupdate(V *__restrict__ p, const V
 template <class V, class T>
 __global__ void __launch_bounds__(kThreads) k_start(const V *__restrict__ r, V *__restrict__ z, V *__restrict__ p,
                                                     T *__restrict__ pT, const V *__restrict__ dinv, long long n,
-                                                    double *part, unsigned *ticket, CGScal *s, double thresh)
+                                                    double *part, unsigned *ticket, CGScal *s, double thresh,
+                                                    int defer)
 {
     const long long S = (long long)gridDim.x * kThreads;
     double v[2] = {0.0, 0.0};
@@ -335,8 +347,9 @@ __global__ void __launch_bounds__(kThreads) k_start(const V *__restrict__ r, V *
         s->rr = t[1];
         s->thresh = thresh;
         s->iters = 0;
+        s->defer = defer;
         s->bad = (isfinite(t[0]) && isfinite(t[1])) ? 0 : 2;
-        s->done = (s->bad || t[1] <= thresh) ? 1 : 0;
+        s->done = (!defer && (s->bad || t[1] <= thresh)) ? 1 : 0;
     }
 }
 
@@ -491,7 +504,10 @@ struct CGWork {
     void *chunk_op[kModes] = {};   // operator launch bindings of the graphs
     CgOperator *chunk_owner[kModes] = {};
     int chunk_len = 25;
+    const CgReducer *red = nullptr;   // set for the duration of a sharded solve
 };
+
+int CgReducer::sum(double *v, int n) const { return fn(v, n, user) == 0 ? NIR_OK : NIR_ERR_COMM; }
 
 void nir_cg_work_invalidate(CGWork *w)
 {
@@ -572,6 +588,12 @@ int cg_diagonal(CgOperator &op, CGWork *w, double lambda, cudaStream_t st)
     if (cudaMemcpyAsync(&bad, w->flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return NIR_ERR_CUDA;
+    if (w->red) {  // every rank takes the same branch
+        double v = bad ? 1.0 : 0.0;
+        rc = w->red->sum(&v, 1);
+        if (rc) return rc;
+        bad = v > 0.0;
+    }
     if (bad) return NIR_ERR_NONFINITE;  // a non-positive diagonal: the operator is not SPD
     w->diag_ready = true;
     w->diag_lambda = lambda;
@@ -625,8 +647,13 @@ int residual64(CgOperator &op, CGWork *w, double lambda, const double *b, const 
     k_dot<double><<<w->grid, kThreads, 0, st>>>(w->r64, w->r64, n, w->part, w->ticket + 2, w->dots);
     if (bb) k_dot<double><<<w->grid, kThreads, 0, st>>>(b, b, n, w->part, w->ticket + 2, w->dots + 1);
     double h[4] = {0, 0, 0, 0};
-    NIR_CUDA_TRY(cudaMemcpyAsync(h, w->dots, sizeof(double) * (extra ? 4 : 2), cudaMemcpyDeviceToHost, st));
+    const int nd = extra ? 4 : 2;
+    NIR_CUDA_TRY(cudaMemcpyAsync(h, w->dots, sizeof(double) * nd, cudaMemcpyDeviceToHost, st));
     NIR_CUDA_TRY(cudaStreamSynchronize(st));
+    if (w->red) {  // sharded: sum this rank's partial dot products over the ranks
+        rc = w->red->sum(h, nd);
+        if (rc) return rc;
+    }
     *rr = h[0];
     if (bb) *bb = h[1];
     if (extra) {
@@ -636,14 +663,85 @@ int residual64(CgOperator &op, CGWork *w, double lambda, const double *b, const 
     return NIR_OK;
 }
 
+// PCG of a solve sharded across ranks: the same kernels with deferred
+// scalars.  Each reduction kernel leaves this rank's partial sum in the
+// scalar block; the host reads it, sums it over the ranks (the caller's
+// reduction), and writes alpha / beta back for the next kernel.  Two host
+// round trips per iteration; every rank runs the same iterations because it
+// decides on the same reduced scalars.
+template <class V, class T>
+int run_pcg_dist(CgOperator &op, CGWork *w, int prec, double lambda, V *x, V *r, V *z, V *p, T *pT, T *Ap,
+                 const V *dinv, double thresh, int max_iter, int *iters, double *rr_out, int *bad_out, cudaStream_t st)
+{
+    const long long n = w->n;
+    T *pTk = (pT == (T *)p) ? nullptr : pT;
+    void *h = nullptr;
+    int rc = op.prepare(prec, lambda, pT ? (const void *)pT : (const void *)p, Ap, &h);
+    if (rc) return rc;
+    CGScal hs;
+    auto fetch = [&]() -> int {
+        if (cudaMemcpyAsync(&hs, w->scal, sizeof(CGScal), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return NIR_ERR_CUDA;
+        return NIR_OK;
+    };
+    auto put = [&](double *dst, double v) -> int {  // pageable source: copied before the call returns
+        return cudaMemcpyAsync(dst, &v, sizeof(double), cudaMemcpyHostToDevice, st) == cudaSuccess ? NIR_OK
+                                                                                                    : NIR_ERR_CUDA;
+    };
+    k_start<V, T><<<w->grid, kThreads, 0, st>>>(r, z, p, pTk, dinv, n, w->part, w->ticket + 3, w->scal, thresh, 1);
+    double v[2] = {0.0, 0.0};
+    int it = 0, bad = 0;
+    rc = fetch();
+    if (!rc) {
+        v[0] = hs.rz;
+        v[1] = hs.rr;
+        rc = w->red->sum(v, 2);
+    }
+    double rz = v[0], rr = v[1];
+    if (!rc && (!std::isfinite(rz) || !std::isfinite(rr))) bad = 2;
+    while (!rc && !bad && rr > thresh && it < max_iter) {
+        rc = op.launch(h, st);
+        if (rc) break;
+        k_alpha<V, T><<<w->grid, kThreads, 0, st>>>(p, Ap, n, w->part, w->ticket, w->scal);
+        if ((rc = fetch())) break;
+        v[0] = hs.pAp;
+        if ((rc = w->red->sum(v, 1))) break;
+        const double pAp = v[0];
+        if (!std::isfinite(pAp)) { bad = 2; break; }
+        if (!(pAp > 0.0)) { bad = 1; break; }
+        if ((rc = put(&w->scal->alpha, rz / pAp))) break;
+        k_update<V, T><<<w->grid, kThreads, 0, st>>>(x, r, z, p, Ap, dinv, n, w->part, w->ticket + 1, w->scal);
+        if ((rc = fetch())) break;
+        v[0] = hs.rzn;
+        v[1] = hs.rr;
+        if ((rc = w->red->sum(v, 2))) break;
+        ++it;
+        if (!std::isfinite(v[0]) || !std::isfinite(v[1])) { bad = 2; break; }
+        const double beta = v[0] / rz;
+        rz = v[0];
+        rr = v[1];
+        if (rr <= thresh) break;
+        if ((rc = put(&w->scal->beta, beta))) break;
+        k_pupdate<V, T><<<w->grid, kThreads, 0, st>>>(p, dinv ? z : r, pTk, n, w->scal);
+    }
+    op.release(h);
+    *iters = it;
+    *rr_out = rr;
+    *bad_out = bad;
+    return rc;
+}
+
 // Run PCG chunks until done or max_iter; returns iterations and final rr.
 template <class V, class T>
 int run_pcg(CgOperator &op, CGWork *w, int mode, int prec, double lambda, V *x, V *r, V *z, V *p, T *pT, T *Ap,
             const V *dinv, double thresh, int max_iter, int *iters, double *rr_out, int *bad_out, cudaStream_t st)
 {
+    if (w->red) return run_pcg_dist<V, T>(op, w, prec, lambda, x, r, z, p, pT, Ap, dinv, thresh, max_iter, iters,
+                                          rr_out, bad_out, st);
     const long long n = w->n;
     k_start<V, T><<<w->grid, kThreads, 0, st>>>(r, z, p, (pT == (T *)p) ? nullptr : pT, dinv, n, w->part,
-                                                w->ticket + 3, w->scal, thresh);
+                                                w->ticket + 3, w->scal, thresh, 0);
     int rc = capture_chunk<V, T>(op, w, mode, prec, lambda, x, r, z, p, pT, Ap, dinv);
     if (rc) return rc;
     CGScal hs;
@@ -788,8 +886,27 @@ int inner_sweep(CgOperator &op, CGWork *w, int prec, double lambda, double rn, c
 
 }  // namespace
 
+namespace {
+int cg_run_impl(CgOperator &op, CGWork *&wref, double lambda, const double *b, double *x, const nir_cg_opts *o,
+                nir_cg_stats *stats, const CgReducer *red);
+}
+
 int nir_cg_run(CgOperator &op, CGWork *&wref, double lambda, const double *b, double *x, const nir_cg_opts *o,
-               nir_cg_stats *stats)
+               nir_cg_stats *stats, const CgReducer *red)
+{
+    if (red && !red->fn) return NIR_ERR_INVALID_ARG;
+    // the reducer lives for this call only (it is cleared on every return path)
+    struct Guard {
+        CGWork *&w;
+        ~Guard() { if (w) w->red = nullptr; }
+    } guard{wref};
+    if (wref) wref->red = red;
+    return cg_run_impl(op, wref, lambda, b, x, o, stats, red);
+}
+
+namespace {
+int cg_run_impl(CgOperator &op, CGWork *&wref, double lambda, const double *b, double *x, const nir_cg_opts *o,
+                nir_cg_stats *stats, const CgReducer *red)
 {
     if (!b || !x || !o || (const void *)b == (const void *)x) return NIR_ERR_INVALID_ARG;
     if (!(o->tol > 0.0) || o->max_inner < 1 || !std::isfinite(lambda)) return NIR_ERR_INVALID_ARG;
@@ -805,6 +922,7 @@ int nir_cg_run(CgOperator &op, CGWork *&wref, double lambda, const double *b, do
     int rc = cg_alloc(op, wref);
     if (rc) return rc;
     CGWork *w = wref;
+    w->red = red;
     cudaStream_t st = op.context()->stream;
     const long long n = w->n;
     if (o->jacobi) {
@@ -914,6 +1032,7 @@ int nir_cg_run(CgOperator &op, CGWork *&wref, double lambda, const double *b, do
     if (stats) *stats = s;
     return status;
 }
+}  // namespace
 
 extern "C" int nir_cg_solve(nir_mesh *m, double lambda, const double *b, double *x, const nir_cg_opts *o,
                             nir_cg_stats *stats)
@@ -926,5 +1045,20 @@ extern "C" int nir_cg_solve(nir_mesh *m, double lambda, const double *b, double 
     }
     int rc = nir_mesh_sync_geometry(m);  // before the preconditioner and graphs are reused
     if (rc) return rc;
-    return nir_cg_run(*m->cg_op, m->cg, lambda, b, x, o, stats);
+    return nir_cg_run(*m->cg_op, m->cg, lambda, b, x, o, stats, nullptr);
+}
+
+extern "C" int nir_cg_solve_dist(nir_mesh *m, double lambda, const double *b, double *x, const nir_cg_opts *o,
+                                 nir_cg_stats *stats, nir_allreduce_fn allreduce, void *user)
+{
+    if (!m || !allreduce) return NIR_ERR_INVALID_ARG;
+    if (!std::isfinite(lambda) || !(lambda > 0.0)) return NIR_ERR_INVALID_ARG;
+    if (!m->cg_op) {
+        m->cg_op = new (std::nothrow) MeshOp(m);
+        if (!m->cg_op) return NIR_ERR_NO_MEMORY;
+    }
+    int rc = nir_mesh_sync_geometry(m);
+    if (rc) return rc;
+    const CgReducer red{allreduce, user};
+    return nir_cg_run(*m->cg_op, m->cg, lambda, b, x, o, stats, &red);
 }

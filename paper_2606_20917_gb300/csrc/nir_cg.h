@@ -29,10 +29,18 @@ struct CgOperator {
     virtual int diagonal(double lambda, double *d, cudaStream_t st) = 0;
 };
 
+// Sum of FP64 scalars over the ranks of a sharded solve (nir_cg_solve_dist).
+struct CgReducer {
+    nir_allreduce_fn fn;
+    void *user;
+    int sum(double *v, int n) const;   // NIR_OK or NIR_ERR_COMM
+};
+
 // Solve H x = b (see nir_cg_solve in nir.h for the options); w is the
-// operator's solver workspace, allocated on first use.
+// operator's solver workspace, allocated on first use.  red: null for a
+// single-rank solve; otherwise every dot product is summed over the ranks.
 int nir_cg_run(CgOperator &op, CGWork *&w, double lambda, const double *b, double *x, const nir_cg_opts *o,
-               nir_cg_stats *stats);
+               nir_cg_stats *stats, const CgReducer *red = nullptr);
 // Drop captured iteration graphs and the preconditioner (operator changed).
 void nir_cg_work_invalidate(CGWork *w);
 void nir_cg_work_free(CGWork *&w);

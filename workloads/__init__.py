@@ -298,3 +298,23 @@ def rotate_elements(nodes: np.ndarray, verts: np.ndarray, g: int, seed: int = 0)
             new_nodes[sel] = nodes[sel][:, nmap[r], :]
             new_verts[sel] = verts[sel][:, vmap[r]]
     return new_nodes, new_verts, which
+
+
+def shard_parts(parts: list[dict], first: list[int], rank: int) -> list[dict]:
+    """The blocks of rank `rank` of a mesh split into contiguous element ranges
+    (first[r] .. first[r+1] over the concatenation of `parts` in block order):
+    each part that overlaps the rank's range is cut to the overlap (its nodes
+    sliced; every other key kept), empty overlaps dropped.  Also records the
+    global element offset of each cut as "global_first"."""
+    lo, hi = first[rank], first[rank + 1]
+    out, off = [], 0
+    for p in parts:
+        n = p["nodes"].shape[0]
+        a, b = max(lo, off), min(hi, off + n)
+        if a < b:
+            q = dict(p)
+            q["nodes"] = np.ascontiguousarray(p["nodes"][a - off:b - off])
+            q["global_first"] = a
+            out.append(q)
+        off += n
+    return out
