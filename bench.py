@@ -889,7 +889,7 @@ def run_gsolve(args, ws, rank, local):
 
 
 def run_sweep(args, ws, rank, local):
-    """Helmholtz throughput against problem size for P = 1..8 on hexahedra and
+    """Helmholtz throughput against problem size for P = 1..9 on hexahedra and
     tetrahedra (the paper's GPU throughput study, Sec. 4.2): one block per
     (shape, P, size), throughput = DOF / device time of one apply (CUDA events
     over repeated applies, the faster of the two code generations of the
@@ -909,7 +909,7 @@ def run_sweep(args, ws, rank, local):
     targets = [float(t) for t in args.sweep_dofs.split(",")]
     recs = []
     for shape in args.sweep_shapes.split(","):
-        for P in range(1, 9):
+        for P in [int(v) for v in args.sweep_orders.split(",")]:
             N, Q = P + 1, P + 2
             M = num_modes(shape, N)
             for target in targets:
@@ -970,7 +970,7 @@ def run_sweep(args, ws, rank, local):
     line = {"metric": "Helmholtz apply GDOF/s vs DOF and P (sweep)", "value": None, "unit": "GDOF/s",
             "n_gpus": ws, "higher_is_better": True, "dtype": prec, "data": "synthetic",
             "config": {"workload": "hex (32-cell-style curved grids, lattice g = 2) and Kuhn-split tet meshes, "
-                                   "P = 1..8, Q = P + 2", "dof_targets": targets, "fp64_peak_tflops": fp64_peak},
+                                   "P = 1..9, Q = P + 2", "dof_targets": targets, "fp64_peak_tflops": fp64_peak},
             "sweep": recs}
     print(json.dumps(line), flush=True)
 
@@ -1078,6 +1078,7 @@ def main():
                     help="apply mode: expansion basis (nodal = GLL-Lagrange, quad/hex)")
     ap.add_argument("--sweep-shapes", default="hex,tet")
     ap.add_argument("--sweep-dofs", default="1e5,1e6,1e7,3e7")
+    ap.add_argument("--sweep-orders", default="1,2,3,4,5,6,7,8,9", help="sweep: polynomial degrees P")
     ap.add_argument("--sweep-no-toe", action="store_true", help="sweep the default strategy only")
     ap.add_argument("--strategy", choices=["groups", "elements"], default="groups",
                     help="apply mode: the default kernels (element groups per CTA) or threading over elements")

@@ -22,7 +22,7 @@
  *     the launch itself are returned, device-side errors surface at the next
  *     synchronising call of the caller.
  *   - P is the polynomial degree (N = P+1 modes per direction), Q the number of
- *     quadrature points per direction; supported: 1 <= P <= 8, Q = P + 2.
+ *     quadrature points per direction; supported: 1 <= P <= 9, Q = P + 2.
  *   - Layouts (element-major):
  *       coefficients [E][M], modes packed p outermost, then q, then r, with
  *         quad  q < N;            M = N^2

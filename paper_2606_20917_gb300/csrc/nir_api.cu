@@ -333,7 +333,7 @@ extern "C" int nir_block_create(nir_ctx *ctx, const nir_block_desc *d, nir_block
     if (!ctx || !d || !out) return NIR_ERR_INVALID_ARG;
     *out = nullptr;
     if (d->shape < NIR_QUAD || d->shape > NIR_TET || d->nelem < 1) return NIR_ERR_INVALID_ARG;
-    if (d->P < 1 || d->P > 8 || d->Q != d->P + 2) return NIR_ERR_UNSUPPORTED;
+    if (d->P < 1 || d->P > 9 || d->Q != d->P + 2) return NIR_ERR_UNSUPPORTED;
     if (d->basis != NIR_BASIS_MODIFIED && d->basis != NIR_BASIS_GLL_LAGRANGE) return NIR_ERR_INVALID_ARG;
     if (d->basis == NIR_BASIS_GLL_LAGRANGE && d->shape != NIR_QUAD && d->shape != NIR_HEX) return NIR_ERR_UNSUPPORTED;
     nir_block *b = new (std::nothrow) nir_block();

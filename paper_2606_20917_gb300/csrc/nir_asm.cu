@@ -688,7 +688,7 @@ extern "C" int nir_c0_numbering(int shape, int P, int basis, int nblocks, const 
 {
     if ((shape != NIR_QUAD && shape != NIR_HEX)) return NIR_ERR_UNSUPPORTED;
     if (basis != NIR_BASIS_MODIFIED && basis != NIR_BASIS_GLL_LAGRANGE) return NIR_ERR_INVALID_ARG;
-    if (P < 1 || P > 8 || nblocks < 1 || !nelem || !vertex_ids) return NIR_ERR_INVALID_ARG;
+    if (P < 1 || P > 9 || nblocks < 1 || !nelem || !vertex_ids) return NIR_ERR_INVALID_ARG;
     std::vector<long long> ne;
     for (int b = 0; b < nblocks; ++b) {
         if (nelem[b] < 1 || !vertex_ids[b]) return NIR_ERR_INVALID_ARG;

@@ -90,6 +90,7 @@ KInfo by_n(int N, int v)
     case 7: return make<7, OP>(v);
     case 8: return make<8, OP>(v);
     case 9: return make<9, OP>(v);
+    case 10: return make<10, OP>(v);
     default: return KInfo{};
     }
 }

@@ -36,6 +36,8 @@ constexpr int kShapes[3] = {HEX, PRISM, TET};
 constexpr int kShapes[2] = {QUAD, TRI};
 #endif
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(int);
+// variants per shape: N = P + 1 = 2 .. 10
+constexpr int kPerShape = 9;
 
 // every variant of one persistent kernel runs with the same thread count
 constexpr int kMeshNT = sizeof(typename CT<TT>::type) == 8 ? 256 : 512;
@@ -46,12 +48,25 @@ constexpr int kMeshNT = sizeof(typename CT<TT>::type) == 8 ? 256 : 512;
 // array at compile-time offsets (tables depend on shape and P only, so all
 // blocks of a variant share them).  The reference weights, read only by the
 // per-element-factor path and the gathers, are left out (they stay in the
-// shared-memory copy), which keeps all 3-D variants within 31 KB.
+// shared-memory copy); only the variants that use the constant bank (use_ctab)
+// take space in it.
+//
+// Constant-bank table operands let the compiler keep more values live: the
+// high-order variants would need up to 128 registers, and one persistent
+// kernel has a single register budget for all variants.  Variants whose
+// constant-table form fits in 64 registers use it; the others read their
+// tables from shared memory (the kernel is capped at 64 registers, two
+// 512-thread CTAs per SM).
+NIR_HD constexpr bool use_ctab(int SH, int N)
+{
+    return SH == HEX ? N <= 4 : SH == PRISM ? N <= 5 : SH == TET ? N <= 3 : true;
+}
+
 template <int VID>
 NIR_HD constexpr int ctab_size()
 {
-    constexpr int SH = kShapes[VID / 8], N = VID % 8 + 2, Q = N + 1;
-    return layout(SH, N, Q).total - npts(SH, Q);
+    constexpr int SH = kShapes[VID / kPerShape], N = VID % kPerShape + 2, Q = N + 1;
+    return use_ctab(SH, N) ? layout(SH, N, Q).total - npts(SH, Q) : 0;
 }
 
 template <int VID>
@@ -61,7 +76,7 @@ NIR_HD constexpr int ctab_base()
     else return ctab_base<VID - 1>() + ctab_size<VID - 1>();
 }
 
-constexpr int kCTabN = ctab_base<kNumShapes * 8 - 1>() + ctab_size<kNumShapes * 8 - 1>();
+constexpr int kCTabN = ctab_base<kNumShapes * kPerShape - 1>() + ctab_size<kNumShapes * kPerShape - 1>();
 
 #if NIR_PREC != 0
 __constant__ float c_tab[kCTabN];
@@ -78,17 +93,6 @@ struct CTab {
     }
 };
 #endif
-
-// Constant-bank table operands let the compiler keep more values live: the
-// high-order variants would need up to 128 registers, and one persistent
-// kernel has a single register budget for all variants.  Variants whose
-// constant-table form fits in 64 registers use it; the others read their
-// tables from shared memory (the kernel is capped at 64 registers, two
-// 512-thread CTAs per SM).
-NIR_HD constexpr bool use_ctab(int SH, int N)
-{
-    return SH == HEX ? N <= 4 : SH == PRISM ? N <= 5 : SH == TET ? N <= 3 : true;
-}
 
 template <int SH, int N, int VID>
 __device__ __noinline__ void run_item(const MeshBlk &mb, const MeshItem &m, unsigned char *smem, int &cur)
@@ -131,9 +135,9 @@ template <int VID>
 __device__ __forceinline__ void dispatch_one(int vid, const MeshBlk &mb, const MeshItem &m, unsigned char *smem,
                                              int &cur)
 {
-    if constexpr (VID < kNumShapes * 8) {
+    if constexpr (VID < kNumShapes * kPerShape) {
         if (vid == VID) {
-            run_item<kShapes[VID / 8], VID % 8 + 2, VID>(mb, m, smem, cur);
+            run_item<kShapes[VID / kPerShape], VID % kPerShape + 2, VID>(mb, m, smem, cur);
             return;
         }
         dispatch_one<VID + 1>(vid, mb, m, smem, cur);
@@ -162,8 +166,8 @@ __global__ void __launch_bounds__(kMeshNT, 2) k_mesh(const MeshBlk *__restrict__
 template <int VID>
 int smem_of(int vid)
 {
-    if constexpr (VID < kNumShapes * 8) {
-        if (vid == VID) return Config<kShapes[VID / 8], VID % 8 + 2, VID % 8 + 3, TT, OP_HELM, 0, kMeshNT>::SMEM;
+    if constexpr (VID < kNumShapes * kPerShape) {
+        if (vid == VID) return Config<kShapes[VID / kPerShape], VID % kPerShape + 2, VID % kPerShape + 3, TT, OP_HELM, 0, kMeshNT>::SMEM;
         return smem_of<VID + 1>(vid);
     }
     return -1;
@@ -172,8 +176,8 @@ int smem_of(int vid)
 template <int VID>
 int epb_of(int vid)
 {
-    if constexpr (VID < kNumShapes * 8) {
-        if (vid == VID) return Config<kShapes[VID / 8], VID % 8 + 2, VID % 8 + 3, TT, OP_HELM, 0, kMeshNT>::EPB;
+    if constexpr (VID < kNumShapes * kPerShape) {
+        if (vid == VID) return Config<kShapes[VID / kPerShape], VID % kPerShape + 2, VID % kPerShape + 3, TT, OP_HELM, 0, kMeshNT>::EPB;
         return epb_of<VID + 1>(vid);
     }
     return -1;
@@ -185,18 +189,19 @@ int epb_of(int vid)
 namespace nirk {
 namespace {
 template <int VID>
-void ctab_range(int vid, int &base, int &wq, int &gap, int &total)
+void ctab_range(int vid, int &base, int &wq, int &gap, int &total, bool &used)
 {
-    if constexpr (VID < kNumShapes * 8) {
+    if constexpr (VID < kNumShapes * kPerShape) {
         if (vid == VID) {
-            constexpr int SH = kShapes[VID / 8], N = VID % 8 + 2, Q = N + 1;
+            constexpr int SH = kShapes[VID / kPerShape], N = VID % kPerShape + 2, Q = N + 1;
+            used = use_ctab(SH, N);
             base = ctab_base<VID>();
             wq = layout(SH, N, Q).wq;
             gap = npts(SH, Q);
             total = layout(SH, N, Q).total;
             return;
         }
-        ctab_range<VID + 1>(vid, base, wq, gap, total);
+        ctab_range<VID + 1>(vid, base, wq, gap, total, used);
     }
 }
 }  // namespace
@@ -208,15 +213,19 @@ void ctab_range(int vid, int &base, int &wq, int &gap, int &total)
 #define NIR_TCAT(a, b) NIR_TCAT2(a, b)
 
 // Copy variant vid's FP32 table blob (the full layout, n values) into the
-// kernel's constant tables, without the reference weights.  FP64 kernels keep
-// their tables in shared memory: nothing to do.
+// kernel's constant tables, without the reference weights.  FP64 kernels, and
+// FP32/BF16 variants that read their tables from shared memory (no space in
+// the constant array), need nothing.
 int NIR_TCAT(NIR_MESH_DIM, NIR_PREC)(int vid, const float *blob, int n, cudaStream_t st)
 {
 #if NIR_PREC != 0
     using namespace nirk;
     int base = -1, wq = 0, gap = 0, total = 0;
-    ctab_range<0>(vid, base, wq, gap, total);
+    bool used = false;
+    ctab_range<0>(vid, base, wq, gap, total, used);
     if (base < 0 || n != total || !blob) return NIR_ERR_INVALID_ARG;
+    if (!used) return NIR_OK;
+    if (base + total - gap > kCTabN) return NIR_ERR_INVALID_ARG;  // never: the layout reserves exactly this
     if (cudaMemcpyToSymbolAsync(c_tab, blob, sizeof(float) * wq, sizeof(float) * base, cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
         cudaMemcpyToSymbolAsync(c_tab, blob + wq + gap, sizeof(float) * (total - wq - gap), sizeof(float) * (base + wq),
@@ -236,8 +245,8 @@ MeshKInfo NIR_MCAT(NIR_MESH_DIM, NIR_PREC)(int shape, int P)
     int si = -1;
     for (int i = 0; i < kNumShapes; ++i)
         if (kShapes[i] == shape) si = i;
-    if (si < 0 || P < 1 || P > 8) return k;
-    k.vid = si * 8 + (P - 1);
+    if (si < 0 || P < 1 || P > kPerShape) return k;
+    k.vid = si * kPerShape + (P - 1);
     k.fn = reinterpret_cast<const void *>(&k_mesh);
     k.smem = smem_of<0>(k.vid);
     k.epb = epb_of<0>(k.vid);

@@ -48,6 +48,7 @@ KInfo NIR_TCAT(NIR_SHAPE, NIR_PREC)(int P)
     case 7: return mk<7>();
     case 8: return mk<8>();
     case 9: return mk<9>();
+    case 10: return mk<10>();
     default: return KInfo{};
     }
 }

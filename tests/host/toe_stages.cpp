@@ -63,6 +63,7 @@ static int by_n(int P, double lam)
     case 7: return run<SH, 7>(lam);
     case 8: return run<SH, 8>(lam);
     case 9: return run<SH, 9>(lam);
+    case 10: return run<SH, 10>(lam);
     }
     return 1;
 }

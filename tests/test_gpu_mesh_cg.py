@@ -290,3 +290,29 @@ def test_full_p6_solve_sampled(nir, ctx, inner, vectors):
     assert rel(xs, xr) <= FWD, (rel(xs, xr), st)
     for i in range(len(ids)):
         assert rel(xs[i], xr[i]) <= FWD, (i, rel(xs[i], xr[i]))
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_mesh_with_p9_blocks(nir, ctx, prec, tol):
+    """P = 9 (the top order of the paper's GPU study) in the persistent mesh
+    kernel and in the block-kernel launch form: the same bits, and the oracle."""
+    parts = [dict(shape="hex", P=9, Q=11, gorder=2, nodes=W.hex_grid(2, 2, amp=0.05)[:7], deformed=True),
+             dict(shape="prism", P=9, Q=11, gorder=1, nodes=W.perturb_vertices(W.prism_split(2, 2, 2), 0.1, 3)[:5],
+                  deformed=False),
+             dict(shape="tet", P=9, Q=11, gorder=1, nodes=W.perturb_vertices(W.tet_kuhn(2), 0.1, 4)[:13],
+                  deformed=False),
+             dict(shape="hex", P=2, Q=4, gorder=2, nodes=W.hex_grid(3, 2, amp=0.05)[:20], deformed=True)]
+    mesh, blocks = build_mesh(nir, ctx, parts)
+    x64 = W.coefficients(1, mesh.ndof, seed=9)[0]
+    x = torch.from_numpy(x64).cuda().to(nir.DTYPE[prec])
+    mesh.set_launch(prec, "persistent")
+    y0 = mesh.helmholtz(x, prec=prec).clone()
+    mesh.set_launch(prec, "blocks")
+    y1 = mesh.helmholtz(x, prec=prec)
+    assert torch.equal(y0, y1)
+    y = y0.double().cpu().numpy()
+    for b, o, p in zip(blocks, mesh.offsets, parts):
+        n = b.nelem * b.M
+        ref = oracle.helmholtz(p["shape"], p["P"], p["Q"], p["gorder"], p["nodes"], 1.0,
+                               x64[o:o + n].reshape(b.nelem, b.M))
+        assert rel(y[o:o + n].reshape(b.nelem, b.M), ref) <= tol, (p["shape"], p["P"])

@@ -56,7 +56,7 @@ def dev(x, prec, nir):
 
 
 @pytest.mark.parametrize("shape", ["quad", "hex"])
-@pytest.mark.parametrize("P", [1, 2, 3, 4, 6, 8])
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 6, 8, 9])
 def test_fp64_modal_operators(nir, ctx, shape, P):
     E = 70 if shape == "quad" else (40 if P <= 4 else 12)
     g, nodes, blk = block(nir, ctx, shape, P, E)

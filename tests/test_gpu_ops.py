@@ -1,7 +1,7 @@
 """GPU parity of every elemental operator against the FP64 oracle.
 
 Through the C ABI (Python binding over libnir.so) on seeded synthetic meshes:
-  * every operator x every shape x P in {1..8} in FP64, element by element
+  * every operator x every shape x P in {1..9} in FP64, element by element
     (norm-wise relative error <= 1e-12 per block, <= 1e-11 per element);
   * FP32 single apply <= 1e-5, BF16 (bf16 storage, FP32 arithmetic) <= 3e-2;
   * element counts chosen to span several CTAs plus a ragged tail, E = 1, and
@@ -142,7 +142,7 @@ OPS = ["bwd", "iprod", "physderiv", "iprod_deriv", "mass", "helm"]
 
 
 @pytest.mark.parametrize("shape", ["quad", "tri", "hex", "prism", "tet"])
-@pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_fp64_all_ops(nir, ctx, shape, P):
     deformed = shape in ("hex", "quad")
     E = nelem_for(shape, P)
@@ -172,7 +172,7 @@ def test_fp64_affine_tensor_blocks(nir, ctx, shape, P):
 
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
 @pytest.mark.parametrize("shape", ["quad", "tri", "hex", "prism", "tet"])
-@pytest.mark.parametrize("P", [1, 4, 8])
+@pytest.mark.parametrize("P", [1, 4, 8, 9])
 def test_low_precision_all_ops(nir, ctx, prec, shape, P):
     deformed = shape in ("hex", "quad")
     E = nelem_for(shape, P)
@@ -185,7 +185,8 @@ def test_low_precision_all_ops(nir, ctx, prec, shape, P):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
-@pytest.mark.parametrize("shape,P", [("hex", 4), ("hex", 6), ("tet", 4), ("prism", 6), ("quad", 4), ("tri", 7)])
+@pytest.mark.parametrize("shape,P", [("hex", 4), ("hex", 6), ("tet", 4), ("prism", 6), ("quad", 4), ("tri", 7),
+                                     ("hex", 9), ("tet", 9)])
 def test_helmholtz_every_launch_variant(nir, ctx, prec, shape, P):
     """Every elements-per-CTA variant the tuner may pick (default, half, double;
     for FP32/BF16 at P = 6 the double group runs without its staging buffer),
@@ -293,7 +294,7 @@ def test_error_paths(nir, ctx):
         fresh.set_geometry(1, torch.from_numpy(bad).cuda())
     assert ei.value.code == -7
     with pytest.raises(nir.NirError) as ei:
-        nir.Block(ctx, "hex", 10, 9)
+        nir.Block(ctx, "hex", 10, 10)   # P = 9 is the highest order compiled
     assert ei.value.code == -2
 
 

@@ -2,7 +2,7 @@
 variant 4: one thread per element, intermediate tensors in global scratch;
 the second GPU strategy of Sec. 3.3) against the FP64 oracle.
 
-  * every shape x P in {1, 2, 3, 5, 8} x precision: the oracle on all elements
+  * every shape x P in {1, 2, 3, 5, 8, 9} x precision: the oracle on all elements
     (on a sample for high-order hexes), plus the whole block against the
     default kernel (in FP64 bit for bit: both strategies run the same
     operations in the same order, so the autotuner may switch between them);
@@ -79,7 +79,7 @@ def apply(nir, blk, prec, x, lam=1.3):
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("P", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("P", [1, 2, 3, 5, 8, 9])
 def test_toe_matches_oracle(nir, ctx, prec, shape, P):
     deformed = shape in ("quad", "hex")
     E = 300 if shape in ("quad", "tri") else (101 if P <= 3 else 45)

@@ -3,7 +3,7 @@ basis, collocation derivatives and the even/odd form) against the oracle's
 independent quadrature and Jacobi code (no GPU involved).
 
 A small program (``tests/host/tables.cpp``) dumps the table blob of every
-shape for P = 1..8; each entry is recomputed here from the oracle's points and
+shape for P = 1..9; each entry is recomputed here from the oracle's points and
 weights (``oracle.ref_points``, collapse factors included), its Jacobi
 polynomials (``oracle.jacobi``) and its collocation matrices
 (``oracle.colloc_1d``), following the basis reading of the modified C0
@@ -84,7 +84,7 @@ def cls_table(z, N):
 
 @pytest.mark.parametrize("shape", list(SHAPES))
 def test_host_tables_match_oracle(dump, shape):
-    for P in range(1, 9):
+    for P in range(1, 10):
         N, Q = P + 1, P + 2
         L, blob = dump(shape, P)
         zs, w = direction_points(shape, Q)

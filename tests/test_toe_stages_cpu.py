@@ -3,7 +3,7 @@ for the host, against the oracle (no GPU involved).
 
 The per-element Helmholtz function of that kernel is built as plain C++ with
 AddressSanitizer (``tests/host/toe_stages.cpp``) and run on one affine element
-x = A xi + c of every shape (A a fixed sheared, scaled matrix) for P = 1..8.
+x = A xi + c of every shape (A a fixed sheared, scaled matrix) for P = 1..9.
 Its metric input is written out here from the mathematics of the collapsed
 coordinates: with the point weights w (collapse factors included),
 J = d eta / d xi and K = J A^-1 = d eta / d x, G = w |det A| K K^T and
@@ -77,7 +77,7 @@ def metric(shape, Q):
 
 @pytest.mark.parametrize("shape", list(SHAPES))
 def test_toe_stage_code_matches_oracle(harness, shape):
-    for P in range(1, 9):
+    for P in range(1, 10):
         Q, lam = P + 2, 1.3
         u = np.random.default_rng(P).uniform(-1, 1, orc.num_modes(shape, P))
         G = metric(shape, Q)
