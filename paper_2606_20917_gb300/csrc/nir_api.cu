@@ -95,16 +95,23 @@ int nir_block_ensure_prec(nir_block *b, int prec)
     const size_t ng = (size_t)(b->geo_pp ? b->epad * b->NQ : b->epad) * b->ng;
     const size_t nl = (size_t)(b->geo_pp ? b->epad * b->NQ : b->epad) * b->nl;
     cudaStream_t st = b->ctx->stream;
+    // per-point metric copies take the packed layout (geo_packed_index);
+    // per-element metrics and the PhysDeriv factors convert in place
+    const long long pblocks = b->geo_pp ? (long long)(b->epad / 32) * b->NQ : 0;
+    auto metric = [&](float *d32, void *d16) {
+        return b->geo_pp ? nir_pack_metric_launch(b->G64, d32, d16, pblocks, b->ng, st)
+                         : nir_convert_launch(b->G64, d32, d16, (long long)ng, st);
+    };
     if (prec == NIR_F32 && !b->G32) {
         if (cudaMalloc(&b->G32, ng * 4) != cudaSuccess || cudaMalloc(&b->L32, nl * 4) != cudaSuccess)
             return NIR_ERR_NO_MEMORY;
-        if (nir_convert_launch(b->G64, b->G32, nullptr, (long long)ng, st)) return NIR_ERR_CUDA;
+        if (metric(b->G32, nullptr)) return NIR_ERR_CUDA;
         if (nir_convert_launch(b->L64, b->L32, nullptr, (long long)nl, st)) return NIR_ERR_CUDA;
     }
     if (prec == NIR_BF16 && !b->G16) {
         if (cudaMalloc(&b->G16, ng * 2) != cudaSuccess || cudaMalloc(&b->L16, nl * 2) != cudaSuccess)
             return NIR_ERR_NO_MEMORY;
-        if (nir_convert_launch(b->G64, nullptr, b->G16, (long long)ng, st)) return NIR_ERR_CUDA;
+        if (metric(nullptr, b->G16)) return NIR_ERR_CUDA;
         if (nir_convert_launch(b->L64, nullptr, b->L16, (long long)nl, st)) return NIR_ERR_CUDA;
     }
     return NIR_OK;

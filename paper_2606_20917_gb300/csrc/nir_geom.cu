@@ -229,6 +229,21 @@ __global__ void k_geometry_from_factors(GeoArgs a)
     }
 }
 
+// FP64 interleaved per-point metric -> FP32/BF16 packed layout (the point
+// blocks of 32 x ng values keep their place; values move within a block).
+template <class T>
+__global__ void k_pack_metric(const double *src, T *dst, long long nblocks, int ng)
+{
+    const long long n = nblocks * ng * 32;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long blk = i / (ng * 32);
+        const int r = (int)(i - blk * ng * 32), c = r >> 5, l = r & 31;
+        const long long o = blk * ng * 32 + geo_packed_off(c, l, ng);
+        if constexpr (sizeof(T) == 4) dst[o] = __double2float_rn(src[i]);
+        else dst[o] = __double2bfloat16(src[i]);
+    }
+}
+
 __global__ void k_to_f32(const double *src, float *dst, long long n)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -315,6 +330,17 @@ int nir_convert_launch(const double *src, float *d32, void *d16, long long n, cu
     if (blocks > 65535LL * 8) blocks = 65535LL * 8;
     if (d32) nirk::k_to_f32<<<(unsigned)blocks, 256, 0, st>>>(src, d32, n);
     if (d16) nirk::k_to_bf16<<<(unsigned)blocks, 256, 0, st>>>(src, reinterpret_cast<__nv_bfloat16 *>(d16), n);
+    return cudaPeekAtLastError() == cudaSuccess ? NIR_OK : (cudaGetLastError(), NIR_ERR_CUDA);
+}
+
+int nir_pack_metric_launch(const double *src, float *d32, void *d16, long long nblocks, int ng, cudaStream_t st)
+{
+    long long blocks = (nblocks * ng * 32 + 255) / 256;
+    if (blocks > 65535LL * 8) blocks = 65535LL * 8;
+    if (d32) nirk::k_pack_metric<float><<<(unsigned)blocks, 256, 0, st>>>(src, d32, nblocks, ng);
+    if (d16)
+        nirk::k_pack_metric<__nv_bfloat16>
+            <<<(unsigned)blocks, 256, 0, st>>>(src, reinterpret_cast<__nv_bfloat16 *>(d16), nblocks, ng);
     return cudaPeekAtLastError() == cudaSuccess ? NIR_OK : (cudaGetLastError(), NIR_ERR_CUDA);
 }
 

@@ -160,6 +160,10 @@ struct NoX {
 struct NoTX {
     __device__ int operator()(int, int) const { return 0; }
 };
+// A hook with nothing to do (run_group's after-metric callback).
+struct NoHook {
+    __device__ void operator()() const {}
+};
 
 template <class A, int NIN, int NOUT, int EPB, int NT, bool ROLL = false, class LD, class TB, class ST>
 __device__ __forceinline__ void pencils0(int per_e, int &rot, LD ld, TB tb, ST st)
@@ -571,19 +575,75 @@ struct Modal {
 // Per-element arrays are [E][NG] and exclude the reference weight, which is
 // multiplied in here for the W component.
 // ---------------------------------------------------------------------------
-template <class T, class A, int NQ, int NG>
+// PACK: the FP32/BF16 metric copies (NG = ngeo) use the packed per-point
+// layout of geo_packed_index (one element's quad, pair and W adjacent);
+// FP64 arrays and the PhysDeriv factors keep the interleaved one.
+template <class T, class A, int NQ, int NG, bool PACK = false>
 struct Geo {
     const T *g;
     const A *wq;
     int pp;
     __device__ __forceinline__ A get(long long e, int n, int c) const
     {
-        if (pp) return to_a(g[((((e >> 5) * NQ + n) * NG + c) << 5) + (e & 31)], A());
+        if (pp) {
+            if constexpr (PACK) return to_a(g[geo_packed_index(e, n, c, NQ, NG)], A());
+            else return to_a(g[((((e >> 5) * NQ + n) * NG + c) << 5) + (e & 31)], A());
+        }
         A v = to_a(g[e * NG + c], A());
         return (c == NG - 1) ? v * wq[n] : v;
     }
+    // All NG values of point n of element e (per-element factors: W scaled by
+    // the reference weight).  Packed per-point arrays take one 16-byte (BF16:
+    // 8-byte) quad, one pair and one scalar load.
+    __device__ __forceinline__ void get_all(long long e, int n, A (&v)[NG]) const
+    {
+        if constexpr (PACK) {
+            if (pp) {
+                const long long blk = (((e >> 5) * NQ + n) * NG) << 5;
+                const int l = (int)(e & 31);
+                load4(g + blk + l * 4, v);
+                if constexpr (NG == 7) {
+                    load2(g + blk + 128 + l * 2, v[4], v[5]);
+                    v[6] = to_a(g[blk + 192 + l], A());
+                }
+                return;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NG; ++c) v[c] = get(e, n, c);
+    }
     // scale of the metric (non-W) components: 1 per point, wq[n] per element
     __device__ __forceinline__ A gscale(int n) const { return pp ? A(1) : wq[n]; }
+
+  private:
+    template <int K>
+    static __device__ __forceinline__ void load4(const float *p, A (&v)[K])
+    {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    template <int K>
+    static __device__ __forceinline__ void load4(const __nv_bfloat16 *p, A (&v)[K])
+    {
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void load2(const float *p, A &x, A &y)
+    {
+        const float2 q = __ldg(reinterpret_cast<const float2 *>(p));
+        x = q.x; y = q.y;
+    }
+    static __device__ __forceinline__ void load2(const __nv_bfloat16 *p, A &x, A &y)
+    {
+        const unsigned q = __ldg(reinterpret_cast<const unsigned *>(p));
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q));
+        x = a.x; y = a.y;
+    }
+    template <int K>
+    static __device__ __forceinline__ void load4(const double *, A (&)[K]) {}
+    static __device__ __forceinline__ void load2(const double *, A &, A &) {}
 };
 
 // Default elements per CTA: fill about 110 KB (FP64) or 56 KB (FP32/BF16) of
@@ -842,18 +902,17 @@ struct HelmStages {
                     d1 *= sc;
                     d2 *= sc;
                 }
+                A g[NG];
+                geo.get_all(eg, n, g);
                 if constexpr (D == 3) {
-                    const A g00 = geo.get(eg, n, 0), g01 = geo.get(eg, n, 1), g02 = geo.get(eg, n, 2);
-                    const A g11 = geo.get(eg, n, 3), g12 = geo.get(eg, n, 4), g22 = geo.get(eg, n, 5);
-                    V1[e * S + n] = fmaa(g00, d0, fmaa(g01, d1, g02 * d2));
-                    V2[e * S + n] = fmaa(g01, d0, fmaa(g11, d1, g12 * d2));
-                    vl[k] = fmaa(g02, d0, fmaa(g12, d1, g22 * d2));
+                    V1[e * S + n] = fmaa(g[0], d0, fmaa(g[1], d1, g[2] * d2));
+                    V2[e * S + n] = fmaa(g[1], d0, fmaa(g[3], d1, g[4] * d2));
+                    vl[k] = fmaa(g[2], d0, fmaa(g[4], d1, g[5] * d2));
                 } else {
-                    const A g00 = geo.get(eg, n, 0), g01 = geo.get(eg, n, 1), g11 = geo.get(eg, n, 2);
-                    V1[e * S + n] = fmaa(g00, d0, g01 * d1);
-                    vl[k] = fmaa(g01, d0, g11 * d1);
+                    V1[e * S + n] = fmaa(g[0], d0, g[1] * d1);
+                    vl[k] = fmaa(g[1], d0, g[2] * d1);
                 }
-                m[k] = lam * geo.get(eg, n, NG - 1) * U[e * S + n];
+                m[k] = lam * g[NG - 1] * U[e * S + n];
             }
 #pragma unroll
             for (int o = 0; o < Q; ++o) {
@@ -1053,10 +1112,13 @@ __device__ __noinline__ void nodal_pairs(A *buf, bool to_pairs)  // out of line:
 // IProductWRTDerivBase, reference weights).
 // fin/fout: the group's first input and output arrays (a field of a
 // multi-field Helmholtz call; a.in0 / a.out0 otherwise).
-template <int SH, int N, int Q, class T, int OP, int EPB_, int NT_, class TP>
+// after_metric: called by every thread once the fused FP32/BF16 Helmholtz
+// has consumed the group's geometric factors (the staged kernel starts the
+// next group's L2 prefetch there).
+template <int SH, int N, int Q, class T, int OP, int EPB_, int NT_, class TP, class HOOK = NoHook>
 __device__ __forceinline__ void run_group(const KArgs &a, const void *fin, void *fout, TP tp,
                                           const typename CT<T>::type *tab, typename CT<T>::type *buf, long long e0,
-                                          int ne, bool staged = false)
+                                          int ne, bool staged = false, HOOK after_metric = HOOK{})
 {
     using C = Config<SH, N, Q, T, OP, EPB_, NT_>;
     using A = typename C::A;
@@ -1067,7 +1129,9 @@ __device__ __forceinline__ void run_group(const KArgs &a, const void *fin, void 
     using HS = HelmStages<SH, N, Q, A, EPB, NT, S>;
     A *B0 = buf, *B1 = buf + EPB * S, *B2 = buf + 2 * EPB * S, *B3 = buf + 3 * EPB * S;
     const A *D0 = tab + L.D1, *D1 = tab + L.D2, *D2 = tab + L.D3;
-    const Geo<T, A, NQ, NG> geo{reinterpret_cast<const T *>(a.geo), tab + L.wq, a.geo_pp};
+    // the FP32/BF16 metric copies are packed (the PhysDeriv factors are not)
+    constexpr bool PACK = sizeof(T) < 8 && NG == ngeo(SH);
+    const Geo<T, A, NQ, NG, PACK> geo{reinterpret_cast<const T *>(a.geo), tab + L.wq, a.geo_pp};
 
     constexpr bool TENSOR = SH == QUAD || SH == HEX;
     auto to_pairs = [&](A *blk) {
@@ -1219,6 +1283,7 @@ __device__ __forceinline__ void run_group(const KArgs &a, const void *fin, void 
             HS::grad_rest(tp, B0, B2);
             if (a.geo_pp) HS::template metric_tlast<true>(tp, geo, e0, lam, B0, B1, B2);
             else HS::template metric_tlast<false>(tp, geo, e0, lam, B0, B1, B2);
+            after_metric();
             HS::t1_first(tp, B0, B1, B2);
             MD::back(tp, B2, nullptr, B0);
         } else {
@@ -1228,6 +1293,7 @@ __device__ __forceinline__ void run_group(const KArgs &a, const void *fin, void 
             HS::grad_rest(tp, B0, B1);
             if (a.geo_pp) HS::template metric_tlast<true>(tp, geo, e0, lam, B0, B2, B1);
             else HS::template metric_tlast<false>(tp, geo, e0, lam, B0, B2, B1);
+            after_metric();
             HS::tmid(tp, B0, B1);
             HS::t1_first(tp, B0, B2, B1);
             MD::back(tp, B1, B2, B0);
@@ -1295,17 +1361,39 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 // by a bulk copy while the current group computes (a group's inputs are
 // [EPB][M] contiguous values).  With a.pf = 1 the group's per-point metric
 // (for EPB a multiple of 32: whole 32-element chunks of the interleaved
-// layout) is bulk-prefetched into L2 when the group starts, so the metric
-// stage finds it there; the autotuner decides whether that pays.  Groups whose
-// copy would not be 16-byte aligned, and the ragged last group, are loaded
-// with plain coalesced loads.
+// layout) is bulk-prefetched into L2 one group ahead (the first group's at
+// the start, each next group's once the current group's metric stage is
+// done), so the metric stage finds it there; the autotuner decides whether
+// that pays.  Groups whose copy would not be 16-byte aligned, and the ragged
+// last group, are loaded with plain coalesced loads.
 // STAGE = false: no staging buffer (coefficients loaded by the group itself),
 // for groups whose buffers alone nearly fill shared memory.
 // MULTI: the multi-field form (1..3 fields per group, a.nfields); the
 // single-field form is a separate instantiation so its code and register
 // allocation do not carry the field loop.
+// CTAs of `threads` threads and `smem` bytes of shared memory that fit on one
+// SM (228 KB, 1 KB reserved per CTA; 2048 threads), at least 1.  Used as the
+// launch bound's minimum blocks per SM: the register budget ptxas may use is
+// then what that occupancy leaves, so a kernel whose shared memory already
+// limits it to one CTA per SM is not squeezed into 64 registers (and spills).
+constexpr int ctas_per_sm(int smem, int threads)
+{
+    const int by_smem = (228 * 1024) / (smem + 1024);
+    const int by_thr = 2048 / threads;
+    const int c = by_smem < by_thr ? by_smem : by_thr;
+    return c < 1 ? 1 : c;
+}
+template <int SH, int N, int Q, class T, int EPB_, bool STAGE>
+constexpr int helm_tma_smem()
+{
+    using C = Config<SH, N, Q, T, OP_HELM, EPB_>;
+    return C::SMEM + (STAGE ? ((C::EPB * C::M * (int)sizeof(T) + 15) / 16) * 16 : 0);
+}
+
 template <int SH, int N, int Q, class T, int EPB_ = 0, bool STAGE = true, bool MULTI = false>
-__global__ void __launch_bounds__(Config<SH, N, Q, T, OP_HELM, EPB_>::NT)
+__global__ void __launch_bounds__(Config<SH, N, Q, T, OP_HELM, EPB_>::NT,
+                                  ctas_per_sm(helm_tma_smem<SH, N, Q, T, EPB_, STAGE>(),
+                                              Config<SH, N, Q, T, OP_HELM, EPB_>::NT))
     k_helm_tma(KArgs a, const __grid_constant__ TabP<typename CT<T>::type, layout(SH, N, Q).total> tp)
 {
     using C = Config<SH, N, Q, T, OP_HELM, EPB_>;
@@ -1356,14 +1444,24 @@ __global__ void __launch_bounds__(Config<SH, N, Q, T, OP_HELM, EPB_>::NT)
     };
     (void)in;
     unsigned phase = 0;
-    if (threadIdx.x == 0) s_next = issue(blockIdx.x, 0);
+    if (threadIdx.x == 0) {
+        s_next = issue(blockIdx.x, 0);
+        if (blockIdx.x < ngroups) prefetch_metric((long long)blockIdx.x * EPB);  // the first group's factors
+    }
     __syncthreads();
     for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
         const long long e0 = g * EPB;
         const int ne = (int)((a.nelem - e0) < EPB ? (a.nelem - e0) : EPB);
+        // once this group's factors are consumed, start bringing the next
+        // group's into L2: they then have the rest of this group and the next
+        // group's first stages to arrive, and about one group of factors per
+        // CTA is resident in L2 at a time
+        const long long gn = g + gridDim.x;
+        auto prefetch_next = [&]() {
+            if (threadIdx.x == 0 && gn < ngroups) prefetch_metric(gn * EPB);
+        };
         for (int f = 0; f < nf; ++f) {
             const bool staged = s_next != 0;
-            if (threadIdx.x == 0 && f == 0) prefetch_metric(e0);
             if (staged) {
                 if (!mbar_wait(&bar, phase, a.err)) s_fail = 1;
                 phase ^= 1u;
@@ -1379,7 +1477,9 @@ __global__ void __launch_bounds__(Config<SH, N, Q, T, OP_HELM, EPB_>::NT)
             if (threadIdx.x == 0)  // stage is free again: the next field, or the next group's first
                 s_next = f + 1 < nf ? issue(g, f + 1) : issue(g + gridDim.x, 0);
             run_group<SH, N, Q, T, OP_HELM, EPB_, 0>(a, field_in(a, f), field_out(a, f), ptab, tab, buf, e0, ne,
-                                                     staged);
+                                                     staged, [&]() {
+                                                         if (f == 0) prefetch_next();
+                                                     });
         }
     }
 }

@@ -33,6 +33,22 @@ NIR_HD constexpr int ngeo(int s) { return dim(s) == 2 ? 4 : 7; }
 // Number of PhysDeriv factors per point: d eta_j / d x_l (row j) plus W.
 NIR_HD constexpr int nlam(int s) { return dim(s) == 2 ? 5 : 10; }
 
+// Per-point metric (ng = ngeo values) of the FP32/BF16 copies, packed so that
+// one element's values are adjacent: per chunk of 32 elements and per point,
+// the 32 elements' quads (G00 G01 G02 G11) -- 2-D: (G00 G01 G11 W) -- then
+// their pairs (G12 G22), then their W.  A thread reads its point's values
+// with three vector loads instead of seven scalar ones; the block of a point
+// is the same 32 x ng values as in the interleaved FP64 layout (value c of
+// element lane l at c * 32 + l), so chunks stay contiguous.
+NIR_HD constexpr long long geo_packed_off(int c, int l, int ng)
+{
+    return (ng == 4 || c < 4) ? l * 4 + c : c < 6 ? 128 + l * 2 + (c - 4) : 192 + l;
+}
+NIR_HD constexpr long long geo_packed_index(long long e, int n, int c, int nq, int ng)
+{
+    return ((((e >> 5) * nq + n) * ng) << 5) + geo_packed_off(c, (int)(e & 31), ng);
+}
+
 // Ragged class tables: class c holds Q x (N - c) values.
 NIR_HD constexpr int cls_cols(int N, int c) { return N - c; }
 NIR_HD constexpr int cls_off(int N, int Q, int c)

@@ -335,7 +335,10 @@ __device__ __forceinline__ void helm_element(const A *tab, const Scr<A, nirk::np
     // (the arithmetic, operation for operation, of the default FP64 kernel, so
     // both strategies give the same bits there)
     auto G = [&](int n, int c) -> A {
-        if (geo_pp) return to_c(geo[((((e >> 5) * NQ + n) * NG + c) << 5) + (e & 31)]);
+        if (geo_pp) {  // FP32/BF16 copies use the packed per-point layout
+            if constexpr (sizeof(T) < 8) return to_c(geo[nirk::geo_packed_index(e, n, c, NQ, NG)]);
+            else return to_c(geo[((((e >> 5) * NQ + n) * NG + c) << 5) + (e & 31)]);
+        }
         const A v = to_c(geo[e * NG + c]);
         return c == NG - 1 ? v * wq[n] : v;  // per element: W takes the reference weight
     };
