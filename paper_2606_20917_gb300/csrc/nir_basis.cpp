@@ -3,9 +3,11 @@
 // interpolation tables used by the device kernels.
 //
 // Quadrature (Sec. 2.2: points avoiding the collapsed endpoints):
-//   * Gauss-Jacobi(alpha, beta) nodes and weights by the Golub-Welsch method:
-//     eigenvalues of the symmetric tridiagonal Jacobi matrix of the weight
-//     (1-x)^alpha (1+x)^beta, weights from the first eigenvector components.
+//   * Gauss-Jacobi(alpha, beta) nodes and weights by the Golub-Welsch
+//     characterisation: the nodes are the eigenvalues of the symmetric
+//     tridiagonal Jacobi matrix of the weight (1-x)^alpha (1+x)^beta (found
+//     here by Sturm-sequence bisection), the weights the Christoffel numbers
+//     mu0 / sum_k p_k(x)^2 of the orthonormal polynomials.
 //   * Gauss-Lobatto-Legendre: +-1 plus the Gauss-Jacobi(1,1) nodes, weights
 //     2 / (Q (Q-1) P_{Q-1}(x)^2).
 // Directions: quad/hex GLL; tri eta1 GJ(0,0), eta2 GJ(1,0); tet eta1 GJ(0,0),
@@ -29,58 +31,43 @@
 
 namespace {
 
-// Symmetric tridiagonal eigenproblem by implicit QL with Wilkinson shifts,
-// tracking only the first row of the eigenvector matrix.
-// d: diagonal (in: matrix, out: eigenvalues), e: off-diagonal e[i] couples
-// i and i+1 (destroyed), z: out first components of the eigenvectors.
-bool tridiag_ql(int n, double *d, double *e, double *z)
+// Eigenvalues of the symmetric tridiagonal matrix T (diagonal d[0..n-1],
+// off-diagonal e[0..n-2], all e != 0) by bisection on Sturm counts: the
+// number of negative pivots of the LDL^T factorisation of T - x I is the
+// number of eigenvalues below x (Sylvester's law of inertia).  Each
+// eigenvalue is isolated in a Gershgorin interval and halved until the
+// interval stops shrinking in floating point.
+int sturm_count(int n, const double *d, const double *e, double x)
 {
-    for (int i = 0; i < n; ++i) z[i] = (i == 0) ? 1.0 : 0.0;
-    if (n > 0) e[n - 1] = 0.0;
-    for (int l = 0; l < n; ++l) {
-        int iter = 0, m;
-        do {
-            for (m = l; m < n - 1; ++m) {
-                double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
-                if (std::fabs(e[m]) <= 1e-17 * dd) break;
-            }
-            if (m != l) {
-                if (++iter > 60) return false;
-                double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-                double r = std::hypot(g, 1.0);
-                g = d[m] - d[l] + e[l] / (g + std::copysign(r, g));
-                double s = 1.0, c = 1.0, p = 0.0;
-                int i;
-                bool underflow = false;
-                for (i = m - 1; i >= l; --i) {
-                    double f = s * e[i], b = c * e[i];
-                    r = std::hypot(f, g);
-                    e[i + 1] = r;
-                    if (r == 0.0) {
-                        d[i + 1] -= p;
-                        e[m] = 0.0;
-                        underflow = true;
-                        break;
-                    }
-                    s = f / r;
-                    c = g / r;
-                    g = d[i + 1] - p;
-                    r = (d[i] - g) * s + 2.0 * c * b;
-                    p = s * r;
-                    d[i + 1] = g + p;
-                    g = c * r - b;
-                    double zf = z[i + 1];
-                    z[i + 1] = s * z[i] + c * zf;
-                    z[i] = c * z[i] - s * zf;
-                }
-                if (underflow) continue;
-                d[l] -= p;
-                e[l] = g;
-                e[m] = 0.0;
-            }
-        } while (m != l);
+    int neg = 0;
+    double q = d[0] - x;
+    for (int k = 0;; ++k) {
+        if (q == 0.0) q = -1e-300;  // perturb an exact zero pivot (x is then an eigenvalue)
+        if (q < 0.0) ++neg;
+        if (k + 1 == n) break;
+        q = (d[k + 1] - x) - e[k] * e[k] / q;
     }
-    return true;
+    return neg;
+}
+
+void tridiag_eigenvalues(int n, const double *d, const double *e, double *lam)
+{
+    double lo = d[0], hi = d[0];
+    for (int k = 0; k < n; ++k) {
+        const double r = (k > 0 ? std::fabs(e[k - 1]) : 0.0) + (k + 1 < n ? std::fabs(e[k]) : 0.0);
+        lo = std::min(lo, d[k] - r);
+        hi = std::max(hi, d[k] + r);
+    }
+    for (int j = 0; j < n; ++j) {  // the (j+1)-th smallest eigenvalue
+        double a = lo, b = hi;
+        for (int it = 0; it < 200; ++it) {
+            const double m = 0.5 * (a + b);
+            if (m <= a || m >= b) break;
+            if (sturm_count(n, d, e, m) > j) b = m;
+            else a = m;
+        }
+        lam[j] = 0.5 * (a + b);
+    }
 }
 
 }  // namespace
@@ -110,7 +97,7 @@ double nirb_jacobi_d(int n, double a, double b, double x)
 
 bool nirb_gauss_jacobi(int Q, double a, double b, double *z, double *w)
 {
-    std::vector<double> d(Q), e(Q), v(Q);
+    std::vector<double> d(Q), e(Q);
     for (int k = 0; k < Q; ++k) {
         double t = 2.0 * k + a + b;
         d[k] = (t == 0.0) ? (b - a) / (a + b + 2.0) : (b * b - a * a) / (t * (t + 2.0));
@@ -119,15 +106,27 @@ bool nirb_gauss_jacobi(int Q, double a, double b, double *z, double *w)
             e[k] = std::sqrt(4.0 * n * (n + a) * (n + b) * (n + a + b) / (s * s * (s + 1.0) * (s - 1.0)));
         }
     }
-    if (!tridiag_ql(Q, d.data(), e.data(), v.data())) return false;
-    double mu0 = std::exp((a + b + 1.0) * std::log(2.0) + std::lgamma(a + 1.0) + std::lgamma(b + 1.0)
-                          - std::lgamma(a + b + 2.0));
-    std::vector<int> idx(Q);
-    for (int k = 0; k < Q; ++k) idx[k] = k;
-    std::sort(idx.begin(), idx.end(), [&](int i, int j) { return d[i] < d[j]; });
-    for (int k = 0; k < Q; ++k) {
-        z[k] = d[idx[k]];
-        w[k] = mu0 * v[idx[k]] * v[idx[k]];
+    // nodes: the eigenvalues of the Jacobi matrix (ascending)
+    tridiag_eigenvalues(Q, d.data(), e.data(), z);
+    // weights (Christoffel numbers): with p_0 .. p_{Q-1} the polynomials
+    // orthonormal for the weight, w(x) = mu0 / sum_k p_k(x)^2, where mu0 is the
+    // weight's total mass; the p_k follow the Jacobi matrix's recurrence
+    // e_k p_{k+1} = (x - d_k) p_k - e_{k-1} p_{k-1}, p_0 = 1.  (The squared
+    // first component of the normalised eigenvector, Golub-Welsch's formula,
+    // is the same number: the eigenvector of eigenvalue x is (p_k(x))_k.)
+    const double mu0 = std::exp((a + b + 1.0) * std::log(2.0) + std::lgamma(a + 1.0) + std::lgamma(b + 1.0)
+                                - std::lgamma(a + b + 2.0));
+    for (int i = 0; i < Q; ++i) {
+        const double x = z[i];
+        double pm = 0.0, pc = 1.0, sum = 1.0;
+        for (int k = 0; k + 1 < Q; ++k) {
+            const double pn = ((x - d[k]) * pc - (k > 0 ? e[k - 1] * pm : 0.0)) / e[k];
+            pm = pc;
+            pc = pn;
+            sum += pc * pc;
+        }
+        if (!(sum > 0.0) || !std::isfinite(sum)) return false;
+        w[i] = mu0 / sum;
     }
     return true;
 }
