@@ -6,7 +6,7 @@ lives in ``oracle.c`` (plain C, dense elemental matrices built from the basis
 definitions); this module compiles it with gcc on first use and wraps it with
 numpy arrays.
 
-Shapes are named "quad", "tri", "hex", "prism", "tet".  Layouts: coefficients
+Shapes are named "quad", "tri", "hex", "prism", "tet", "pyr".  Layouts: coefficients
 [E][M] (modes packed p outermost), physical values [E][Nq] with point index
 i + Q*(j + Q*k) (first direction fastest), derivative fields [d][E][Nq].
 """
@@ -22,8 +22,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
-_SHAPE = {"quad": 0, "tri": 1, "hex": 2, "prism": 3, "tet": 4}
-_DIM = {"quad": 2, "tri": 2, "hex": 3, "prism": 3, "tet": 3}
+_SHAPE = {"quad": 0, "tri": 1, "hex": 2, "prism": 3, "tet": 4, "pyr": 5}
+_DIM = {"quad": 2, "tri": 2, "hex": 3, "prism": 3, "tet": 3, "pyr": 3}
 _lock = threading.Lock()
 _lib = None
 

@@ -1,7 +1,8 @@
 /*
  * oracle.c -- plain, slow, FP64 CPU reference for the spectral/hp elemental
  * operators (BwdTrans, IProductWRTBase, PhysDeriv, IProductWRTDerivBase, mass,
- * Helmholtz) on quadrilaterals, triangles, hexahedra, prisms and tetrahedra.
+ * Helmholtz) on quadrilaterals, triangles, hexahedra, prisms, tetrahedra and
+ * pyramids.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, imports or
  * calls this file; only the tests, the smoke check and the benchmark's CPU
@@ -30,6 +31,14 @@
  *     polynomial in xi are defined with that factor replaced by 1.
  *   - quadrature: GLL on tensor directions, Gauss-Jacobi(alpha,0) on collapsed
  *     directions with the collapse Jacobian absorbed in the weights.
+ *   - pyramid (a shape the paper motivates and leaves to future work): apex at
+ *     xi = (-1,-1,1), eta1 = 2(1+xi1)/(1-xi3) - 1, eta2 = 2(1+xi2)/(1-xi3) - 1,
+ *     eta3 = xi3; modes p, q < N, r < N - max(p,q), phi_pqr =
+ *     psiA_p(eta1) psiA_q(eta2) psiB_(max(p,q)) r(eta3), the apex mode (0,0,1)
+ *     being psiA_1(eta3) alone; GLL in eta1, eta2 and Gauss-Jacobi(2,0) in
+ *     eta3 with the collapse Jacobian ((1-eta3)/2)^2 in the weights; the
+ *     element map is the vertex map of the five vertex functions (rational in
+ *     xi; affine for a parallelogram base).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -38,7 +47,7 @@
 #include <omp.h>
 #endif
 
-enum { ORC_QUAD = 0, ORC_TRI = 1, ORC_HEX = 2, ORC_PRISM = 3, ORC_TET = 4 };
+enum { ORC_QUAD = 0, ORC_TRI = 1, ORC_HEX = 2, ORC_PRISM = 3, ORC_TET = 4, ORC_PYR = 5 };
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2, ORC_ESING = -3 };
 
 #define ORC_MAXQ 16
@@ -46,7 +55,7 @@ enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2, ORC_ESING = -3 };
 
 static int orc_dim(int shape) { return (shape == ORC_QUAD || shape == ORC_TRI) ? 2 : 3; }
 
-static int shape_ok(int shape) { return shape >= ORC_QUAD && shape <= ORC_TET; }
+static int shape_ok(int shape) { return shape >= ORC_QUAD && shape <= ORC_PYR; }
 
 int orc_num_modes(int shape, int P)
 {
@@ -57,6 +66,7 @@ int orc_num_modes(int shape, int P)
     case ORC_TRI: return N * (N + 1) / 2;
     case ORC_HEX: return N * N * N;
     case ORC_PRISM: return N * N * (N + 1) / 2;
+    case ORC_PYR: return N * (N + 1) * (2 * N + 1) / 6;   /* sum over c = max(p,q) of (2c+1)(N-c) */
     default: return N * (N + 1) * (N + 2) / 6;
     }
 }
@@ -168,6 +178,7 @@ static void shape_rules(int shape, int Q, double z[3][ORC_MAXQ], double w[3][ORC
     case ORC_PRISM: kinds[2] = 2; scale[2] = 0.5; break;                      /* (1-eta3)/2 */
     case ORC_TET: kinds[0] = 1; kinds[1] = 2; kinds[2] = 3;                   /* (1-eta2)/2 ((1-eta3)/2)^2 */
         scale[1] = 0.5; scale[2] = 0.25; break;
+    case ORC_PYR: kinds[2] = 3; scale[2] = 0.25; break;                       /* ((1-eta3)/2)^2 */
     default: break;
     }
     for (int d = 0; d < 3; ++d) {
@@ -194,6 +205,11 @@ static void eta_to_xi(int shape, const double *e, double *x)
         x[1] = 0.5 * (1.0 + e[1]) * (1.0 - e[2]) - 1.0;
         x[2] = e[2];
         break;
+    case ORC_PYR:
+        x[0] = 0.5 * (1.0 + e[0]) * (1.0 - e[2]) - 1.0;
+        x[1] = 0.5 * (1.0 + e[1]) * (1.0 - e[2]) - 1.0;
+        x[2] = e[2];
+        break;
     default:
         for (int i = 0; i < orc_dim(shape); ++i) x[i] = e[i];
     }
@@ -214,6 +230,11 @@ static void xi_to_eta(int shape, const double *x, double *e)
         break;
     case ORC_TET:
         e[0] = 2.0 * (1.0 + x[0]) / (-x[1] - x[2]) - 1.0;
+        e[1] = 2.0 * (1.0 + x[1]) / (1.0 - x[2]) - 1.0;
+        e[2] = x[2];
+        break;
+    case ORC_PYR:
+        e[0] = 2.0 * (1.0 + x[0]) / (1.0 - x[2]) - 1.0;
         e[1] = 2.0 * (1.0 + x[1]) / (1.0 - x[2]) - 1.0;
         e[2] = x[2];
         break;
@@ -245,6 +266,12 @@ static void deta_dxi(int shape, const double *e, double A[3][3])
         A[1][2] = (1.0 + e[1]) / (1.0 - e[2]);
         break;
     }
+    case ORC_PYR:
+        A[0][0] = 2.0 / (1.0 - e[2]);
+        A[0][2] = (1.0 + e[0]) / (1.0 - e[2]);
+        A[1][1] = 2.0 / (1.0 - e[2]);
+        A[1][2] = (1.0 + e[1]) / (1.0 - e[2]);
+        break;
     default: break;
     }
 }
@@ -302,6 +329,10 @@ static int mode_list(int shape, int P, int (*pqr)[3])
         for (int p = 0; p < N; ++p) for (int q = 0; q < N - p; ++q) for (int r = 0; r < N - p - q; ++r) {
             pqr[m][0] = p; pqr[m][1] = q; pqr[m][2] = r; ++m; }
         break;
+    case ORC_PYR:
+        for (int p = 0; p < N; ++p) for (int q = 0; q < N; ++q) for (int r = 0; r < N - (p > q ? p : q); ++r) {
+            pqr[m][0] = p; pqr[m][1] = q; pqr[m][2] = r; ++m; }
+        break;
     }
     return m;
 }
@@ -342,6 +373,15 @@ static void mode_eval_eta(int shape, const int *pqr, const double *e, double *f,
         psiB(p, q, e[1], &b, &db); psiB(p + q, r, e[2], &c, &dc);
         if (p == 0 && q == 1) { a = 1.0; da = 0.0; }          /* collapsed edge */
         else psiA(p, e[0], &a, &da);
+        *f = a * b * c; g[0] = da * b * c; g[1] = a * db * c; g[2] = a * b * dc;
+        break;
+    case ORC_PYR:
+        if (p == 0 && q == 0 && r == 1) {                      /* apex: eta1, eta2 factors dropped */
+            psiA(1, e[2], &c, &dc);
+            *f = c; g[2] = dc;
+            break;
+        }
+        psiA(p, e[0], &a, &da); psiA(q, e[1], &b, &db); psiB(p > q ? p : q, r, e[2], &c, &dc);
         *f = a * b * c; g[0] = da * b * c; g[1] = a * db * c; g[2] = a * b * dc;
         break;
     }
@@ -549,6 +589,27 @@ static void element_jacobian(int shape, int gorder, const double *nodes, const d
         N[1] = 0.5 * (1.0 + xi[0]); G[1][0] = 0.5;
         N[2] = 0.5 * (1.0 + xi[1]); G[2][1] = 0.5;
         N[3] = 0.5 * (1.0 + xi[2]); G[3][2] = 0.5;
+    } else if (shape == ORC_PYR) {
+        /* vertices (-1,-1,-1), (1,-1,-1), (1,1,-1), (-1,1,-1), apex (-1,-1,1):
+         * base functions a_i b_j (1-xi3)/2 with a_0 = (-xi1-xi3)/(1-xi3),
+         * a_1 = (1+xi1)/(1-xi3) (b likewise in xi2), apex (1+xi3)/2; written
+         * as N = u v / (2 s), s = 1 - xi3, and differentiated by the quotient
+         * rule. */
+        nv = 5;
+        double s = 1.0 - xi[2];
+        double u[2] = {-xi[0] - xi[2], 1.0 + xi[0]}, du1[2] = {-1.0, 1.0}, du3[2] = {-1.0, 0.0};
+        double v[2] = {-xi[1] - xi[2], 1.0 + xi[1]}, dv2[2] = {-1.0, 1.0}, dv3[2] = {-1.0, 0.0};
+        int ai[4] = {0, 1, 1, 0}, bj[4] = {0, 0, 1, 1};
+        for (int k = 0; k < 4; ++k) {
+            double uu = u[ai[k]], vv = v[bj[k]];
+            N[k] = uu * vv / (2.0 * s);
+            G[k][0] = du1[ai[k]] * vv / (2.0 * s);
+            G[k][1] = uu * dv2[bj[k]] / (2.0 * s);
+            /* d/dxi3 of uu vv / (2 s) with ds/dxi3 = -1 */
+            G[k][2] = (du3[ai[k]] * vv + uu * dv3[bj[k]]) / (2.0 * s) + uu * vv / (2.0 * s * s);
+        }
+        N[4] = 0.5 * (1.0 + xi[2]);
+        G[4][2] = 0.5;
     } else { /* prism: triangle (xi1, xi3) x segment xi2 */
         nv = 6;
         double T[3] = {-0.5 * (xi[0] + xi[2]), 0.5 * (1.0 + xi[0]), 0.5 * (1.0 + xi[2])};
@@ -602,7 +663,7 @@ static int nodes_per_elem(int shape, int gorder)
         return d == 2 ? (gorder + 1) * (gorder + 1) : (gorder + 1) * (gorder + 1) * (gorder + 1);
     }
     if (gorder != 1) return ORC_EINVAL;
-    return shape == ORC_TRI ? 3 : shape == ORC_TET ? 4 : 6;
+    return shape == ORC_TRI ? 3 : shape == ORC_TET ? 4 : shape == ORC_PYR ? 5 : 6;
 }
 
 /* Per-point W = w |J| and Lambda[n][i][l] = d xi_i / d x_l of one element.

@@ -29,7 +29,7 @@ import numpy as np
 
 SHAPES = ("quad", "tri", "hex", "prism", "tet")
 DIM = {"quad": 2, "tri": 2, "hex": 3, "prism": 3, "tet": 3}
-NVERT = {"tri": 3, "tet": 4, "prism": 6}
+NVERT = {"tri": 3, "tet": 4, "prism": 6, "pyr": 5}
 
 
 def lattice_offsets(g: int, d: int) -> np.ndarray:
@@ -137,6 +137,33 @@ def prism_split(nx: int, ny: int, nz: int) -> np.ndarray:
     ref = np.stack(ref)
     V = org[:, None, None, :] + ref[None] * h
     return V.reshape(-1, 6, 3).astype(np.float64)
+
+
+def pyramid_split(nx: int, ny: int, nz: int) -> np.ndarray:
+    """Each cell of an nx*ny*nz grid split into 6 pyramids, one per face, with
+    their apex at the cell centre (each pyramid over a square: affine).
+
+    Vertices [E][5][3]: the base (V0..V3) counter-clockwise seen from the apex
+    (V4), the reference order, so every element is positively oriented.
+    """
+    org, h = _cube_corners(nx, ny, nz)
+    pyrs = []
+    for axis in range(3):
+        for side in (0.0, 1.0):
+            quad = []
+            for a, b in ((0, 0), (1, 0), (1, 1), (0, 1)):
+                v = [0.0, 0.0, 0.0]
+                v[axis] = side
+                v[(axis + 1) % 3] = a
+                v[(axis + 2) % 3] = b
+                quad.append(v)
+            quad = np.array(quad)
+            apex = np.array([0.5, 0.5, 0.5])
+            if np.linalg.det(np.stack([quad[1] - quad[0], quad[3] - quad[0], apex - quad[0]])) < 0:
+                quad = quad[[0, 3, 2, 1]]
+            pyrs.append(np.vstack([quad, apex]))
+    local = np.stack(pyrs)                                    # [6][5][3] in the unit cube
+    return (org[:, None, None, :] + h * local[None]).reshape(-1, 5, 3)
 
 
 def tri_grid(nx: int, ny: int) -> np.ndarray:
