@@ -42,13 +42,15 @@ def helm_flops_per_elem(shape: str, N: int, Q: int) -> int:
     transpose (2 Q^(d+1) flops per direction each way) and the per-point
     metric (20 flops in 3-D, 10 in 2-D).  Collapsed shapes contract their
     ragged mode ranges in the order of Eq. bwdsumfactet: tet M Q + N(N+1)/2 Q^2
-    + N Q^3, prism M Q + N^2 Q^2 + N Q^3, triangle M Q + N Q^2."""
+    + N Q^3, prism and pyramid M Q + N^2 Q^2 + N Q^3, triangle M Q + N Q^2."""
     if shape == "hex":
         stages = N * N * N * Q + N * N * Q * Q + N * Q ** 3
     elif shape == "tet":
         stages = (N * (N + 1) * (N + 2) // 6) * Q + (N * (N + 1) // 2) * Q * Q + N * Q ** 3
     elif shape == "prism":
         stages = (N * N * (N + 1) // 2) * Q + N * N * Q * Q + N * Q ** 3
+    elif shape == "pyr":
+        stages = (N * (N + 1) * (2 * N + 1) // 6) * Q + N * N * Q * Q + N * Q ** 3
     elif shape == "quad":
         return 4 * (N * N * Q + N * Q * Q) + 8 * Q ** 3 + 10 * Q ** 2
     elif shape == "tri":
@@ -84,7 +86,7 @@ def op_work_per_elem(op: str, N: int, Q: int, wb: int, deformed: bool):
 
 def num_modes(shape: str, N: int) -> int:
     return {"quad": N * N, "tri": N * (N + 1) // 2, "hex": N ** 3, "prism": N * N * (N + 1) // 2,
-            "tet": N * (N + 1) * (N + 2) // 6}[shape]
+            "tet": N * (N + 1) * (N + 2) // 6, "pyr": N * (N + 1) * (2 * N + 1) // 6}[shape]
 
 
 def helm_bytes_per_elem(shape: str, N: int, Q: int, wb: int, deformed: bool) -> int:
@@ -93,7 +95,7 @@ def helm_bytes_per_elem(shape: str, N: int, Q: int, wb: int, deformed: bool) -> 
     element (undeformed quad/hex)."""
     d = 2 if shape in ("quad", "tri") else 3
     ng = 4 if d == 2 else 7
-    per_point = deformed or shape in ("tri", "tet", "prism")
+    per_point = deformed or shape in ("tri", "tet", "prism", "pyr")
     geo = ng * Q ** d if per_point else ng
     return 2 * num_modes(shape, N) * wb + geo * wb
 
@@ -325,7 +327,9 @@ def roofline_entry(prec, flops, nbytes, sec, fp64_peak, peaks):
     return {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk}
 
 
-CONFIG_WORKLOADS = ("quad8x8_p4", "tet20_kuhn_p4", "prism40x40x20_p4")
+# the other configurations, plus the pyramid mesh (the shape the paper leaves
+# to future work; not one of the measured configurations)
+CONFIG_WORKLOADS = ("quad8x8_p4", "tet20_kuhn_p4", "prism40x40x20_p4", "pyr20_split_p4")
 
 
 def config_table(nir, ctx, dev, stream, peaks, fp64_peak, args):
@@ -917,9 +921,10 @@ def run_sweep(args, ws, rank, local):
                 if shape == "hex":
                     n = max(1, int(round(E ** (1.0 / 3.0))))
                     nodes, gorder, deformed = W.hex_grid(n, 2), 2, True
-                else:
+                else:   # 6 tets or 6 pyramids per cell
                     n = max(1, int(round((E / 6.0) ** (1.0 / 3.0))))
-                    nodes, gorder, deformed = W.tet_kuhn(n), 1, False
+                    nodes = W.tet_kuhn(n) if shape == "tet" else W.pyramid_split(n, n, n)
+                    gorder, deformed = 1, False
                 E = nodes.shape[0]
                 blk = nir.Block(ctx, shape, E, P, deformed=deformed)
                 blk.set_geometry(gorder, torch.from_numpy(nodes).to(dev))
@@ -956,7 +961,7 @@ def run_sweep(args, ws, rank, local):
                     return {"frac_hbm": E * helm_bytes_per_elem(shape, N, Q, wb, deformed) / tt / 1e9
                             / peaks["hbm_gbs"]}
                 rec.update(frac(t))
-                if not args.sweep_no_toe:
+                if not args.sweep_no_toe and shape != "pyr":
                     # the other strategy: threading over elements (one thread per element)
                     blk.set_tuning(prec, 4, 0, 0)
                     tt = time_apply()
@@ -1076,7 +1081,7 @@ def main():
     ap.add_argument("--mode", choices=["apply", "solve", "gsolve", "hybrid", "sweep"], default="apply")
     ap.add_argument("--basis", choices=["modified", "nodal"], default="modified",
                     help="apply mode: expansion basis (nodal = GLL-Lagrange, quad/hex)")
-    ap.add_argument("--sweep-shapes", default="hex,tet")
+    ap.add_argument("--sweep-shapes", default="hex,tet", help="sweep: shapes among hex, tet, pyr")
     ap.add_argument("--sweep-dofs", default="1e5,1e6,1e7,3e7")
     ap.add_argument("--sweep-orders", default="1,2,3,4,5,6,7,8,9", help="sweep: polynomial degrees P")
     ap.add_argument("--sweep-no-toe", action="store_true", help="sweep the default strategy only")

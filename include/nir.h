@@ -30,15 +30,22 @@
  *         hex   q, r < N;         M = N^3
  *         prism q < N, r < N-p;   M = N^2(N+1)/2
  *         tet   q < N-p, r < N-p-q; M = N(N+1)(N+2)/6     (Eq. bwdsumfactet bounds)
+ *         pyr   q < N, r < N-max(p,q); M = N(N+1)(2N+1)/6
  *       physical values [E][Nq], Nq = Q^d, point index i + Q*(j + Q*k), the
  *         first direction (xi1 / eta1) fastest.
  *   - Basis: modified C0 expansion (psiA, psiB, psiC of Sec. 2.2); collapsed
  *     vertex/edge modes whose eta factor is not a polynomial in xi are defined
- *     with that factor replaced by 1.
+ *     with that factor replaced by 1.  Pyramid (the shape the paper motivates
+ *     for hybrid meshes and leaves to future work): apex at xi = (-1,-1,1),
+ *     eta1 = 2(1+xi1)/(1-xi3) - 1, eta2 = 2(1+xi2)/(1-xi3) - 1, eta3 = xi3,
+ *     phi_pqr = psiA_p(eta1) psiA_q(eta2) psiB_{max(p,q) r}(eta3), the apex
+ *     mode (0,0,1) being psiA_1(eta3) alone (a rational expansion whose traces
+ *     are Q_P on the square base and P_P on the triangular faces).
  *   - Quadrature: Gauss-Lobatto-Legendre on quad/hex directions and the prism's
  *     eta1, eta2; Gauss-Jacobi(alpha,0) on collapsed directions (tri eta1 a=0,
- *     eta2 a=1; tet eta1 a=0, eta2 a=1, eta3 a=2; prism eta3 a=1), with the
- *     collapse Jacobian absorbed in the weights.
+ *     eta2 a=1; tet eta1 a=0, eta2 a=1, eta3 a=2; prism eta3 a=1; pyramid
+ *     eta1, eta2 GLL, eta3 a=2), with the collapse Jacobian absorbed in the
+ *     weights.
  */
 #ifndef NIR_H
 #define NIR_H
@@ -50,7 +57,7 @@
 extern "C" {
 #endif
 
-typedef enum { NIR_QUAD = 0, NIR_TRI = 1, NIR_HEX = 2, NIR_PRISM = 3, NIR_TET = 4 } nir_shape;
+typedef enum { NIR_QUAD = 0, NIR_TRI = 1, NIR_HEX = 2, NIR_PRISM = 3, NIR_TET = 4, NIR_PYR = 5 } nir_shape;
 
 /* Storage/arithmetic precision of an operator call.  NIR_BF16 stores
  * coefficients, physical values and geometric factors in bfloat16 and computes
@@ -136,9 +143,12 @@ int nir_block_points(const nir_block *blk, double *eta_out, double *xi_out);
  *   quad/hex: [E][(g+1)^d][d] coordinates of an equispaced lattice of degree
  *             g = gorder per direction (node a + (g+1)(b + (g+1) c) at
  *             xi = -1 + 2(a,b,c)/g); the element map is its Lagrange interpolant.
- *   tri/tet/prism: gorder = 1, vertices [E][nv][d] in the order
+ *   tri/tet/prism/pyr: gorder = 1, vertices [E][nv][d] in the order
  *             tri (-1,-1),(1,-1),(-1,1); tet (-1,-1,-1),(1,-1,-1),(-1,1,-1),(-1,-1,1);
- *             prism (-1,-1,-1),(1,-1,-1),(1,1,-1),(-1,1,-1),(-1,-1,1),(-1,1,1).
+ *             prism (-1,-1,-1),(1,-1,-1),(1,1,-1),(-1,1,-1),(-1,-1,1),(-1,1,1);
+ *             pyr (-1,-1,-1),(1,-1,-1),(1,1,-1),(-1,1,-1),(-1,-1,1), mapped by the
+ *             vertex functions a_i(eta1) b_j(eta2) (1-eta3)/2 and (1+eta3)/2
+ *             (affine for a parallelogram base).
  * The library computes, in FP64 on the GPU, per point (or per element for an
  * undeformed quad/hex block) the Jacobian, W = w|J|, d eta/d x and the metric
  * G = W (d eta/d x)(d eta/d x)^T, and derives FP32/BF16 copies on first use.

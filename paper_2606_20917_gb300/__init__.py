@@ -19,8 +19,8 @@ import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnir.so")
-SHAPES = {"quad": 0, "tri": 1, "hex": 2, "prism": 3, "tet": 4}
-DIM = {"quad": 2, "tri": 2, "hex": 3, "prism": 3, "tet": 3}
+SHAPES = {"quad": 0, "tri": 1, "hex": 2, "prism": 3, "tet": 4, "pyr": 5}
+DIM = {"quad": 2, "tri": 2, "hex": 3, "prism": 3, "tet": 3, "pyr": 3}
 PREC = {"f64": 0, "f32": 1, "bf16": 2}
 DTYPE = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
 
@@ -273,7 +273,7 @@ class Block:
         if self.shape in ("quad", "hex"):
             npe = (int(gorder) + 1) ** self.dim
         else:
-            npe = {"tri": 3, "tet": 4, "prism": 6}[self.shape]
+            npe = {"tri": 3, "tet": 4, "prism": 6, "pyr": 5}[self.shape]
         if nodes.numel() != self.nelem * npe * self.dim:
             raise ValueError(f"nodes must be [{self.nelem}][{npe}][{self.dim}]")
         _chk(_lib.nir_block_set_geometry(self.h, int(gorder), _ptr(nodes)), "nir_block_set_geometry")

@@ -33,11 +33,11 @@ def _nvcc() -> str:
 
 def _units():
     units = []
-    for s in range(5):
+    for s in range(6):   # quad, tri, hex, prism, tet, pyramid
         for p in range(3):
             units.append((os.path.join(CSRC, "nir_inst.cu"), f"inst_s{s}_p{p}.o",
                           [f"-DNIR_SHAPE={s}", f"-DNIR_PREC={p}"]))
-    for s in range(5):
+    for s in range(5):   # no threading-over-elements kernel for pyramids
         for p in range(3):
             units.append((os.path.join(CSRC, "nir_toe.cu"), f"toe_s{s}_p{p}.o",
                           [f"-DNIR_SHAPE={s}", f"-DNIR_PREC={p}"]))

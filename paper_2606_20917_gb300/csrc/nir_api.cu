@@ -23,16 +23,17 @@ NIR_DECL(1, 0) NIR_DECL(1, 1) NIR_DECL(1, 2)
 NIR_DECL(2, 0) NIR_DECL(2, 1) NIR_DECL(2, 2)
 NIR_DECL(3, 0) NIR_DECL(3, 1) NIR_DECL(3, 2)
 NIR_DECL(4, 0) NIR_DECL(4, 1) NIR_DECL(4, 2)
+NIR_DECL(5, 0) NIR_DECL(5, 1) NIR_DECL(5, 2)
 #undef NIR_DECL
 
 KInfo nir_kinfo(int shape, int P, int prec, int op, int variant)
 {
     typedef KInfo (*F)(int, int, int);
-    static const F tab[5][3] = {
+    static const F tab[6][3] = {
         {nir_kinfo_s0_p0, nir_kinfo_s0_p1, nir_kinfo_s0_p2}, {nir_kinfo_s1_p0, nir_kinfo_s1_p1, nir_kinfo_s1_p2},
         {nir_kinfo_s2_p0, nir_kinfo_s2_p1, nir_kinfo_s2_p2}, {nir_kinfo_s3_p0, nir_kinfo_s3_p1, nir_kinfo_s3_p2},
-        {nir_kinfo_s4_p0, nir_kinfo_s4_p1, nir_kinfo_s4_p2}};
-    if (shape < 0 || shape > 4 || prec < 0 || prec > 2) return KInfo{};
+        {nir_kinfo_s4_p0, nir_kinfo_s4_p1, nir_kinfo_s4_p2}, {nir_kinfo_s5_p0, nir_kinfo_s5_p1, nir_kinfo_s5_p2}};
+    if (shape < 0 || shape > 5 || prec < 0 || prec > 2) return KInfo{};
     return tab[shape][prec](P, op, variant);
 }
 
@@ -53,6 +54,7 @@ KInfo nir_toe_kinfo(int shape, int P, int prec)
         {nir_toe_kinfo_s2_p0, nir_toe_kinfo_s2_p1, nir_toe_kinfo_s2_p2},
         {nir_toe_kinfo_s3_p0, nir_toe_kinfo_s3_p1, nir_toe_kinfo_s3_p2},
         {nir_toe_kinfo_s4_p0, nir_toe_kinfo_s4_p1, nir_toe_kinfo_s4_p2}};
+    // pyramids (shape 5) have no threading-over-elements kernel: UNSUPPORTED
     if (shape < 0 || shape > 4 || prec < 0 || prec > 2) return KInfo{};
     return tab[shape][prec](P);
 }
@@ -339,7 +341,7 @@ extern "C" int nir_block_create(nir_ctx *ctx, const nir_block_desc *d, nir_block
 {
     if (!ctx || !d || !out) return NIR_ERR_INVALID_ARG;
     *out = nullptr;
-    if (d->shape < NIR_QUAD || d->shape > NIR_TET || d->nelem < 1) return NIR_ERR_INVALID_ARG;
+    if (d->shape < NIR_QUAD || d->shape > NIR_PYR || d->nelem < 1) return NIR_ERR_INVALID_ARG;
     if (d->P < 1 || d->P > 9 || d->Q != d->P + 2) return NIR_ERR_UNSUPPORTED;
     if (d->basis != NIR_BASIS_MODIFIED && d->basis != NIR_BASIS_GLL_LAGRANGE) return NIR_ERR_INVALID_ARG;
     if (d->basis == NIR_BASIS_GLL_LAGRANGE && d->shape != NIR_QUAD && d->shape != NIR_HEX) return NIR_ERR_UNSUPPORTED;
@@ -354,7 +356,8 @@ extern "C" int nir_block_create(nir_ctx *ctx, const nir_block_desc *d, nir_block
     b->ng = nirk::ngeo(d->shape);
     b->nl = nirk::nlam(d->shape);
     b->epad = ((d->nelem + 63) / 64) * 64;
-    b->geo_pp = (d->deformed || d->shape == NIR_TRI || d->shape == NIR_TET || d->shape == NIR_PRISM) ? 1 : 0;
+    b->geo_pp = (d->deformed || d->shape == NIR_TRI || d->shape == NIR_TET || d->shape == NIR_PRISM ||
+                 d->shape == NIR_PYR) ? 1 : 0;
     const int ntab = nirb_table_size(d->shape, d->P, d->Q);
     b->tab_h.assign(ntab, 0.0);
     if (!nirb_build_tables(d->shape, d->P, d->Q, b->tab_h.data(), d->basis)) {
@@ -432,6 +435,11 @@ extern "C" int nir_block_points(const nir_block *b, double *eta, double *xi)
         case NIR_PRISM: x[0] = 0.5 * (1 + e[0]) * (1 - e[2]) - 1; x[1] = e[1]; x[2] = e[2]; break;
         case NIR_TET:
             x[0] = 0.25 * (1 + e[0]) * (1 - e[1]) * (1 - e[2]) - 1;
+            x[1] = 0.5 * (1 + e[1]) * (1 - e[2]) - 1;
+            x[2] = e[2];
+            break;
+        case NIR_PYR:
+            x[0] = 0.5 * (1 + e[0]) * (1 - e[2]) - 1;
             x[1] = 0.5 * (1 + e[1]) * (1 - e[2]) - 1;
             x[2] = e[2];
             break;

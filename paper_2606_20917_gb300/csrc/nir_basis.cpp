@@ -11,9 +11,10 @@
 //   * Gauss-Lobatto-Legendre: +-1 plus the Gauss-Jacobi(1,1) nodes, weights
 //     2 / (Q (Q-1) P_{Q-1}(x)^2).
 // Directions: quad/hex GLL; tri eta1 GJ(0,0), eta2 GJ(1,0); tet eta1 GJ(0,0),
-// eta2 GJ(1,0), eta3 GJ(2,0); prism eta1, eta2 GLL, eta3 GJ(1,0).  The
-// collapse Jacobians (1-eta2)/2 and ((1-eta3)/2)^2 are absorbed as factors
-// 1/2 and 1/4 of the Gauss-Jacobi weights (Eq. iprodtet's tilde weights).
+// eta2 GJ(1,0), eta3 GJ(2,0); prism eta1, eta2 GLL, eta3 GJ(1,0); pyramid
+// eta1, eta2 GLL, eta3 GJ(2,0).  The collapse Jacobians (1-eta2)/2 and
+// ((1-eta3)/2)^2 are absorbed as factors 1/2 and 1/4 of the Gauss-Jacobi
+// weights (Eq. iprodtet's tilde weights).
 //
 // Basis (Sec. 2.2, Eqs. bwdsumfachex/bwdsumfactet, modified C0 expansion):
 //   psiA_p(z): (1-z)/2, (1+z)/2, (1-z)(1+z)/4 P^{(1,1)}_{p-2}(z)
@@ -234,6 +235,7 @@ bool nirb_shape_rules(int shape, int Q, double *z /*[3][Q]*/, double *w /*[3][Q]
     if (shape == TRI) { kind[0] = 1; kind[1] = 2; sc[1] = 0.5; }
     if (shape == TET) { kind[0] = 1; kind[1] = 2; kind[2] = 3; sc[1] = 0.5; sc[2] = 0.25; }
     if (shape == PRISM) { kind[2] = 2; sc[2] = 0.5; }
+    if (shape == PYR) { kind[2] = 3; sc[2] = 0.25; }
     for (int dir = 0; dir < 3; ++dir) {
         bool ok = kind[dir] == 0 ? nirb_gll(Q, z + dir * Q, w + dir * Q)
                                  : nirb_gauss_jacobi(Q, kind[dir] - 1.0, 0.0, z + dir * Q, w + dir * Q);
@@ -279,8 +281,8 @@ bool nirb_build_tables(int shape, int P, int Q, double *blob, int basis)
     const double *z1 = z.data(), *z2 = z.data() + Q, *z3 = z.data() + 2 * Q;
     for (int k = 0; k < Q; ++k)
         for (int r = 0; r < N; ++r) blob[L.Ba + k * N + r] = basis ? nirb_nodal_pair(r, N, z1[k]) : nirb_psiA(r, z1[k]);
-    if (shape == TRI || shape == TET || shape == PRISM) {
-        const double *zb = (shape == PRISM) ? z3 : z2;
+    if (shape == TRI || shape == TET || shape == PRISM || shape == PYR) {
+        const double *zb = (shape == PRISM || shape == PYR) ? z3 : z2;
         for (int p = 0; p < N; ++p) {
             const int nc = cls_cols(N, p);
             double *T = blob + L.Bb + cls_off(N, Q, p);
@@ -298,7 +300,7 @@ bool nirb_build_tables(int shape, int P, int Q, double *blob, int basis)
     }
     nirb_colloc(Q, z1, blob + L.D1);
     if (shape == TRI || shape == TET) nirb_colloc(Q, z2, blob + L.D2);
-    if (shape == TET || shape == PRISM) nirb_colloc(Q, z3, blob + L.D3);
+    if (shape == TET || shape == PRISM || shape == PYR) nirb_colloc(Q, z3, blob + L.D3);
     // even/odd form of Ba (the first-direction points are symmetric for every shape)
     {
         const int ne = sym_ne(N), no = sym_no(N), w = ne + no;

@@ -17,9 +17,29 @@
 
 namespace nirk {
 
-__device__ void vertex_grads(int shape, const double *xi, double G[6][3], int &nv)
+__device__ void vertex_grads(int shape, const double *xi, const double *eta, double G[6][3], int &nv)
 {
     for (int v = 0; v < 6; ++v) G[v][0] = G[v][1] = G[v][2] = 0.0;
+    if (shape == PYR) {
+        // base vertices a_i(eta1) b_j(eta2) (1-eta3)/2 with a_0 = (1-eta1)/2,
+        // a_1 = (1+eta1)/2 (b likewise), apex (1+eta3)/2; the eta-gradient is
+        // taken to xi by d eta/d xi (eta1 and eta2 collapse with 1 - eta3)
+        nv = 5;
+        const double h = 0.5 * (1.0 - eta[2]), r = 1.0 / (1.0 - eta[2]);
+        const double a[2] = {0.5 * (1.0 - eta[0]), 0.5 * (1.0 + eta[0])}, da[2] = {-0.5, 0.5};
+        const double b[2] = {0.5 * (1.0 - eta[1]), 0.5 * (1.0 + eta[1])}, db[2] = {-0.5, 0.5};
+        const int ai[4] = {0, 1, 1, 0}, bj[4] = {0, 0, 1, 1};
+        for (int v = 0; v < 4; ++v) {
+            const double g1 = da[ai[v]] * b[bj[v]] * h;   // d/d eta1
+            const double g2 = a[ai[v]] * db[bj[v]] * h;   // d/d eta2
+            const double g3 = -0.5 * a[ai[v]] * b[bj[v]]; // d/d eta3
+            G[v][0] = g1 * 2.0 * r;
+            G[v][1] = g2 * 2.0 * r;
+            G[v][2] = g1 * (1.0 + eta[0]) * r + g2 * (1.0 + eta[1]) * r + g3;
+        }
+        G[4][2] = 0.5;
+        return;
+    }
     if (shape == TRI) {
         nv = 3;
         G[0][0] = G[0][1] = -0.5;
@@ -68,6 +88,10 @@ __device__ void point_coords(const GeoArgs &a, int n, double eta[3], double xi[3
         xi[0] = 0.25 * (1.0 + eta[0]) * (1.0 - eta[1]) * (1.0 - eta[2]) - 1.0;
         xi[1] = 0.5 * (1.0 + eta[1]) * (1.0 - eta[2]) - 1.0;
         xi[2] = eta[2];
+    } else if (a.shape == PYR) {
+        xi[0] = 0.5 * (1.0 + eta[0]) * (1.0 - eta[2]) - 1.0;
+        xi[1] = 0.5 * (1.0 + eta[1]) * (1.0 - eta[2]) - 1.0;
+        xi[2] = eta[2];
     } else {
         for (int c = 0; c < d; ++c) xi[c] = eta[c];
     }
@@ -97,6 +121,11 @@ __device__ void store_factors(const GeoArgs &a, long long e, int n, const double
         const double s = (1.0 - eta[1]) * (1.0 - eta[2]);
         A[0][0] = 4.0 / s;
         A[0][1] = A[0][2] = 2.0 * (1.0 + eta[0]) / s;
+        A[1][1] = 2.0 / (1.0 - eta[2]);
+        A[1][2] = (1.0 + eta[1]) / (1.0 - eta[2]);
+    } else if (a.shape == PYR) {
+        A[0][0] = 2.0 / (1.0 - eta[2]);
+        A[0][2] = (1.0 + eta[0]) / (1.0 - eta[2]);
         A[1][1] = 2.0 / (1.0 - eta[2]);
         A[1][2] = (1.0 + eta[1]) / (1.0 - eta[2]);
     }
@@ -172,7 +201,7 @@ __global__ void k_geometry(GeoArgs a)
         } else {
             double Gv[6][3];
             int nv = 0;
-            vertex_grads(a.shape, xi, Gv, nv);
+            vertex_grads(a.shape, xi, eta, Gv, nv);
             const double *X = a.nodes + (size_t)e * nv * d;
             for (int v = 0; v < nv; ++v)
                 for (int l = 0; l < d; ++l)

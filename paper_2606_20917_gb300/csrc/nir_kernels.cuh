@@ -289,7 +289,7 @@ struct Modal {
     static constexpr int QQ = Q * Q;
     // class-split stages of the collapsed shapes keep their output loops
     // rolled from P = 6 on in FP32/BF16 (code size; FP64 is bound by its FMA pipe)
-    static constexpr bool R = (SH == TRI || SH == TET || SH == PRISM) && N >= 7 && sizeof(A) == 4;
+    static constexpr bool R = (SH == TRI || SH == TET || SH == PRISM || SH == PYR) && N >= 7 && sizeof(A) == 4;
 
     // All BwdTrans stages but the last: 2-D p0 -> p1; 3-D p0 -> p1 -> p2.
     template <class TP>
@@ -346,6 +346,28 @@ struct Modal {
                         [=](int z, int o, int r) { return (p == 1 && r == nc) ? B0(z, o * N + 1) : Bp(z, o * nc + r); },
                         [=](int e, int q, int o, A v) { p1[e * S + (p * N + q) * Q + o] = v; });
                 });
+            } else if constexpr (SH == PYR) {
+                // t1[p][q][k] = sum_{r<N-c} u[m(p,q,r)] psiB_cr(z3_k), c = max(p,q), over the
+                // 2c+1 pairs of class c; the apex mode (0,0,1) -- psiA_1(eta3) alone -- also
+                // feeds the class-1 pairs (1,0), (1,1), (0,1) through psiB_01(z3_k) = psiA_1(z3_k)
+                // (with psiA_0 + psiA_1 = 1 in eta1 and eta2, the four pairs with p, q <= 1
+                // then carry psiA_1(eta3) to every point).
+                sfor<0, N>([&](auto cc) {
+                    constexpr int c = decltype(cc)::value;
+                    constexpr int nc = N - c;
+                    constexpr int nin = nc + (c == 1 ? 1 : 0);
+                    const TP Bc = tab + L.Bb + cls_off(N, Q, c);
+                    const TP B0 = tab + L.Bb;
+                    pencils0<A, nin, Q, EPB, NT, R>(2 * c + 1, rot,
+                        [=](int e, int s, A *x) {
+                            const A *b = p0 + e * S + pyr_m0(N, pyr_pair_p(c, s), pyr_pair_q(c, s));
+#pragma unroll
+                            for (int r = 0; r < nc; ++r) x[r] = b[r];
+                            if constexpr (c == 1) x[nc] = p0[e * S + 1]; },
+                        [=](int z, int o, int r) { return (c == 1 && r == nc) ? B0(z, o * N + 1) : Bc(z, o * nc + r); },
+                        [=](int e, int s, int o, A v) {
+                            p1[e * S + (pyr_pair_p(c, s) * N + pyr_pair_q(c, s)) * Q + o] = v; });
+                });
             } else {  // TET
                 // t1[pair(p,q)][k] = sum_{r<N-p-q} u[m(p,q,r)] psiB_(p+q)r(z3_k); the collapsed
                 // top vertex (0,0,1) also feeds pairs (0,1) and (1,0) through psiB_01(z3_k).
@@ -366,7 +388,7 @@ struct Modal {
             }
             __syncthreads();
             // ---- stage 2: contract q -> j
-            if constexpr (SH == HEX || SH == PRISM) {
+            if constexpr (SH == HEX || SH == PRISM || SH == PYR) {
                 sym_bwd<A, N, Q, EPB, NT>(N * Q, rot, tab + L.Bs,
                     [=](int e, int s, A *x) { const int p = s / Q, k = s - p * Q;
                         const A *b = p1 + e * S + p * N * Q + k;
@@ -428,7 +450,7 @@ struct Modal {
             __syncthreads();
         } else {
             // ---- transpose of stage 2
-            if constexpr (SH == HEX || SH == PRISM) {
+            if constexpr (SH == HEX || SH == PRISM || SH == PYR) {
                 sym_iprod<A, N, Q, EPB, NT>(N * Q, rot, tab + L.Bs,
                     [=](int e, int s, A *x) { const int p = s / Q, k = s - p * Q;
                         const A *b = p1 + e * S + p * QQ + k;
@@ -480,6 +502,36 @@ struct Modal {
                             for (int r = 0; r < nex; ++r) xx[r] = b[r]; },
                         [=](int z, int r) { return B0(z, r * N + 1); },
                         [=](int e, int q, int o, A v) { outm[e * S + prism_m0(N, p, q) + o] = v; });
+                });
+            } else if constexpr (SH == PYR) {
+                // u[m(p,q,r)] = sum_k psiB_cr(z3_k) t[p][q][k] per pair of class c; the apex
+                // mode (0,0,1) also collects the class-1 pairs (0,1), (1,0), (1,1) through
+                // psiA_1(z3_k) (the transpose of the extra input of the forward stage)
+                sfor<0, N>([&](auto cc) {
+                    constexpr int c = decltype(cc)::value;
+                    constexpr int nc = N - c;
+                    constexpr int nex = (c == 0 && N > 1) ? 3 * Q : 0;
+                    const TP Bc = tab + L.Bb + cls_off(N, Q, c);
+                    const TP B0 = tab + L.Bb;
+                    pencils<A, Q, nc, nex, 1, EPB, NT, R>(2 * c + 1, rot,
+                        [=](int e, int s, A *x) {
+                            const A *b = p2 + e * S + (pyr_pair_p(c, s) * N + pyr_pair_q(c, s)) * Q;
+#pragma unroll
+                            for (int r = 0; r < Q; ++r) x[r] = b[r]; },
+                        [=](int z, int o, int r) { return Bc(z, r * nc + o); },
+                        [=](int e, int, A *xx) {
+                            const A *b1 = p2 + e * S + (0 * N + 1) * Q;
+                            const A *b2 = p2 + e * S + (1 * N + 0) * Q;
+                            const A *b3 = p2 + e * S + (1 * N + 1) * Q;
+#pragma unroll
+                            for (int r = 0; r < nex / 3; ++r) {
+                                xx[r] = b1[r];
+                                xx[r + nex / 3] = b2[r];
+                                xx[r + 2 * (nex / 3)] = b3[r];
+                            } },
+                        [=](int z, int r) { return B0(z, (r % Q) * N + 1); },
+                        [=](int e, int s, int o, A v) {
+                            outm[e * S + pyr_m0(N, pyr_pair_p(c, s), pyr_pair_q(c, s)) + o] = v; });
                 });
             } else {  // TET: the top vertex (0,0,1) collects pairs (0,1) and (1,0)
                 sfor<0, N>([&](auto cc) {

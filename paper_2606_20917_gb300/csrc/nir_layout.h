@@ -3,8 +3,9 @@
 //
 // Notation: N = P+1 modes per direction, Q points per direction, d = 2 or 3.
 // Modes are packed p outermost, then q, then r; the collapsed shapes bound
-// q < N-p (tri, tet) and r < N-p-q (tet) or r < N-p (prism), as in the
-// sum-factorised loops of Sec. 2.2 (Eq. bwdsumfactet).  Points are indexed
+// q < N-p (tri, tet) and r < N-p-q (tet), r < N-p (prism) or
+// r < N-max(p,q) (pyramid), as in the sum-factorised loops of Sec. 2.2
+// (Eq. bwdsumfactet).  Points are indexed
 // i + Q*(j + Q*k) with the first (eta1/xi1) direction fastest.
 #pragma once
 
@@ -16,14 +17,15 @@
 
 namespace nirk {
 
-enum Shape { QUAD = 0, TRI = 1, HEX = 2, PRISM = 3, TET = 4 };
+enum Shape { QUAD = 0, TRI = 1, HEX = 2, PRISM = 3, TET = 4, PYR = 5 };
 
 NIR_HD constexpr int dim(int s) { return (s == QUAD || s == TRI) ? 2 : 3; }
 
 NIR_HD constexpr int nmodes(int s, int N)
 {
     return s == QUAD ? N * N : s == TRI ? N * (N + 1) / 2 : s == HEX ? N * N * N
-         : s == PRISM ? N * N * (N + 1) / 2 : N * (N + 1) * (N + 2) / 6;
+         : s == PRISM ? N * N * (N + 1) / 2 : s == PYR ? N * (N + 1) * (2 * N + 1) / 6
+         : N * (N + 1) * (N + 2) / 6;
 }
 
 NIR_HD constexpr int npts(int s, int Q) { return dim(s) == 2 ? Q * Q : Q * Q * Q; }
@@ -86,10 +88,26 @@ NIR_HD constexpr int prism_m0(int N, int p, int q)
     for (int a = 0; a < p; ++a) o += N * (N - a);
     return o + q * (N - p);
 }
+// pyramid: pair (p,q) holds N - max(p,q) modes r; pairs p outer, q inner.
+// Row p holds sum_q (N - max(p,q)) = (N-p)(N+p+1)/2 modes, so the rows before
+// p hold p N(N+1)/2 - (p-1)p(p+1)/6; within row p, pair q starts after
+// q (N-p) modes when q <= p, else after (p+1)(N-p) + sum_{b=p+1}^{q-1} (N-b).
+NIR_HD constexpr int pyr_m0(int N, int p, int q)
+{
+    const int base = p * N * (N + 1) / 2 - (p - 1) * p * (p + 1) / 6;
+    const int in_row = q <= p ? q * (N - p)
+                              : (p + 1) * (N - p) + (q - p - 1) * N - (q - 1) * q / 2 + p * (p + 1) / 2;
+    return base + in_row;
+}
+// Pyramid pair s (0 <= s < 2c+1) of class c = max(p,q): s <= c is (c, s),
+// s > c is (s - c - 1, c).
+NIR_HD constexpr int pyr_pair_p(int c, int s) { return s <= c ? c : s - c - 1; }
+NIR_HD constexpr int pyr_pair_q(int c, int s) { return s <= c ? s : c; }
 
 // Table blob layout (units of the compute type).
 //  Ba : Q x N, Ba[k*N + r] = psiA_r(z1_k)           (first direction)
-//  Bb : ragged classes p = 0..N-1, Q x (N-p): psiB_pq(z2_j)  (tri/tet eta2; prism eta3)
+//  Bb : ragged classes p = 0..N-1, Q x (N-p): psiB_pq(z2_j)  (tri/tet eta2; prism eta3;
+//       pyramid eta3 with the class c = max(p,q))
 //  Bc : ragged classes c = 0..N-1, Q x (N-c): psiB_cr(z3_k)  (tet eta3; c = p+q)
 //  D1, D2, D3 : Q x Q collocation derivative matrices, D[i*Q + i'] = l'_i'(z_i)
 //  wq : reference quadrature weight per point (collapse factors included)
@@ -108,17 +126,17 @@ NIR_HD constexpr TabLayout layout(int s, int N, int Q)
     TabLayout L{0, 0, 0, 0, 0, 0, 0, 0, 0};
     int o = 0;
     L.Ba = o; o += Q * N;
-    L.Bb = o; if (s == TRI || s == TET || s == PRISM) o += cls_size(N, Q);
+    L.Bb = o; if (s == TRI || s == TET || s == PRISM || s == PYR) o += cls_size(N, Q);
     L.Bc = o; if (s == TET) o += cls_size(N, Q);
     L.D1 = o; o += Q * Q;
     L.D2 = o; if (s == TRI || s == TET) o += Q * Q;
-    L.D3 = o; if (s == TET || s == PRISM) o += Q * Q;
+    L.D3 = o; if (s == TET || s == PRISM || s == PYR) o += Q * Q;
     L.wq = o; o += npts(s, Q);
     L.Bs = o; o += ((Q + 1) / 2) * (sym_ne(N) + sym_no(N));
     L.total = o;
     // directions sharing a rule share a table
     if (s == QUAD || s == HEX) { L.D2 = L.D1; L.D3 = L.D1; }
-    if (s == PRISM) L.D2 = L.D1;
+    if (s == PRISM || s == PYR) L.D2 = L.D1;
     return L;
 }
 

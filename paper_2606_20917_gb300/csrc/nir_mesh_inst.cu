@@ -31,7 +31,7 @@ using TT = __nv_bfloat16;
 #endif
 
 #if NIR_MESH_DIM == 3
-constexpr int kShapes[3] = {HEX, PRISM, TET};
+constexpr int kShapes[4] = {HEX, PRISM, TET, PYR};
 #else
 constexpr int kShapes[2] = {QUAD, TRI};
 #endif
@@ -59,7 +59,7 @@ constexpr int kMeshNT = sizeof(typename CT<TT>::type) == 8 ? 256 : 512;
 // 512-thread CTAs per SM).
 NIR_HD constexpr bool use_ctab(int SH, int N)
 {
-    return SH == HEX ? N <= 4 : SH == PRISM ? N <= 5 : SH == TET ? N <= 3 : true;
+    return SH == HEX ? N <= 4 : SH == PRISM ? N <= 5 : (SH == TET || SH == PYR) ? N <= 3 : true;
 }
 
 template <int VID>

@@ -28,6 +28,9 @@ double helm_flops(int shape, int P)
     case NIR_HEX: return 4 * (N * N * N * Q + N * N * Q * Q + N * Q * Q * Q) + 12 * Q * Q * Q * Q + 20 * Q * Q * Q;
     case NIR_PRISM:
         return 4 * (N * N * (N + 1) / 2 * Q + N * N * Q * Q + N * Q * Q * Q) + 12 * Q * Q * Q * Q + 20 * Q * Q * Q;
+    case NIR_PYR:
+        return 4 * (N * (N + 1) * (2 * N + 1) / 6 * Q + N * N * Q * Q + N * Q * Q * Q) + 12 * Q * Q * Q * Q +
+               20 * Q * Q * Q;
     case NIR_TET:
         return 4 * (N * (N + 1) * (N + 2) / 6 * Q + N * (N + 1) / 2 * Q * Q + N * Q * Q * Q) + 12 * Q * Q * Q * Q +
                20 * Q * Q * Q;

@@ -11,7 +11,8 @@ expansion:
   psiA_0 = (1-z)/2, psiA_1 = (1+z)/2, psiA_p = (1-z)(1+z)/4 P^(1,1)_{p-2}(z);
   psiB_0q = psiA_q, psiB_p0 = ((1-z)/2)^p,
   psiB_pq = ((1-z)/2)^p (1+z)/2 P^(2p-1,1)_{q-1}(z)  (p, q >= 1);
-  the tetrahedron's third direction uses psiB_cr with c = p + q.
+  the tetrahedron's third direction uses psiB_cr with c = p + q, the
+  pyramid's with c = max(p, q).
 """
 import os
 import shutil
@@ -24,7 +25,7 @@ import oracle as orc
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2606_20917_gb300", "csrc")
-SHAPES = {"quad": 0, "tri": 1, "hex": 2, "prism": 3, "tet": 4}
+SHAPES = {"quad": 0, "tri": 1, "hex": 2, "prism": 3, "tet": 4, "pyr": 5}
 
 
 @pytest.fixture(scope="module")
@@ -95,7 +96,7 @@ def test_host_tables_match_oracle(dump, shape):
         # ragged classes of the collapsed directions
         if shape in ("tri", "tet"):
             assert np.allclose(seg("Bb", L["Bc"] - L["Bb"]), cls_table(zs[1], N), rtol=0, atol=1e-13), (P, "Bb")
-        if shape == "prism":
+        if shape in ("prism", "pyr"):   # eta3 classes: p (prism), max(p, q) (pyramid)
             assert np.allclose(seg("Bb", L["Bc"] - L["Bb"]), cls_table(zs[2], N), rtol=0, atol=1e-13), (P, "Bb")
         if shape == "tet":
             assert np.allclose(seg("Bc", L["D1"] - L["Bc"]), cls_table(zs[2], N), rtol=0, atol=1e-13), (P, "Bc")

@@ -18,6 +18,9 @@ Geometry conventions (the element maps both sides must implement):
 * prism: the triangle lives in the (xi1, xi3) plane and is extruded along xi2:
   V0=(-1,-1,-1), V1=(1,-1,-1), V2=(1,1,-1), V3=(-1,1,-1), V4=(-1,-1,1),
   V5=(-1,1,1); the map is linear in the triangle and in xi2.
+* pyr: base V0=(-1,-1,-1), V1=(1,-1,-1), V2=(1,1,-1), V3=(-1,1,-1), apex
+  V4=(-1,-1,1); the map is that of the five vertex functions (affine when
+  the base is a parallelogram, as in ``pyramid_split``).
 
 The curved hexahedral meshes use the periodic displacement
 ``x = X + a sin(2 pi Y) sin(2 pi Z)`` with the same formula permuted cyclically
@@ -219,6 +222,8 @@ def workload(name: str) -> dict:
         return dict(shape="tet", P=4, Q=6, gorder=1, nodes=tet_kuhn(20), deformed=False)
     if name == "prism40x40x20_p4":
         return dict(shape="prism", P=4, Q=6, gorder=1, nodes=prism_split(40, 40, 20), deformed=False)
+    if name == "pyr20_split_p4":
+        return dict(shape="pyr", P=4, Q=6, gorder=1, nodes=pyramid_split(20, 20, 20), deformed=False)
     if name == "hex48_curved_p6":
         return dict(shape="hex", P=6, Q=8, gorder=6, nodes=hex_grid(48, 6), deformed=True)
     raise KeyError(name)
