@@ -721,13 +721,17 @@ struct Config {
     static constexpr int EPB_DEF = raw >= 64 ? 64 : raw >= 32 ? 32 : raw >= 16 ? 16 : raw >= 8 ? 8 : raw >= 4 ? 4
                                  : raw >= 2 ? 2 : 1;
     static constexpr int EPB = EPB_ > 0 ? EPB_ : EPB_DEF;
-    // Threads: 256 (512 for the fused FP32/BF16 Helmholtz), fewer when a group
-    // is small: the fused stages then have Q^2 (3-D) or Q (2-D) pencils per
-    // element, and a CTA of half that many threads runs its heaviest stages in
-    // two full rounds instead of leaving warps idle at every barrier.  NT_ > 0
-    // forces a size (the persistent mesh kernel shares one size).
+    // Threads: 256 (up to 512 for the fused FP32/BF16 Helmholtz): the fused
+    // stages have Q^2 (3-D) or Q (2-D) pencils per element, and the CTA is
+    // sized so that its heaviest stages run in whole rounds (two, or more when
+    // two would exceed 512 threads) instead of leaving warps idle at every
+    // barrier.  NT_ > 0 forces a size (the persistent mesh kernel shares one).
     static constexpr int PENCILS = (D == 3 ? Q * Q : Q) * EPB;
-    static constexpr int NT_HALF = ((PENCILS / 2 + 31) / 32) * 32;
+    // at least two rounds, and as many as keep the CTA within 512 threads,
+    // every thread running the same number of rounds (1152 pencils: 3 x 384
+    // rather than 2.25 x 512)
+    static constexpr int ROUNDS = (PENCILS + 511) / 512 > 2 ? (PENCILS + 511) / 512 : 2;
+    static constexpr int NT_HALF = ((PENCILS / ROUNDS + (PENCILS % ROUNDS ? 1 : 0) + 31) / 32) * 32;
     static constexpr int NT_AUTO = FUSED ? (NT_HALF >= 512 ? 512 : NT_HALF < 128 ? 128 : NT_HALF) : 256;
     static constexpr int NT = NT_ > 0 ? NT_ : NT_AUTO;
     static constexpr int BUFB = NBUF * EPB * S * (int)sizeof(A);

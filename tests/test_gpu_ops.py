@@ -357,7 +357,8 @@ def test_kernel_info_reports_the_launched_kernel(nir, ctx):
     for prec in ("f64", "f32"):
         for op in ("bwd", "helm"):
             ki = blk.kernel_info(prec, op)
-            assert 0 < ki["registers"] <= 255 and ki["threads"] in (128, 256, 512, 1024)
+            # whole warps; the fused FP32/BF16 CTA is sized to run its heaviest stages in whole rounds
+            assert 0 < ki["registers"] <= 255 and ki["threads"] % 32 == 0 and 32 <= ki["threads"] <= 1024
             assert ki["smem_bytes"] > 0 and ki["elems_per_cta"] >= 1
     blk.set_tuning("f32", 1, 0, 0)
     half = blk.kernel_info("f32", "helm")["elems_per_cta"]
