@@ -123,6 +123,18 @@ int nir_ctx_check(nir_ctx *ctx);
  * reports NIR_ERR_CUDA and clears the word.  Asynchronous.  Errors:
  * INVALID_ARG, CUDA. */
 int nir_ctx_selftest_wait(nir_ctx *ctx, int64_t limit_cycles);
+/* Debug mode (a library facility; the paper has no counterpart).  When on,
+ * every device-buffer operator call (the block operators, nir_mesh_helmholtz,
+ * nir_asm_gather / assemble / pick / apply) synchronises the context stream
+ * after its launch and reports a failed kernel, or a device error word set by
+ * it or by earlier work on the stream, as NIR_ERR_CUDA at that call (clearing
+ * the word) instead of at a later nir_ctx_check.  Calls made while the stream
+ * is being captured into a CUDA graph are not synchronised.  The initial state
+ * comes from the environment variable NIR_DEBUG at nir_ctx_create (set and not
+ * "0": on).  Costs one host round trip per call.  Errors: INVALID_ARG (on not
+ * 0 or 1). */
+int nir_ctx_set_debug(nir_ctx *ctx, int on);
+int nir_ctx_get_debug(const nir_ctx *ctx, int *on);
 
 /* Create a block; builds the FP64 basis/quadrature tables (Eqs. basis matrix,
  * bwdsumfachex, bwdsumfactet, stdderiv) and uploads them.  Errors:
@@ -281,7 +293,9 @@ int nir_mesh_num_dofs(const nir_mesh *mesh, int64_t *ndof);
 int nir_mesh_helmholtz(nir_mesh *mesh, int prec, double lambda, const void *in, void *out);
 /* Autotune elements-per-CTA and grid size of every (shape, P, prec) of the mesh
  * by timing candidates, and per precision the launch form (below); reads/writes
- * a JSON cache when cache_path != NULL. */
+ * a JSON cache at cache_path, or, when cache_path is NULL or empty, at the path
+ * the environment variable NIR_TUNE_CACHE names (no cache if that is unset or
+ * empty too).  Errors: INVALID_ARG (also an unwritable cache), NO_MEMORY, CUDA. */
 int nir_tune(nir_mesh *mesh, const char *cache_path);
 
 /* Launch form of a mesh apply: NIR_MESH_PERSISTENT = one persistent kernel

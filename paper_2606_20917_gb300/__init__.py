@@ -92,6 +92,8 @@ _SIGS = {
     "nir_probe_fp64_peak": [_vp, C.POINTER(_d)],
     "nir_probe_fp64_mma_peak": [_vp, C.POINTER(_d)],
     "nir_ctx_selftest_wait": [_vp, _i64],
+    "nir_ctx_set_debug": [_vp, C.c_int],
+    "nir_ctx_get_debug": [_vp, C.POINTER(C.c_int)],
     "nir_cg_solve_dist": [_vp, _d, _vp, _vp, C.POINTER(CGOpts), C.POINTER(CGStats), _vp, _vp],
     "nir_partition_elements": [_i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i64), _i, C.POINTER(_i64)],
     "nir_asm_create": [_vp, C.POINTER(_vp), C.POINTER(_vp), _i, C.POINTER(_vp)],
@@ -203,6 +205,19 @@ class Context:
         v = _d()
         _chk(_lib.nir_probe_fp64_mma_peak(self.h, C.byref(v)), "nir_probe_fp64_mma_peak")
         return v.value
+
+    @property
+    def debug(self) -> bool:
+        """Debug mode: every device-buffer operator call synchronises and
+        raises at the call whose kernel (or earlier stream work) failed.
+        Initially on when the environment variable NIR_DEBUG is set and not "0"."""
+        v = C.c_int(0)
+        _chk(_lib.nir_ctx_get_debug(self.h, C.byref(v)), "nir_ctx_get_debug")
+        return bool(v.value)
+
+    @debug.setter
+    def debug(self, on: bool):
+        _chk(_lib.nir_ctx_set_debug(self.h, 1 if on else 0), "nir_ctx_set_debug")
 
     def selftest_wait(self, limit_cycles: int):
         """Launch the bounded-wait self-test (see nir_ctx_selftest_wait); the

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -298,6 +299,8 @@ extern "C" int nir_ctx_create(nir_ctx **out, int device, void *stream)
     if (!c) return NIR_ERR_NO_MEMORY;
     c->device = device;
     c->stream = (cudaStream_t)stream;
+    const char *dbg = std::getenv("NIR_DEBUG");
+    c->debug = dbg && dbg[0] && std::strcmp(dbg, "0") != 0;
     if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&c->derr, sizeof(int)) != cudaSuccess || cudaMemset(c->derr, 0, sizeof(int)) != cudaSuccess) {
         if (c->derr) cudaFree(c->derr);
@@ -320,6 +323,36 @@ extern "C" void nir_ctx_destroy(nir_ctx *ctx)
     if (!ctx) return;
     if (ctx->derr) cudaFree(ctx->derr);
     delete ctx;
+}
+
+extern "C" int nir_ctx_set_debug(nir_ctx *ctx, int on)
+{
+    if (!ctx || (on != 0 && on != 1)) return NIR_ERR_INVALID_ARG;
+    ctx->debug = on != 0;
+    return NIR_OK;
+}
+
+extern "C" int nir_ctx_get_debug(const nir_ctx *ctx, int *on)
+{
+    if (!ctx || !on) return NIR_ERR_INVALID_ARG;
+    *on = ctx->debug ? 1 : 0;
+    return NIR_OK;
+}
+
+int nir_debug_after(nir_ctx *ctx, int rc)
+{
+    if (rc || !ctx || !ctx->debug) return rc;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return NIR_ERR_CUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return rc;  // synchronising would end the capture
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return NIR_ERR_CUDA;
+    }
+    return nir_ctx_check(ctx);
 }
 
 extern "C" int nir_ctx_check(nir_ctx *ctx)
@@ -589,8 +622,9 @@ bool distinct(std::initializer_list<const void *> ps)
 extern "C" int nir_bwd_trans(nir_block *b, int prec, const void *coeff, void *phys)
 {
     if (!b || !valid_prec(prec) || !coeff || !phys || coeff == phys) return NIR_ERR_INVALID_ARG;
-    return nir_launch_op(b, prec, nirk::OP_BWD, 0.0, coeff, nullptr, nullptr, phys, nullptr, nullptr,
-                         b->ctx->stream, 0);
+    const int lrc = nir_launch_op(b, prec, nirk::OP_BWD, 0.0, coeff, nullptr, nullptr, phys, nullptr, nullptr,
+                                  b->ctx->stream, 0);
+    return nir_debug_after(b->ctx, lrc);
 }
 
 extern "C" int nir_iproduct_wrt_base(nir_block *b, int prec, const void *phys, void *coeff)
@@ -598,8 +632,9 @@ extern "C" int nir_iproduct_wrt_base(nir_block *b, int prec, const void *phys, v
     int rc = check_block(b, prec);
     if (rc) return rc;
     if (!phys || !coeff || phys == coeff) return NIR_ERR_INVALID_ARG;
-    return nir_launch_op(b, prec, nirk::OP_IPROD, 0.0, phys, nullptr, nullptr, coeff, nullptr, nullptr,
-                         b->ctx->stream, 0);
+    const int lrc = nir_launch_op(b, prec, nirk::OP_IPROD, 0.0, phys, nullptr, nullptr, coeff, nullptr,
+                                  nullptr, b->ctx->stream, 0);
+    return nir_debug_after(b->ctx, lrc);
 }
 
 extern "C" int nir_phys_deriv(nir_block *b, int prec, const void *phys, void *d0, void *d1, void *d2)
@@ -608,7 +643,9 @@ extern "C" int nir_phys_deriv(nir_block *b, int prec, const void *phys, void *d0
     if (rc) return rc;
     if (!phys || !d0 || !d1 || (b->dim == 3) != (d2 != nullptr)) return NIR_ERR_INVALID_ARG;
     if (!distinct({phys, d0, d1, d2})) return NIR_ERR_INVALID_ARG;
-    return nir_launch_op(b, prec, nirk::OP_PHYSDERIV, 0.0, phys, nullptr, nullptr, d0, d1, d2, b->ctx->stream, 0);
+    const int lrc = nir_launch_op(b, prec, nirk::OP_PHYSDERIV, 0.0, phys, nullptr, nullptr, d0, d1, d2,
+                                  b->ctx->stream, 0);
+    return nir_debug_after(b->ctx, lrc);
 }
 
 extern "C" int nir_iproduct_wrt_deriv_base(nir_block *b, int prec, const void *f0, const void *f1,
@@ -618,8 +655,9 @@ extern "C" int nir_iproduct_wrt_deriv_base(nir_block *b, int prec, const void *f
     if (rc) return rc;
     if (!f0 || !f1 || !coeff || (b->dim == 3) != (f2 != nullptr)) return NIR_ERR_INVALID_ARG;
     if (!distinct({f0, f1, f2, coeff})) return NIR_ERR_INVALID_ARG;
-    return nir_launch_op(b, prec, nirk::OP_IPROD_DERIV, 0.0, f0, f1, f2, coeff, nullptr, nullptr,
-                         b->ctx->stream, 0);
+    const int lrc = nir_launch_op(b, prec, nirk::OP_IPROD_DERIV, 0.0, f0, f1, f2, coeff, nullptr, nullptr,
+                                  b->ctx->stream, 0);
+    return nir_debug_after(b->ctx, lrc);
 }
 
 extern "C" int nir_mass(nir_block *b, int prec, const void *in, void *out)
@@ -627,8 +665,9 @@ extern "C" int nir_mass(nir_block *b, int prec, const void *in, void *out)
     int rc = check_block(b, prec);
     if (rc) return rc;
     if (!in || !out || in == out) return NIR_ERR_INVALID_ARG;
-    return nir_launch_op(b, prec, nirk::OP_MASS, 0.0, in, nullptr, nullptr, out, nullptr, nullptr,
-                         b->ctx->stream, 0);
+    const int lrc = nir_launch_op(b, prec, nirk::OP_MASS, 0.0, in, nullptr, nullptr, out, nullptr, nullptr,
+                                  b->ctx->stream, 0);
+    return nir_debug_after(b->ctx, lrc);
 }
 
 extern "C" int nir_helmholtz(nir_block *b, int prec, double lambda, const void *in, void *out)
@@ -636,8 +675,9 @@ extern "C" int nir_helmholtz(nir_block *b, int prec, double lambda, const void *
     int rc = check_block(b, prec);
     if (rc) return rc;
     if (!in || !out || in == out || !std::isfinite(lambda)) return NIR_ERR_INVALID_ARG;
-    return nir_launch_op(b, prec, nirk::OP_HELM, lambda, in, nullptr, nullptr, out, nullptr, nullptr,
-                         b->ctx->stream, 0);
+    const int lrc = nir_launch_op(b, prec, nirk::OP_HELM, lambda, in, nullptr, nullptr, out, nullptr, nullptr,
+                                  b->ctx->stream, 0);
+    return nir_debug_after(b->ctx, lrc);
 }
 
 extern "C" int nir_helmholtz_fields(nir_block *b, int prec, double lambda, int nfields, const void *const *in,
@@ -655,9 +695,10 @@ extern "C" int nir_helmholtz_fields(nir_block *b, int prec, double lambda, int n
     for (size_t i = 0; i < ptrs.size(); ++i)
         for (size_t j = i + 1; j < ptrs.size(); ++j)
             if (ptrs[i] == ptrs[j]) return NIR_ERR_INVALID_ARG;
-    return nir_launch_op(b, prec, nirk::OP_HELM, lambda, in[0], nfields > 1 ? in[1] : nullptr,
-                         nfields > 2 ? in[2] : nullptr, out[0], nfields > 1 ? out[1] : nullptr,
-                         nfields > 2 ? out[2] : nullptr, b->ctx->stream, 0);
+    const int lrc = nir_launch_op(b, prec, nirk::OP_HELM, lambda, in[0], nfields > 1 ? in[1] : nullptr,
+                                  nfields > 2 ? in[2] : nullptr, out[0], nfields > 1 ? out[1] : nullptr,
+                                  nfields > 2 ? out[2] : nullptr, b->ctx->stream, 0);
+    return nir_debug_after(b->ctx, lrc);
 }
 
 // Host-buffer Helmholtz: the elements are split into chunks (multiples of 64

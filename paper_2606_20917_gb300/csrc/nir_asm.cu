@@ -276,7 +276,7 @@ int launch_apply_t(nir_asm *a, int op, int prec, double lambda, const T *x, long
         (void)cudaGetLastError();
         return NIR_ERR_CUDA;
     }
-    return NIR_OK;
+    return nir_debug_after(a->ctx, NIR_OK);
 }
 
 // y[0:nrows] = (A^T H A x)[0:nrows] with x[g] = 0 for g >= n_avail.
@@ -747,7 +747,7 @@ extern "C" int nir_asm_gather(nir_asm *a, int prec, const void *x_global, void *
         (void)cudaGetLastError();
         return NIR_ERR_CUDA;
     }
-    return NIR_OK;
+    return nir_debug_after(a->ctx, NIR_OK);
 }
 
 extern "C" int nir_asm_assemble(nir_asm *a, int prec, const void *y_local, void *y_global)
@@ -769,7 +769,7 @@ extern "C" int nir_asm_assemble(nir_asm *a, int prec, const void *y_local, void 
         (void)cudaGetLastError();
         return NIR_ERR_CUDA;
     }
-    return NIR_OK;
+    return nir_debug_after(a->ctx, NIR_OK);
 }
 
 extern "C" int nir_asm_pick(nir_asm *a, const double *x_local, double *x_global)
@@ -780,7 +780,7 @@ extern "C" int nir_asm_pick(nir_asm *a, const double *x_local, double *x_global)
         (void)cudaGetLastError();
         return NIR_ERR_CUDA;
     }
-    return NIR_OK;
+    return nir_debug_after(a->ctx, NIR_OK);
 }
 
 extern "C" int nir_asm_apply(nir_asm *a, int op, double lambda, int prec, const void *x_global, void *y_global)
@@ -790,7 +790,8 @@ extern "C" int nir_asm_apply(nir_asm *a, int op, double lambda, int prec, const 
         return NIR_ERR_INVALID_ARG;
     for (nir_block *b : a->blocks)
         if (!b->geo_set) return NIR_ERR_STATE;
-    return launch_apply(a, op, prec, lambda, x_global, a->nglob, y_global, a->nglob, a->ctx->stream);
+    return nir_debug_after(a->ctx,
+                           launch_apply(a, op, prec, lambda, x_global, a->nglob, y_global, a->nglob, a->ctx->stream));
 }
 
 extern "C" int nir_asm_cg_solve(nir_asm *a, int op, double lambda, int fix_boundary, const double *b, double *x,

@@ -28,6 +28,11 @@ struct KInfo {
     const void *fn_fields = nullptr;  // Helmholtz, default variant: the multi-field form
 };
 
+// Debug mode: after a successful operator launch, synchronise the context
+// stream (unless it is being captured) and report a launch failure or a set
+// device error word at this call.  Returns rc unchanged otherwise.
+int nir_debug_after(nir_ctx *ctx, int rc);
+
 // Provided by the instantiation units (one per shape x precision).
 KInfo nir_kinfo(int shape, int P, int prec, int op, int variant);
 // The threading-over-elements Helmholtz kernel (Helmholtz variant 4).
@@ -39,6 +44,7 @@ struct nir_ctx {
     cudaStream_t stream = nullptr;
     int num_sms = 0;
     int *derr = nullptr;                    // device error word of bounded in-kernel waits
+    bool debug = false;                     // check every operator call synchronously
     std::mutex mu;
     std::map<const void *, int> occupancy;  // CTAs per SM per kernel
     std::map<std::string, int> tuned_grid;  // autotuner overrides (key: shape/P/prec/op)

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <map>
@@ -384,7 +385,7 @@ extern "C" int nir_mesh_helmholtz(nir_mesh *m, int prec, double lambda, const vo
 {
     if (!m || !valid_prec(prec) || !in || !out || in == out || !std::isfinite(lambda)) return NIR_ERR_INVALID_ARG;
     NIR_CUDA_TRY(cudaSetDevice(m->ctx->device));
-    return nir_mesh_apply(m, prec, lambda, in, out, m->ctx->stream);
+    return nir_debug_after(m->ctx, nir_mesh_apply(m, prec, lambda, in, out, m->ctx->stream));
 }
 
 // --------------------------------------------------------------------------- autotuner
@@ -481,6 +482,10 @@ extern "C" int nir_tune(nir_mesh *m, const char *cache_path)
     nir_ctx *ctx = m->ctx;
     NIR_CUDA_TRY(cudaSetDevice(ctx->device));
     const std::string gpu = gpu_name(ctx->device);
+    if (!cache_path || !cache_path[0]) {  // the environment may name the cache
+        const char *env = std::getenv("NIR_TUNE_CACHE");
+        cache_path = env && env[0] ? env : nullptr;
+    }
     auto kv = read_cache(cache_path);
     cudaStream_t st = ctx->stream;
     const char *pname[3] = {"f64", "f32", "bf16"};

@@ -92,6 +92,19 @@ def test_tune_and_cache(nir, ctx, tmp_path):
     assert torch.equal(mesh.helmholtz(x), before)
 
 
+def test_tune_cache_named_by_environment(nir, ctx, tmp_path, monkeypatch):
+    """With no cache path given, the tuner uses the file NIR_TUNE_CACHE names."""
+    mesh, _ = build_mesh(nir, ctx, small_hybrid())
+    cache = tmp_path / "env_tune.json"
+    monkeypatch.setenv("NIR_TUNE_CACHE", str(cache))
+    mesh.tune(None)
+    kv = json.load(open(cache))
+    assert any("|mesh|" in k for k in kv)
+    stamp = cache.stat().st_mtime_ns
+    mesh.tune("")                      # an empty path falls back to the environment too
+    assert json.load(open(cache)) == kv and cache.stat().st_mtime_ns >= stamp
+
+
 def hex_problem(nir, ctx, n=4, P=3, amp=0.05):
     nodes = W.hex_grid(n, 2, amp=amp)
     parts = [dict(shape="hex", P=P, Q=P + 2, gorder=2, nodes=nodes, deformed=True)]
