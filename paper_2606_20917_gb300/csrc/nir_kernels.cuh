@@ -38,6 +38,18 @@
 
 #include "nir_layout.h"
 
+// Values the compiler must treat as unknown (a loop bound it could otherwise
+// prove small, a zero it could fold).  The stage code also compiles as host
+// C++ (a CTA emulation that checks its shared-memory indexing and barriers);
+// there both are plain assignments.
+#ifdef __CUDA_ARCH__
+#define NIR_OPAQUE(v) asm volatile("mov.u32 %0, %0;" : "+r"(v))
+#define NIR_ZERO(v) asm volatile("mov.u32 %0, 0;" : "=r"(v))
+#else
+#define NIR_OPAQUE(v) ((void)(v))
+#define NIR_ZERO(v) ((v) = 0)
+#endif
+
 namespace nirk {
 
 enum Op { OP_BWD = 0, OP_IPROD = 1, OP_PHYSDERIV = 2, OP_IPROD_DERIV = 3, OP_MASS = 4, OP_HELM = 5 };
@@ -101,14 +113,14 @@ __device__ __forceinline__ void pencils(int per_e, int &rot, LD ld, TB tb, LDX l
     // otherwise prove the loop runs at most once and straight-lines whole stages
     // into code that needs several times the registers.
     int total = per_e * EPB;
-    asm volatile("mov.u32 %0, %0;" : "+r"(total));
+    NIR_OPAQUE(total);
     int w = (int)threadIdx.x - (rot % NT);
     if (w < 0) w += NT;
     for (; w < total; w += NT) {
         const int e = w % EPB;
         const int s = w / EPB;
         int z;
-        asm volatile("mov.u32 %0, 0;" : "=r"(z));
+        NIR_ZERO(z);
         A x[NIN];
         ld(e, s, x);
         A xx[NEX > 0 ? NEX : 1];
@@ -143,12 +155,12 @@ template <int EPB, int NT, class F>
 __device__ __forceinline__ void for_items(int per_e, int &rot, F f)
 {
     int total = per_e * EPB;
-    asm volatile("mov.u32 %0, %0;" : "+r"(total));
+    NIR_OPAQUE(total);
     int w = (int)threadIdx.x - (rot % NT);
     if (w < 0) w += NT;
     for (; w < total; w += NT) {
         int z;
-        asm volatile("mov.u32 %0, 0;" : "=r"(z));
+        NIR_ZERO(z);
         f(w % EPB, w / EPB, z);
     }
     rot += total;
@@ -1360,6 +1372,7 @@ __device__ __forceinline__ void run_group(const KArgs &a, const void *fin, void 
     __syncthreads();
 }
 
+#ifdef __CUDACC__  // device-only from here: bulk copies, mbarriers and the kernels
 // ---------------------------------------------------------------------------
 // Bulk asynchronous copies (TMA, non-tensor form) and mbarriers.
 // ---------------------------------------------------------------------------
@@ -1579,5 +1592,7 @@ __global__ void __launch_bounds__(256)
         }
     }
 }
+
+#endif  // __CUDACC__
 
 }  // namespace nirk
