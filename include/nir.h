@@ -250,9 +250,10 @@ int nir_helmholtz_host_noalloc(nir_block *blk, int prec, double lambda, const vo
  * sets): variant 0 = default elements per CTA, 1 = half, 2 = double (where it
  * fits in shared memory; otherwise the default), 3 = the default group run by
  * the multi-field kernel (same results, another register allocation); grid =
- * CTAs launched (0: one wave at the kernel's occupancy); pf = 1 to prefetch
- * each group's metric to L2 (FP32/BF16 with per-point factors; ignored
- * elsewhere).
+ * CTAs launched (0: one wave at the kernel's occupancy); pf = L2 prefetch of
+ * the groups' metric (FP32/BF16 with per-point factors; ignored elsewhere):
+ * 0 none, 1 each CTA's next group while the current one finishes, 2 each
+ * group's own when it starts.
  * Variant 4 selects the other threading strategy of Sec. 3.3, threading over
  * elements: one thread per element runs all stages, its intermediate tensors
  * in library-owned global scratch of 5 Q^d values per thread of the grid
@@ -265,8 +266,16 @@ int nir_helmholtz_host_noalloc(nir_block *blk, int prec, double lambda, const vo
  * scratch.  Selecting or leaving variant 4 allocates or frees device memory
  * and synchronises the device, so it must not overlap a stream capture on
  * this device; while the context stream is capturing it returns STATE.
- * Errors: INVALID_ARG, STATE; with variant 4 also UNSUPPORTED (nodal basis),
- * TOO_LARGE (2^31 or more scratch values), NO_MEMORY, CUDA. */
+ * Variant 5 (FP32/BF16, quad and hex; UNSUPPORTED elsewhere) runs the default
+ * group with two elements per thread: each pencil carries elements 2e and
+ * 2e+1 side by side in shared memory (one 8-byte access for both) and each
+ * table coefficient multiplies both in one packed FP32x2 operation, halving
+ * the per-pencil index and memory instructions.  Same arithmetic per element
+ * as variant 0, up to the compiler's contraction of separate multiplies and
+ * adds.
+ * Errors: INVALID_ARG (also pf outside 0..2), STATE; with variant 4 also
+ * UNSUPPORTED (nodal basis), TOO_LARGE (2^31 or more scratch values),
+ * NO_MEMORY, CUDA; with variant 5 UNSUPPORTED. */
 int nir_block_set_tuning(nir_block *blk, int prec, int variant, int grid, int pf);
 int nir_block_get_tuning(const nir_block *blk, int prec, int *variant, int *grid, int *pf);
 

@@ -874,8 +874,10 @@ extern "C" int nir_helmholtz_host(nir_block *b, int prec, double lambda, const v
 // --------------------------------------------------------------------------- probe / misc
 extern "C" int nir_block_set_tuning(nir_block *b, int prec, int variant, int grid, int pf)
 {
-    if (!b || !valid_prec(prec) || variant < 0 || variant > NIR_VARIANT_TOE || grid < 0 || (pf != 0 && pf != 1))
+    if (!b || !valid_prec(prec) || variant < 0 || variant > NIR_VARIANT_MAX || grid < 0 || pf < 0 || pf > 2)
         return NIR_ERR_INVALID_ARG;
+    if (variant == NIR_VARIANT_PAIR && !nir_kinfo(b->d.shape, b->d.P, prec, nirk::OP_HELM, variant).fn)
+        return NIR_ERR_UNSUPPORTED;
     // choosing or leaving the threading-over-elements kernel may allocate or
     // free its scratch, which synchronises the device: not inside a capture
     const bool touches_scratch = variant == NIR_VARIANT_TOE || b->helm_variant[prec] == NIR_VARIANT_TOE;

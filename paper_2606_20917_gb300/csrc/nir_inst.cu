@@ -22,15 +22,15 @@ using TT = float;
 using TT = __nv_bfloat16;
 #endif
 
-template <int N, int OP, int EPB, bool STAGE = true>
+template <int N, int OP, int EPB, bool STAGE = true, bool PAIR = false>
 KInfo make1()
 {
-    using C = Config<NIR_SHAPE, N, N + 1, TT, OP, EPB>;
+    using C = Config<NIR_SHAPE, N, N + 1, TT, OP, EPB, 0, PAIR>;
     KInfo k;
     if constexpr (C::FUSED) {  // FP32/BF16 Helmholtz: bulk-copy staged kernel
         constexpr int stg = STAGE ? ((C::EPB * C::M * (int)sizeof(TT) + 15) / 16) * 16 : 0;
-        k.fn = reinterpret_cast<const void *>(&k_helm_tma<NIR_SHAPE, N, N + 1, TT, EPB, STAGE>);
-        if constexpr (EPB == 0 && STAGE)
+        k.fn = reinterpret_cast<const void *>(&k_helm_tma<NIR_SHAPE, N, N + 1, TT, EPB, STAGE, false, PAIR>);
+        if constexpr (EPB == 0 && STAGE && !PAIR)
             k.fn_fields = reinterpret_cast<const void *>(&k_helm_tma<NIR_SHAPE, N, N + 1, TT, 0, true, true>);
         k.smem = C::SMEM + stg;
     } else {
@@ -49,8 +49,10 @@ KInfo make1()
 // 227 KB of shared memory; an FP32/BF16 double group that fits only without
 // its staging buffer loads its coefficients itself); 3: the default group run
 // by the multi-field kernel with one field (the compiler allocates its
-// registers differently, which wins at some orders).  Only the Helmholtz
-// operator has variants.
+// registers differently, which wins at some orders); 5 (FP32/BF16, quad and
+// hex): the default group with two elements per thread (F2 values).  Only
+// the Helmholtz operator has variants (4 is the threading-over-elements
+// kernel, registered separately).
 template <int N, int OP>
 KInfo make(int variant)
 {
@@ -72,6 +74,11 @@ KInfo make(int variant)
             if (!k.fn_fields) return KInfo{};
             k.fn = k.fn_fields;
             return k;
+        }
+        if (variant == 5) {  // two elements per thread
+            if constexpr (C0::FUSED && (NIR_SHAPE == QUAD || NIR_SHAPE == HEX))
+                return make1<N, OP, 0, true, true>();
+            else return KInfo{};
         }
     }
     if (variant != 0) return KInfo{};

@@ -38,6 +38,9 @@ KInfo nir_kinfo(int shape, int P, int prec, int op, int variant);
 // The threading-over-elements Helmholtz kernel (Helmholtz variant 4).
 KInfo nir_toe_kinfo(int shape, int P, int prec);
 #define NIR_VARIANT_TOE 4
+// The FP32/BF16 Helmholtz with two elements per thread (quad/hex).
+#define NIR_VARIANT_PAIR 5
+#define NIR_VARIANT_MAX 5
 
 struct nir_ctx {
     int device = 0;

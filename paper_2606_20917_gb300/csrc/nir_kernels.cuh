@@ -50,6 +50,10 @@
 #define NIR_ZERO(v) ((v) = 0)
 #endif
 
+// Loads of the metric: read once per apply, so streamed with the evict-first
+// policy (the L2 then keeps the prefetched groups rather than consumed ones).
+#define NIR_METRIC_LD __ldcs
+
 namespace nirk {
 
 enum Op { OP_BWD = 0, OP_IPROD = 1, OP_PHYSDERIV = 2, OP_IPROD_DERIV = 3, OP_MASS = 4, OP_HELM = 5 };
@@ -83,6 +87,39 @@ __device__ __forceinline__ void from_a(float v, float *p) { *p = v; }
 __device__ __forceinline__ void from_a(float v, __nv_bfloat16 *p) { *p = __float2bfloat16_rn(v); }
 
 template <class A> __device__ __forceinline__ A fmaa(A a, A b, A c) { return fma(a, b, c); }
+
+// Two elements' values in one lane (element 2e in x, 2e+1 in y): the value
+// type of the paired FP32/BF16 Helmholtz, whose threads each carry one pencil
+// of two elements.  The stage code is shared with the one-element form; the
+// tables stay scalar, and each table coefficient multiplies both elements
+// (one packed FP32x2 multiply-add on sm_100 and later).
+struct F2 {
+    float x, y;
+    F2() = default;
+    __device__ __forceinline__ constexpr F2(float v) : x(v), y(v) {}
+    __device__ __forceinline__ constexpr F2(float a, float b) : x(a), y(b) {}
+};
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+__device__ __forceinline__ F2 f2_of(float2 v) { return F2(v.x, v.y); }
+__device__ __forceinline__ float2 f2_raw(F2 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ F2 fmaa(float a, F2 b, F2 c) { return f2_of(__ffma2_rn(make_float2(a, a), f2_raw(b), f2_raw(c))); }
+__device__ __forceinline__ F2 fmaa(F2 a, F2 b, F2 c) { return f2_of(__ffma2_rn(f2_raw(a), f2_raw(b), f2_raw(c))); }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return f2_of(__fadd2_rn(f2_raw(a), f2_raw(b))); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return f2_of(__fmul2_rn(f2_raw(a), f2_raw(b))); }
+#else
+__device__ __forceinline__ F2 fmaa(float a, F2 b, F2 c) { return F2(fmaf(a, b.x, c.x), fmaf(a, b.y, c.y)); }
+__device__ __forceinline__ F2 fmaa(F2 a, F2 b, F2 c) { return F2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)); }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(a.x * b.x, a.y * b.y); }
+#endif
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ F2 operator*(float a, F2 b) { return F2(a) * b; }
+__device__ __forceinline__ F2 operator*(F2 a, float b) { return a * F2(b); }
+__device__ __forceinline__ F2 &operator*=(F2 &a, F2 b) { return a = a * b; }
+__device__ __forceinline__ F2 &operator+=(F2 &a, F2 b) { return a = a + b; }
+// the compute type of a value type (F2 holds two FP32 values)
+template <class A> struct Scalar { using type = A; };
+template <> struct Scalar<F2> { using type = float; };
 
 template <int I, int E, class F>
 __device__ __forceinline__ void sfor(F &&f)
@@ -301,7 +338,8 @@ struct Modal {
     static constexpr int QQ = Q * Q;
     // class-split stages of the collapsed shapes keep their output loops
     // rolled from P = 6 on in FP32/BF16 (code size; FP64 is bound by its FMA pipe)
-    static constexpr bool R = (SH == TRI || SH == TET || SH == PRISM || SH == PYR) && N >= 7 && sizeof(A) == 4;
+    static constexpr bool R = (SH == TRI || SH == TET || SH == PRISM || SH == PYR) && N >= 7 &&
+                              sizeof(typename Scalar<A>::type) == 4;
 
     // All BwdTrans stages but the last: 2-D p0 -> p1; 3-D p0 -> p1 -> p2.
     template <class TP>
@@ -683,25 +721,25 @@ struct Geo {
     template <int K>
     static __device__ __forceinline__ void load4(const float *p, A (&v)[K])
     {
-        const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+        const float4 q = NIR_METRIC_LD(reinterpret_cast<const float4 *>(p));
         v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
     }
     template <int K>
     static __device__ __forceinline__ void load4(const __nv_bfloat16 *p, A (&v)[K])
     {
-        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
+        const uint2 q = NIR_METRIC_LD(reinterpret_cast<const uint2 *>(p));
         const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.x));
         const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.y));
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
     static __device__ __forceinline__ void load2(const float *p, A &x, A &y)
     {
-        const float2 q = __ldg(reinterpret_cast<const float2 *>(p));
+        const float2 q = NIR_METRIC_LD(reinterpret_cast<const float2 *>(p));
         x = q.x; y = q.y;
     }
     static __device__ __forceinline__ void load2(const __nv_bfloat16 *p, A &x, A &y)
     {
-        const unsigned q = __ldg(reinterpret_cast<const unsigned *>(p));
+        const unsigned q = NIR_METRIC_LD(reinterpret_cast<const unsigned *>(p));
         const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q));
         x = a.x; y = a.y;
     }
@@ -710,10 +748,89 @@ struct Geo {
     static __device__ __forceinline__ void load2(const double *, A &, A &) {}
 };
 
+// The metric of element pairs (2u, 2u+1) for the paired FP32/BF16 Helmholtz.
+// In the packed layout the two elements' quads, pairs and W values are
+// adjacent: one point takes two 16-byte, one 16-byte and one 8-byte load
+// (BF16: 16, 8 and 4 bytes) for both elements.
+template <class T, int NQ, int NG, bool PACK>
+struct GeoPair {
+    Geo<T, float, NQ, NG, PACK> g1;
+    const float *wq;
+    __device__ __forceinline__ void get_all(long long u, int n, F2 (&v)[NG]) const
+    {
+        const long long e = 2 * u;
+        if constexpr (PACK) {
+            if (g1.pp) {
+                const long long blk = (((e >> 5) * NQ + n) * NG) << 5;
+                const int l = (int)(e & 31);
+                float q[8];
+                load8(g1.g + blk + l * 4, q);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[c] = F2(q[c], q[4 + c]);
+                if constexpr (NG == 7) {
+                    float r[4], w[2];
+                    load4(g1.g + blk + 128 + l * 2, r);
+                    load2(g1.g + blk + 192 + l, w);
+                    v[4] = F2(r[0], r[2]);
+                    v[5] = F2(r[1], r[3]);
+                    v[6] = F2(w[0], w[1]);
+                }
+                return;
+            }
+        }
+        float a[NG], b[NG];
+        g1.get_all(e, n, a);
+        g1.get_all(e + 1, n, b);
+#pragma unroll
+        for (int c = 0; c < NG; ++c) v[c] = F2(a[c], b[c]);
+    }
+
+  private:
+    static __device__ __forceinline__ void load8(const float *p, float (&v)[8])
+    {
+        const float4 a = NIR_METRIC_LD(reinterpret_cast<const float4 *>(p));
+        const float4 b = NIR_METRIC_LD(reinterpret_cast<const float4 *>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+    static __device__ __forceinline__ void load4(const float *p, float (&v)[4])
+    {
+        const float4 a = NIR_METRIC_LD(reinterpret_cast<const float4 *>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    static __device__ __forceinline__ void load2(const float *p, float (&v)[2])
+    {
+        const float2 a = NIR_METRIC_LD(reinterpret_cast<const float2 *>(p));
+        v[0] = a.x; v[1] = a.y;
+    }
+    static __device__ __forceinline__ void unpack2(unsigned w, float &a, float &b)
+    {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
+        a = f.x;
+        b = f.y;
+    }
+    static __device__ __forceinline__ void load8(const __nv_bfloat16 *p, float (&v)[8])
+    {
+        const uint4 a = NIR_METRIC_LD(reinterpret_cast<const uint4 *>(p));
+        unpack2(a.x, v[0], v[1]); unpack2(a.y, v[2], v[3]); unpack2(a.z, v[4], v[5]); unpack2(a.w, v[6], v[7]);
+    }
+    static __device__ __forceinline__ void load4(const __nv_bfloat16 *p, float (&v)[4])
+    {
+        const uint2 a = NIR_METRIC_LD(reinterpret_cast<const uint2 *>(p));
+        unpack2(a.x, v[0], v[1]); unpack2(a.y, v[2], v[3]);
+    }
+    static __device__ __forceinline__ void load2(const __nv_bfloat16 *p, float (&v)[2])
+    {
+        unpack2(NIR_METRIC_LD(reinterpret_cast<const unsigned *>(p)), v[0], v[1]);
+    }
+    template <int K> static __device__ __forceinline__ void load8(const double *, float (&)[K]) {}
+    template <int K> static __device__ __forceinline__ void load4(const double *, float (&)[K]) {}
+    template <int K> static __device__ __forceinline__ void load2(const double *, float (&)[K]) {}
+};
+
 // Default elements per CTA: fill about 110 KB (FP64) or 56 KB (FP32/BF16) of
 // shared memory with the operator's buffers.  EPB_ > 0 overrides it (the
 // autotuner picks among compiled alternatives).
-template <int SH, int N, int Q, class T, int OP, int EPB_ = 0, int NT_ = 0>
+template <int SH, int N, int Q, class T, int OP, int EPB_ = 0, int NT_ = 0, bool PAIR = false>
 struct Config {
     using A = typename CT<T>::type;
     static constexpr int D = dim(SH);
@@ -722,6 +839,7 @@ struct Config {
     static constexpr int S = odd_stride(NQ);
     // the fused FP32/BF16 Helmholtz recomputes du/d eta3 in registers: 3 buffers
     static constexpr bool FUSED = (OP == OP_HELM && sizeof(A) == 4);
+    static_assert(!PAIR || FUSED, "paired elements: FP32/BF16 Helmholtz only");
     static constexpr int NBUF = (OP == OP_BWD || OP == OP_IPROD || OP == OP_MASS) ? 2 : FUSED ? 3 : D + 1;
     static constexpr int TABN = layout(SH, N, Q).total;
     static constexpr int TABB = ((TABN * (int)sizeof(A) + 15) / 16) * 16;
@@ -732,13 +850,17 @@ struct Config {
     static constexpr int raw = (budget - TABB) / per_elem;
     static constexpr int EPB_DEF = raw >= 64 ? 64 : raw >= 32 ? 32 : raw >= 16 ? 16 : raw >= 8 ? 8 : raw >= 4 ? 4
                                  : raw >= 2 ? 2 : 1;
-    static constexpr int EPB = EPB_ > 0 ? EPB_ : EPB_DEF;
+    static constexpr int EPB = EPB_ > 0 ? EPB_ : (PAIR && EPB_DEF < 2 ? 2 : EPB_DEF);
+    static_assert(!PAIR || EPB % 2 == 0, "paired elements: an even group");
+    // work units per group: elements, or element pairs (a pair's values are
+    // adjacent, at the unit's index, so one 8-byte access serves both)
+    static constexpr int EPU = PAIR ? EPB / 2 : EPB;
     // Threads: 256 (up to 512 for the fused FP32/BF16 Helmholtz): the fused
     // stages have Q^2 (3-D) or Q (2-D) pencils per element, and the CTA is
     // sized so that its heaviest stages run in whole rounds (two, or more when
     // two would exceed 512 threads) instead of leaving warps idle at every
     // barrier.  NT_ > 0 forces a size (the persistent mesh kernel shares one).
-    static constexpr int PENCILS = (D == 3 ? Q * Q : Q) * EPB;
+    static constexpr int PENCILS = (D == 3 ? Q * Q : Q) * EPU;
     // at least two rounds, and as many as keep the CTA within 512 threads,
     // every thread running the same number of rounds (1152 pencils: 3 x 384
     // rather than 2.25 x 512)
@@ -771,6 +893,33 @@ __device__ __forceinline__ void gstore(T *__restrict__ g, long long e0, int ne, 
 }
 
 // d u / d eta_dir at point (i,j,k) by collocation (Eq. stdderiv).
+// Paired-element forms: unit u holds elements 2u (x) and 2u+1 (y) of the group.
+template <class T, int LEN, int S, int NT>
+__device__ __forceinline__ void gload_pair(const T *__restrict__ g, long long e0, int ne, F2 *sm)
+{
+    const T *src = g + e0 * LEN;
+    const int nu = (ne + 1) / 2;
+    for (int i = threadIdx.x; i < nu * LEN; i += NT) {
+        const int u = i / LEN, m = i - u * LEN;
+        const float a = to_a(__ldg(src + (2 * u) * LEN + m), float());
+        const float b = (2 * u + 1 < ne) ? to_a(__ldg(src + (2 * u + 1) * LEN + m), float()) : 0.0f;
+        sm[u * S + m] = F2(a, b);
+    }
+}
+
+template <class T, int LEN, int S, int NT>
+__device__ __forceinline__ void gstore_pair(T *__restrict__ g, long long e0, int ne, const F2 *sm)
+{
+    T *dst = g + e0 * LEN;
+    const int nu = (ne + 1) / 2;
+    for (int i = threadIdx.x; i < nu * LEN; i += NT) {
+        const int u = i / LEN, m = i - u * LEN;
+        const F2 v = sm[u * S + m];
+        from_a(v.x, dst + (2 * u) * LEN + m);
+        if (2 * u + 1 < ne) from_a(v.y, dst + (2 * u + 1) * LEN + m);
+    }
+}
+
 template <class A, int Q, int D>
 __device__ __forceinline__ A dcol(const A *Ue, const A *Dm, int dir, int i, int j, int k)
 {
@@ -1183,12 +1332,12 @@ __device__ __noinline__ void nodal_pairs(A *buf, bool to_pairs)  // out of line:
 // after_metric: called by every thread once the fused FP32/BF16 Helmholtz
 // has consumed the group's geometric factors (the staged kernel starts the
 // next group's L2 prefetch there).
-template <int SH, int N, int Q, class T, int OP, int EPB_, int NT_, class TP, class HOOK = NoHook>
+template <int SH, int N, int Q, class T, int OP, int EPB_, int NT_, bool PAIR = false, class TP, class HOOK = NoHook>
 __device__ __forceinline__ void run_group(const KArgs &a, const void *fin, void *fout, TP tp,
                                           const typename CT<T>::type *tab, typename CT<T>::type *buf, long long e0,
                                           int ne, bool staged = false, HOOK after_metric = HOOK{})
 {
-    using C = Config<SH, N, Q, T, OP, EPB_, NT_>;
+    using C = Config<SH, N, Q, T, OP, EPB_, NT_, PAIR>;
     using A = typename C::A;
     constexpr int D = C::D, NQ = C::NQ, M = C::M, S = C::S, EPB = C::EPB, NT = C::NT;
     constexpr TabLayout L = layout(SH, N, Q);
@@ -1337,6 +1486,42 @@ __device__ __forceinline__ void run_group(const KArgs &a, const void *fin, void 
             from_pairs(B1);
             gstore<T, A, M, S, NT>(reinterpret_cast<T *>(fout), e0, ne, B1);
         }
+    } else if constexpr (PAIR) {  // OP_HELM, FP32 / BF16, two elements per work unit (see F2)
+        using V = F2;
+        constexpr int EPU = C::EPU;
+        using MV = Modal<SH, N, Q, V, EPU, NT, S>;
+        using HV = HelmStages<SH, N, Q, V, EPU, NT, S>;
+        V *U0 = reinterpret_cast<V *>(buf), *U1 = U0 + EPU * S, *U2 = U1 + EPU * S;
+        const GeoPair<T, NQ, NG, PACK> gp{geo, tab + L.wq};
+        const V lam = V(float(a.lambda));
+        const long long u0 = e0 / 2;  // groups hold an even number of elements
+        if (!staged) {  // otherwise the caller has already put the coefficients in U1
+            gload_pair<T, M, S, NT>(reinterpret_cast<const T *>(fin), e0, ne, U1);
+            __syncthreads();
+        }
+        if constexpr (TENSOR) { if (a.nodal) nodal_pairs<SH, N, V, EPU, NT, S>(U1, true); }
+        if constexpr (D == 2) {
+            MV::front(tp, U1, U2, nullptr);
+            HV::last_grad1(tp, U2, U0, U1);
+            HV::grad_rest(tp, U0, U2);
+            if (a.geo_pp) HV::template metric_tlast<true>(tp, gp, u0, lam, U0, U1, U2);
+            else HV::template metric_tlast<false>(tp, gp, u0, lam, U0, U1, U2);
+            after_metric();
+            HV::t1_first(tp, U0, U1, U2);
+            MV::back(tp, U2, nullptr, U0);
+        } else {
+            MV::front(tp, U1, U2, U1);
+            HV::last_grad1(tp, U1, U0, U2);
+            HV::grad_rest(tp, U0, U1);
+            if (a.geo_pp) HV::template metric_tlast<true>(tp, gp, u0, lam, U0, U2, U1);
+            else HV::template metric_tlast<false>(tp, gp, u0, lam, U0, U2, U1);
+            after_metric();
+            HV::tmid(tp, U0, U1);
+            HV::t1_first(tp, U0, U2, U1);
+            MV::back(tp, U1, U2, U0);
+        }
+        if constexpr (TENSOR) { if (a.nodal) nodal_pairs<SH, N, V, EPU, NT, S>(U0, false); }
+        gstore_pair<T, M, S, NT>(reinterpret_cast<T *>(fout), e0, ne, U0);
     } else {  // OP_HELM, FP32 / BF16: fused register-blocked pencils
         const A lam = A(a.lambda);
         if (!staged) {  // otherwise the caller has already put the coefficients in B1
@@ -1432,8 +1617,9 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 // (for EPB a multiple of 32: whole 32-element chunks of the interleaved
 // layout) is bulk-prefetched into L2 one group ahead (the first group's at
 // the start, each next group's once the current group's metric stage is
-// done), so the metric stage finds it there; the autotuner decides whether
-// that pays.  Groups whose copy would not be 16-byte aligned, and the ragged
+// done), so the metric stage finds it there; with a.pf = 2 each group's own
+// metric is prefetched when the group starts (half the L2 footprint in
+// flight, half the lead time); the autotuner decides which pays.  Groups whose copy would not be 16-byte aligned, and the ragged
 // last group, are loaded with plain coalesced loads.
 // STAGE = false: no staging buffer (coefficients loaded by the group itself),
 // for groups whose buffers alone nearly fill shared memory.
@@ -1459,13 +1645,13 @@ constexpr int helm_tma_smem()
     return C::SMEM + (STAGE ? ((C::EPB * C::M * (int)sizeof(T) + 15) / 16) * 16 : 0);
 }
 
-template <int SH, int N, int Q, class T, int EPB_ = 0, bool STAGE = true, bool MULTI = false>
-__global__ void __launch_bounds__(Config<SH, N, Q, T, OP_HELM, EPB_>::NT,
+template <int SH, int N, int Q, class T, int EPB_ = 0, bool STAGE = true, bool MULTI = false, bool PAIR = false>
+__global__ void __launch_bounds__(Config<SH, N, Q, T, OP_HELM, EPB_, 0, PAIR>::NT,
                                   ctas_per_sm(helm_tma_smem<SH, N, Q, T, EPB_, STAGE>(),
-                                              Config<SH, N, Q, T, OP_HELM, EPB_>::NT))
+                                              Config<SH, N, Q, T, OP_HELM, EPB_, 0, PAIR>::NT))
     k_helm_tma(KArgs a, const __grid_constant__ TabP<typename CT<T>::type, layout(SH, N, Q).total> tp)
 {
-    using C = Config<SH, N, Q, T, OP_HELM, EPB_>;
+    using C = Config<SH, N, Q, T, OP_HELM, EPB_, 0, PAIR>;
     using A = typename C::A;
     static_assert(C::FUSED, "FP32/BF16 Helmholtz only");
     constexpr int EPB = C::EPB, NT = C::NT, M = C::M, S = C::S, NQ = C::NQ, NG = ngeo(SH);
@@ -1527,8 +1713,9 @@ __global__ void __launch_bounds__(Config<SH, N, Q, T, OP_HELM, EPB_>::NT,
         // CTA is resident in L2 at a time
         const long long gn = g + gridDim.x;
         auto prefetch_next = [&]() {
-            if (threadIdx.x == 0 && gn < ngroups) prefetch_metric(gn * EPB);
+            if (threadIdx.x == 0 && gn < ngroups && a.pf == 1) prefetch_metric(gn * EPB);
         };
+        if (a.pf == 2 && threadIdx.x == 0 && g != blockIdx.x) prefetch_metric(e0);  // this group's, now
         for (int f = 0; f < nf; ++f) {
             const bool staged = s_next != 0;
             if (staged) {
@@ -1536,19 +1723,27 @@ __global__ void __launch_bounds__(Config<SH, N, Q, T, OP_HELM, EPB_>::NT,
                 phase ^= 1u;
                 __syncthreads();
                 if (s_fail) return;  // every thread leaves together; the error word is set
-                A *B1 = buf + EPB * S;
-                for (int i = threadIdx.x; i < EPB * M; i += NT) {
-                    const int e = i / M, m = i - e * M;
-                    B1[e * S + m] = to_a(stage[i], A());
+                if constexpr (PAIR) {  // element pairs (2u, 2u+1) into one unit each
+                    F2 *B1 = reinterpret_cast<F2 *>(buf) + C::EPU * S;
+                    for (int i = threadIdx.x; i < C::EPU * M; i += NT) {
+                        const int u = i / M, m = i - u * M;
+                        B1[u * S + m] = F2(to_a(stage[2 * u * M + m], A()), to_a(stage[(2 * u + 1) * M + m], A()));
+                    }
+                } else {
+                    A *B1 = buf + EPB * S;
+                    for (int i = threadIdx.x; i < EPB * M; i += NT) {
+                        const int e = i / M, m = i - e * M;
+                        B1[e * S + m] = to_a(stage[i], A());
+                    }
                 }
             }
             __syncthreads();
             if (threadIdx.x == 0)  // stage is free again: the next field, or the next group's first
                 s_next = f + 1 < nf ? issue(g, f + 1) : issue(g + gridDim.x, 0);
-            run_group<SH, N, Q, T, OP_HELM, EPB_, 0>(a, field_in(a, f), field_out(a, f), ptab, tab, buf, e0, ne,
-                                                     staged, [&]() {
-                                                         if (f == 0) prefetch_next();
-                                                     });
+            run_group<SH, N, Q, T, OP_HELM, EPB_, 0, PAIR>(a, field_in(a, f), field_out(a, f), ptab, tab, buf, e0,
+                                                           ne, staged, [&]() {
+                                                               if (f == 0) prefetch_next();
+                                                           });
         }
     }
 }

@@ -515,17 +515,20 @@ extern "C" int nir_tune(nir_mesh *m, const char *cache_path)
                 // scratch here; an unknown variant falls back to 0
                 int &v = b->helm_variant[prec];
                 if (v == NIR_VARIANT_TOE && nir_toe_prepare(b, prec, b->helm_grid[prec]) != NIR_OK) v = 0;
-                if (v < 0 || v > NIR_VARIANT_TOE) v = 0;
+                if (v < 0 || v > NIR_VARIANT_MAX || (v != NIR_VARIANT_TOE &&
+                                                     !nir_kinfo(b->d.shape, b->d.P, prec, 5, v).fn))
+                    v = 0;
                 if (v != NIR_VARIANT_TOE) nir_toe_release(b);
                 continue;
             }
             float best = 1e30f;
             int bv = 0, bg = 0, bp = 0;
-            for (int v = 0; v < 4 && !rc; ++v) {
+            for (int v = 0; v <= NIR_VARIANT_MAX && !rc; ++v) {
+                if (v == NIR_VARIANT_TOE) continue;  // timed below
                 KInfo ki = nir_kinfo(b->d.shape, b->d.P, prec, 5, v);
                 if (!ki.fn || ((v == 1 || v == 2) && ki.epb == nir_kinfo(b->d.shape, b->d.P, prec, 5, 0).epb)) continue;
                 int occ = nir_occupancy(ctx, ki);
-                const int npf = (prec != NIR_F64 && b->geo_pp && (ki.epb % 32 == 0 || 32 % ki.epb == 0)) ? 2 : 1;
+                const int npf = (prec != NIR_F64 && b->geo_pp && (ki.epb % 32 == 0 || 32 % ki.epb == 0)) ? 3 : 1;
                 for (int c = 1; c <= std::max(1, occ) && !rc; ++c)
                     for (int pf = 0; pf < npf && !rc; ++pf) {
                         b->helm_variant[prec] = v;

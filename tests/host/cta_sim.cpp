@@ -22,7 +22,8 @@
 // per CTA instead).  Ops 0..5 as nirk::Op; prec 0 FP64, 1 FP32, 2 BF16;
 // variant 0 the default group, 1 half, 2 double (Helmholtz only), 3 the
 // persistent mesh kernel's form (fixed thread count, tables from shared
-// memory).  Environment: SIM_ORDER = fwd | rev | <shuffle seed>.
+// memory), 5 two elements per thread (FP32/BF16 Helmholtz, quad and hex).
+// Environment: SIM_ORDER = fwd | rev | <shuffle seed>.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <pthread.h>
@@ -105,6 +106,11 @@ static inline T __ldg(const T *p)
 {
     return *p;
 }
+template <class T>
+static inline T __ldcs(const T *p)
+{
+    return *p;
+}
 
 #include "nir_basis.h"
 #include "nir_kernels.cuh"
@@ -180,11 +186,11 @@ struct Input {
     double lambda;
 };
 
-template <int SH, int N, class T, int OP, int EPB_, int NT_, bool STAGE, bool MESH>
+template <int SH, int N, class T, int OP, int EPB_, int NT_, bool STAGE, bool MESH, bool PAIR = false>
 int run(const Input &in)
 {
     constexpr int Q = N + 1;
-    using C = Config<SH, N, Q, T, OP, EPB_, NT_>;
+    using C = Config<SH, N, Q, T, OP, EPB_, NT_, PAIR>;
     using A = typename C::A;
     constexpr int D = C::D, NQ = C::NQ, M = C::M, EPB = C::EPB, NT = C::NT, S = C::S;
     constexpr TabLayout L = layout(SH, N, Q);
@@ -292,16 +298,24 @@ int run(const Input &in)
                     const bool staged = s_next != 0;
                     if (staged) {
                         __syncthreads();  // the completed copy (the kernel's mbarrier wait)
-                        A *B1 = buf + EPB * S;
-                        for (int i = t; i < EPB * M; i += NT) {
-                            const int e = i / M, m = i - e * M;
-                            B1[e * S + m] = to_a(stage[i], A());
+                        if constexpr (PAIR) {
+                            F2 *B1 = reinterpret_cast<F2 *>(buf) + C::EPU * S;
+                            for (int i = t; i < C::EPU * M; i += NT) {
+                                const int u = i / M, m = i - u * M;
+                                B1[u * S + m] = F2(to_a(stage[2 * u * M + m], A()), to_a(stage[(2 * u + 1) * M + m], A()));
+                            }
+                        } else {
+                            A *B1 = buf + EPB * S;
+                            for (int i = t; i < EPB * M; i += NT) {
+                                const int e = i / M, m = i - e * M;
+                                B1[e * S + m] = to_a(stage[i], A());
+                            }
                         }
                     }
                     __syncthreads();
                     if (t == 0) s_next = f + 1 < nf ? issue(g, f + 1) : issue(g + 1, 0);
-                    run_group<SH, N, Q, T, OP, EPB_, NT_>(a, field_in(a, f), field_out(a, f), ptab, tab, buf, e0,
-                                                          ne, staged);
+                    run_group<SH, N, Q, T, OP, EPB_, NT_, PAIR>(a, field_in(a, f), field_out(a, f), ptab, tab, buf,
+                                                                e0, ne, staged);
                 }
             }
         } else {
@@ -356,6 +370,8 @@ int by_variant(int variant, const Input &in)
         if (variant == 1) return run<SH, N, T, OP, eh, 0, true, false>(in);
         if (variant == 2) return run<SH, N, T, OP, ed, 0, !fits_unstaged, false>(in);
         if (variant == 3) return run<SH, N, T, OP, 0, mesh_nt, true, true>(in);
+        if constexpr (C0::FUSED && (SH == QUAD || SH == HEX))
+            if (variant == 5) return run<SH, N, T, OP, 0, 0, true, false, true>(in);
     }
     return 4;
 }

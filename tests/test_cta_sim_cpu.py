@@ -251,12 +251,17 @@ def test_every_operator(sims, shape):
 @pytest.mark.parametrize("shape", list(SHAPES))
 def test_helmholtz_variants_fields_and_bf16(sims, shape):
     """The Helmholtz launch variants (half and double groups, the persistent
-    mesh kernel's form), three fields in one call, and BF16 storage."""
+    mesh kernel's form, two elements per thread on quads/hexes), three fields
+    in one call, and BF16 storage."""
     cases = [dict(shape=shape, P=P, op="helm", prec=prec, variant=v, orders=SHUFFLED)
              for prec in ("f64", "f32") for v in (1, 2, 3) for P in (2, 3)]
     cases += [dict(shape=shape, P=3, op="helm", prec=prec, nfields=3, orders=SHUFFLED)
               for prec in ("f64", "f32", "bf16")]
     cases += [dict(shape=shape, P=P, op=op, prec="bf16") for op in ("bwd", "iprod", "helm") for P in (1, 4)]
+    if shape in ("quad", "hex"):   # two elements per thread
+        cases += [dict(shape=shape, P=P, op="helm", prec=prec, variant=5, orders=SHUFFLED)
+                  for prec in ("f32", "bf16") for P in (1, 2, 3, 4)]
+        cases += [dict(shape=shape, P=3, op="helm", prec="f32", variant=5, nfields=3)]
     run_cases(sims, cases)
 
 
@@ -266,6 +271,8 @@ def test_per_element_factors_and_nodal_basis(sims, shape):
     cases = [dict(shape=shape, P=3, op=op, prec=prec, deformed=None) for op in OPS for prec in ("f64", "f32")]
     cases += [dict(shape=shape, P=P, op=op, prec=prec, nodal=1) for op in ("bwd", "iprod", "mass", "helm")
               for prec in ("f64", "f32") for P in (2, 4)]
+    cases += [dict(shape=shape, P=P, op="helm", prec="f32", variant=5, **kw)
+              for P in (2, 4) for kw in (dict(deformed=None), dict(nodal=1))]
     run_cases(sims, cases)
 
 

@@ -189,26 +189,35 @@ def test_low_precision_all_ops(nir, ctx, prec, shape, P):
                                      ("hex", 9), ("tet", 9)])
 def test_helmholtz_every_launch_variant(nir, ctx, prec, shape, P):
     """Every elements-per-CTA variant the tuner may pick (default, half, double;
-    for FP32/BF16 at P = 6 the double group runs without its staging buffer),
-    with and without the L2 metric prefetch and at two grid sizes."""
+    for FP32/BF16 at P = 6 the double group runs without its staging buffer;
+    FP32/BF16 quad/hex also two elements per thread), under every L2 metric
+    prefetch policy and at two grid sizes."""
     deformed = shape in ("hex", "quad")
     E = 300 if DIM[shape] == 2 else (150 if P <= 4 else 101)   # several groups of every variant + a ragged tail
     g, nodes, blk = setup(nir, ctx, shape, P, E, deformed)
     x = inputs(blk, "helm")
     ref = oracle_op(shape, P, g, nodes, "helm", x, 1.0)
-    for variant in (0, 1, 2, 3):
-        for pf in (0, 1):
+    paired = prec != "f64" and shape in ("hex", "quad")   # variant 5: two elements per thread
+    variants = (0, 1, 2, 3) + ((5,) if paired else ())
+    for variant in variants:
+        for pf in (0, 1, 2):
             for grid in (0, 152):
                 blk.set_tuning(prec, variant, grid, pf)
                 got = run_op(blk, "helm", prec, x, 1.0)
                 assert rel(got, ref) <= TOL[prec], (variant, pf, grid, rel(got, ref))
-    assert blk.get_tuning(prec) == (3, 152, 1)
+    assert blk.get_tuning(prec) == (variants[-1], 152, 2)
     blk.set_tuning(prec, 0, 0, 0)
     y0 = run_op(blk, "helm", prec, x, 1.0)
     blk.set_tuning(prec, 3, 0, 0)
     assert np.array_equal(run_op(blk, "helm", prec, x, 1.0), y0)   # same arithmetic, other allocation
-    with pytest.raises(nir.NirError):
-        blk.set_tuning(prec, 5)
+    if not paired:
+        with pytest.raises(nir.NirError) as ei:
+            blk.set_tuning(prec, 5)
+        assert ei.value.code == -2
+    for bad in (dict(variant=6), dict(variant=0, pf=3), dict(variant=0, pf=-1)):
+        with pytest.raises(nir.NirError) as ei:
+            blk.set_tuning(prec, **bad)
+        assert ei.value.code == -1
 
 
 @pytest.mark.parametrize("shape", ["quad", "tri", "hex", "prism", "tet"])
