@@ -300,12 +300,50 @@ def cpu_baseline(args, wl, budget_s: float = 15.0, y_gpu=None):
     return out
 
 
-def time_calls(fn, stream, reps: int) -> float:
-    """Seconds per call: CUDA events on the launching stream around `reps`
-    calls, after 3 untimed ones."""
+_FLUSH = {}
+
+
+def needs_flush(nbytes: int) -> bool:
+    """A step streaming less than twice the L2 could find part of its data
+    still in L2 from the previous step: such timings flush L2 in between."""
+    return nbytes < 2 * L2_BYTES
+
+
+def l2_flush(stream):
+    """Write a buffer of twice the L2 size on `stream` (evicts what the
+    previous launch left in L2)."""
+    import torch
+    dev = torch.cuda.current_device()
+    if dev not in _FLUSH:
+        _FLUSH[dev] = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    with torch.cuda.stream(stream):
+        _FLUSH[dev].fill_(1.0)
+
+
+def l2_note(nbytes: int) -> str:
+    mib = nbytes / 2 ** 20
+    if needs_flush(nbytes):
+        return f"flushed: {2 * L2_BYTES / 2**20:.0f} MiB written before each timed launch ({mib:.0f} MiB per step)"
+    return f"no flush: {mib:.0f} MiB streamed per step > 2 x 129 MiB L2"
+
+
+def time_calls(fn, stream, reps: int, nbytes: int = 0) -> float:
+    """Seconds per call: CUDA events on the launching stream, after 3 untimed
+    calls; around all `reps` calls, or, when the call streams less than twice
+    the L2 (`nbytes`), around each call with L2 flushed before it."""
     import torch
     for _ in range(3):
         fn()
+    if nbytes and needs_flush(nbytes):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            l2_flush(stream)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / reps * 1e-3
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record(stream)
@@ -356,11 +394,11 @@ def config_table(nir, ctx, dev, stream, peaks, fp64_peak, args):
         for prec in ("f64", "f32"):
             u = torch.from_numpy(u64).to(dev, nir.DTYPE[prec])
             y = torch.empty_like(u)
-            sec = time_calls(lambda: blk.helmholtz(u, prec=prec, out=y), stream, reps)
             wb = u.element_size()
-            rec[prec] = {"gdofs": E * blk.M / sec / 1e9, "ms_per_apply": sec * 1e3,
-                         "roofline": roofline_entry(prec, E * helm_flops_per_elem(shape, P + 1, Q),
-                                                    E * helm_bytes_per_elem(shape, P + 1, Q, wb, wl["deformed"]),
+            nb = E * helm_bytes_per_elem(shape, P + 1, Q, wb, wl["deformed"])
+            sec = time_calls(lambda: blk.helmholtz(u, prec=prec, out=y), stream, reps, nb)
+            rec[prec] = {"gdofs": E * blk.M / sec / 1e9, "ms_per_apply": sec * 1e3, "l2": l2_note(nb),
+                         "roofline": roofline_entry(prec, E * helm_flops_per_elem(shape, P + 1, Q), nb,
                                                     sec, fp64_peak, peaks),
                          "rel_error_vs_oracle": rel_err(y.double().cpu().numpy()[ids], y_or)}
         out[name] = rec
@@ -385,15 +423,16 @@ def config_table(nir, ctx, dev, stream, peaks, fp64_peak, args):
     for prec in ("f64", "f32"):
         x = torch.from_numpy(x64).to(dev, nir.DTYPE[prec])
         y = torch.empty_like(x)
-        sec = time_calls(lambda: mesh.helmholtz(x, prec=prec, out=y), stream, 20)
         wb = x.element_size()
         flops = sum(p["nodes"].shape[0] * helm_flops_per_elem(p["shape"], p["P"] + 1, p["Q"]) for p in parts)
         nbytes = sum(p["nodes"].shape[0] * helm_bytes_per_elem(p["shape"], p["P"] + 1, p["Q"], wb, p["deformed"])
                      for p in parts)
+        sec = time_calls(lambda: mesh.helmholtz(x, prec=prec, out=y), stream, 20, nbytes)
         yh = y.double().cpu().numpy()
         got = np.concatenate([yh[o:o + b.nelem * b.M].reshape(b.nelem, b.M)[ids].ravel() for o, b, ids, _ in samples])
         want = np.concatenate([r.ravel() for *_, r in samples])
         rec[prec] = {"gdofs": mesh.ndof / sec / 1e9, "ms_per_apply": sec * 1e3, "launch": mesh.get_launch(prec),
+                     "l2": l2_note(nbytes),
                      "roofline": roofline_entry(prec, flops, nbytes, sec, fp64_peak, peaks),
                      "rel_error_vs_oracle": rel_err(got, want)}
     out["hybrid150k_p2to8"] = rec
@@ -459,20 +498,23 @@ def run_nir(args, ws, rank, local):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier(ws)
     torch.cuda.synchronize()
+    flush = needs_flush(work_bytes)   # then L2 is flushed before each launch, outside its events
     with ClockSampler(local) as clk:
         t_all0 = torch.cuda.Event(enable_timing=True)
         t_all1 = torch.cuda.Event(enable_timing=True)
         t_all0.record(stream)
         for k in range(args.steps):
+            if flush:
+                l2_flush(stream)
             ev[k][0].record(stream)
             blk.helmholtz(u, lam=1.0, prec=args.prec, out=y)
             ev[k][1].record(stream)
         t_all1.record(stream)
         torch.cuda.synchronize()
         barrier(ws)
-    ms_total = t_all0.elapsed_time(t_all1)
-    ms_total = max_over_ranks(ws, ms_total, dev)
     per_launch = [a.elapsed_time(b) for a, b in ev]
+    ms_total = sum(per_launch) if flush else t_all0.elapsed_time(t_all1)
+    ms_total = max_over_ranks(ws, ms_total, dev)
     ms_step = ms_total / args.steps
     dof = E * M
     value = ws * dof * args.steps / (ms_total * 1e-3) / 1e9
@@ -522,16 +564,10 @@ def run_nir(args, ws, rank, local):
     if ws == 1 and not args.no_operators:
         us = [u, u.clone(), u.clone()]
         ys = [torch.empty_like(u) for _ in range(3)]
-        for _ in range(3):
-            blk.helmholtz_fields(us, lam=1.0, prec=args.prec, outs=ys)
-        fa, fb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        fa.record(stream)
-        for _ in range(args.steps):
-            blk.helmholtz_fields(us, lam=1.0, prec=args.prec, outs=ys)
-        fb.record(stream)
-        torch.cuda.synchronize()
-        fms = fa.elapsed_time(fb) / args.steps
-        fields = {"fields": 3, "ms_per_launch": fms, "gdofs": 3 * dof / (fms * 1e-3) / 1e9,
+        nb3 = work_bytes + 4 * E * M * wb   # two more fields in and out; the metric once
+        fms = time_calls(lambda: blk.helmholtz_fields(us, lam=1.0, prec=args.prec, outs=ys), stream, args.steps,
+                         nb3) * 1e3
+        fields = {"fields": 3, "ms_per_launch": fms, "gdofs": 3 * dof / (fms * 1e-3) / 1e9, "l2": l2_note(nb3),
                   "speedup_per_field_vs_single": (3 * dof / (fms * 1e-3)) / (dof / avg_launch_s)}
         del us, ys
     operators = {}
@@ -545,22 +581,15 @@ def run_nir(args, ws, rank, local):
                 continue
             up = u.to(nir.DTYPE[p])
             yp = torch.empty_like(up)
-            for _ in range(3):
-                blk.helmholtz(up, prec=p, out=yp)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            a.record(stream)
-            for _ in range(10):
-                blk.helmholtz(up, prec=p, out=yp)
-            b.record(stream)
-            torch.cuda.synchronize()
-            extras[f"{p}_apply_gdofs"] = dof / (a.elapsed_time(b) / 10 * 1e-3) / 1e9
+            nb = E * helm_bytes_per_elem(shape, P + 1, Q, up.element_size(), wl["deformed"])
+            sec = time_calls(lambda: blk.helmholtz(up, prec=p, out=yp), stream, 10, nb)
+            extras[f"{p}_apply_gdofs"] = dof / sec / 1e9
     line = {"metric": "Helmholtz apply GDOF/s", "value": value, "unit": "GDOF/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
             "config": dict(workload_config(args, wl), tuned=not args.no_tune,
                            strategy="threading over elements" if toe else "element groups per CTA",
-                           l2=f"no flush: {work_bytes / 2**20:.0f} MiB streamed per step > 129 MiB L2"),
+                           l2=l2_note(work_bytes)),
             "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk.summary(),
             "multi_field": fields,
             "kernel_ms_per_launch": statistics.mean(per_launch)}
@@ -601,18 +630,10 @@ def operator_table(blk, prec, dev, stream, wl, ctx, peaks, fp64_peak):
     }
     res = {}
     for op, fn in calls.items():
-        for _ in range(3):
-            fn()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        for _ in range(10):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        sec = a.elapsed_time(b) / 10 * 1e-3
         flops, byts = op_work_per_elem(op, N, Q, wb, wl["deformed"])
-        r = {"gdofs": E * M / sec / 1e9, "ms": sec * 1e3, "flops_per_elem": flops, "bytes_per_elem": byts}
+        sec = time_calls(fn, stream, 10, byts * E)
+        r = {"gdofs": E * M / sec / 1e9, "ms": sec * 1e3, "flops_per_elem": flops, "bytes_per_elem": byts,
+             "l2": l2_note(byts * E)}
         if prec == "f64" and fp64_peak:
             # FP64 on GB300: the ridge is ~0.19 flop/B, so every operator is FP64-pipe bound
             ach = flops * E / sec / 1e12
