@@ -310,20 +310,24 @@ def needs_flush(nbytes: int) -> bool:
 
 
 def l2_flush(stream):
-    """Write a buffer of twice the L2 size on `stream` (evicts what the
-    previous launch left in L2)."""
+    """Write a buffer of twice the L2 size on `stream` and read it back: what
+    the previous launch left in L2 is evicted, and the write-back of the
+    buffer's own dirty lines happens here rather than inside the next timed
+    launch (L2 then holds only clean lines of the buffer)."""
     import torch
     dev = torch.cuda.current_device()
     if dev not in _FLUSH:
         _FLUSH[dev] = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
     with torch.cuda.stream(stream):
         _FLUSH[dev].fill_(1.0)
+        _FLUSH[dev].sum()
 
 
 def l2_note(nbytes: int) -> str:
     mib = nbytes / 2 ** 20
     if needs_flush(nbytes):
-        return f"flushed: {2 * L2_BYTES / 2**20:.0f} MiB written before each timed launch ({mib:.0f} MiB per step)"
+        return (f"flushed: {2 * L2_BYTES / 2**20:.0f} MiB written and read back before each timed launch "
+                f"({mib:.0f} MiB per step)")
     return f"no flush: {mib:.0f} MiB streamed per step > 2 x 129 MiB L2"
 
 
