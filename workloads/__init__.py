@@ -226,6 +226,8 @@ def workload(name: str) -> dict:
         return dict(shape="pyr", P=4, Q=6, gorder=1, nodes=pyramid_split(20, 20, 20), deformed=False)
     if name == "hex48_curved_p6":
         return dict(shape="hex", P=6, Q=8, gorder=6, nodes=hex_grid(48, 6), deformed=True)
+    if name == "tet12_kuhn_p8":   # high-order tets (the sweep's weakest FP32 point), for profiling
+        return dict(shape="tet", P=8, Q=10, gorder=1, nodes=tet_kuhn(12), deformed=False)
     raise KeyError(name)
 
 
