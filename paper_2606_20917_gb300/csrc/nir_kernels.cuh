@@ -836,7 +836,7 @@ struct Config {
     static constexpr int D = dim(SH);
     static constexpr int NQ = npts(SH, Q);
     static constexpr int M = nmodes(SH, N);
-    static constexpr int S = odd_stride(NQ);
+    static constexpr int S0 = odd_stride(NQ);
     // the fused FP32/BF16 Helmholtz recomputes du/d eta3 in registers: 3 buffers
     static constexpr bool FUSED = (OP == OP_HELM && sizeof(A) == 4);
     static_assert(!PAIR || FUSED, "paired elements: FP32/BF16 Helmholtz only");
@@ -846,7 +846,7 @@ struct Config {
     // FP32/BF16 aim at >= 32 elements so a warp covers one structural index of
     // 32 elements (conflict-free with the odd stride); FP64 keeps ~110 KB.
     static constexpr int budget = sizeof(A) == 8 ? 110 * 1024 : 100 * 1024;
-    static constexpr int per_elem = NBUF * S * (int)sizeof(A);
+    static constexpr int per_elem = NBUF * S0 * (int)sizeof(A);
     static constexpr int raw = (budget - TABB) / per_elem;
     static constexpr int EPB_DEF = raw >= 64 ? 64 : raw >= 32 ? 32 : raw >= 16 ? 16 : raw >= 8 ? 8 : raw >= 4 ? 4
                                  : raw >= 2 ? 2 : 1;
@@ -855,6 +855,14 @@ struct Config {
     // work units per group: elements, or element pairs (a pair's values are
     // adjacent, at the unit's index, so one 8-byte access serves both)
     static constexpr int EPU = PAIR ? EPB / 2 : EPB;
+    // Per-unit stride of the group buffers.  Odd, so that one structural index of 32 units
+    // spans the 32 banks.  With fewer units per group a warp's items span KW = 32 / EPU
+    // structural indices; the fused FP32/BF16 stages then take S = KW (mod 32), so that units
+    // e and neighbouring indices s (an odd step apart) land on distinct banks: e S + s covers
+    // 0..31 once (P = 6 hexes: 16 elements per group, +13 %).  Paired units (8 bytes) and FP64
+    // keep the odd stride.
+    static constexpr int KW = EPU < 32 ? 32 / EPU : 1;
+    static constexpr int S = (FUSED && !PAIR && KW > 1) ? S0 + ((KW - S0 % 32) % 32 + 32) % 32 : S0;
     // Threads: 256 (up to 512 for the fused FP32/BF16 Helmholtz): the fused
     // stages have Q^2 (3-D) or Q (2-D) pencils per element, and the CTA is
     // sized so that its heaviest stages run in whole rounds (two, or more when
