@@ -50,9 +50,13 @@
 #define NIR_ZERO(v) ((v) = 0)
 #endif
 
-// Loads of the metric: read once per apply, so streamed with the evict-first
-// policy (the L2 then keeps the prefetched groups rather than consumed ones).
-#define NIR_METRIC_LD __ldcs
+// Loads of the metric.  Read once per apply; the paired-element form streams
+// them with the evict-first policy (the L2 then keeps prefetched groups rather
+// than consumed ones: 3-6 % on P = 4 hexes), while for the one-element form
+// that policy costs up to a quarter on high-order and collapsed shapes (tet
+// P = 8: 7.1 against 9.2 GDOF/s), so it keeps plain read-only loads.
+#define NIR_METRIC_LD __ldg
+#define NIR_METRIC_LD_PAIR __ldcs
 
 namespace nirk {
 
@@ -131,6 +135,37 @@ __device__ __forceinline__ void sfor(F &&f)
 }
 
 constexpr int odd_stride(int n) { return (n % 2 == 0) ? n + 1 : n; }
+
+// Shared-memory bank degree of one warp's 4-byte accesses when its items are
+// units e < epu at kw neighbouring structural indices c apart: the most
+// addresses e * S + c * s that fall on one of the 32 banks.
+constexpr int bank_ways(int S, int c, int epu, int kw)
+{
+    int cnt[32] = {};
+    int worst = 0;
+    for (int e = 0; e < epu; ++e)
+        for (int s = 0; s < kw; ++s) {
+            const int b = (e * S + c * s) % 32;
+            if (++cnt[b] > worst) worst = cnt[b];
+        }
+    return worst;
+}
+
+// The per-unit stride in [s0, s0 + 32) with the least summed bank degree over
+// the steps the stages take between neighbouring items: 1, N (modal lines) and
+// Q (point lines); the smallest such stride on ties.
+constexpr int pick_stride(int s0, int epu, int kw, int n, int q)
+{
+    int best = s0, bw = 1 << 30;
+    for (int d = 0; d < 32; ++d) {
+        const int w = bank_ways(s0 + d, 1, epu, kw) + bank_ways(s0 + d, n, epu, kw) + bank_ways(s0 + d, q, epu, kw);
+        if (w < bw) {
+            bw = w;
+            best = s0 + d;
+        }
+    }
+    return best;
+}
 
 // One pencil stage over EPB * per_e work items.  out_o = sum_r T(o,r) x_r
 // (+ sum_r TX(r) xx_r when o == OEX).  `rot` rotates the thread->item map so
@@ -788,18 +823,18 @@ struct GeoPair {
   private:
     static __device__ __forceinline__ void load8(const float *p, float (&v)[8])
     {
-        const float4 a = NIR_METRIC_LD(reinterpret_cast<const float4 *>(p));
-        const float4 b = NIR_METRIC_LD(reinterpret_cast<const float4 *>(p) + 1);
+        const float4 a = NIR_METRIC_LD_PAIR(reinterpret_cast<const float4 *>(p));
+        const float4 b = NIR_METRIC_LD_PAIR(reinterpret_cast<const float4 *>(p) + 1);
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
     }
     static __device__ __forceinline__ void load4(const float *p, float (&v)[4])
     {
-        const float4 a = NIR_METRIC_LD(reinterpret_cast<const float4 *>(p));
+        const float4 a = NIR_METRIC_LD_PAIR(reinterpret_cast<const float4 *>(p));
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
     }
     static __device__ __forceinline__ void load2(const float *p, float (&v)[2])
     {
-        const float2 a = NIR_METRIC_LD(reinterpret_cast<const float2 *>(p));
+        const float2 a = NIR_METRIC_LD_PAIR(reinterpret_cast<const float2 *>(p));
         v[0] = a.x; v[1] = a.y;
     }
     static __device__ __forceinline__ void unpack2(unsigned w, float &a, float &b)
@@ -810,17 +845,17 @@ struct GeoPair {
     }
     static __device__ __forceinline__ void load8(const __nv_bfloat16 *p, float (&v)[8])
     {
-        const uint4 a = NIR_METRIC_LD(reinterpret_cast<const uint4 *>(p));
+        const uint4 a = NIR_METRIC_LD_PAIR(reinterpret_cast<const uint4 *>(p));
         unpack2(a.x, v[0], v[1]); unpack2(a.y, v[2], v[3]); unpack2(a.z, v[4], v[5]); unpack2(a.w, v[6], v[7]);
     }
     static __device__ __forceinline__ void load4(const __nv_bfloat16 *p, float (&v)[4])
     {
-        const uint2 a = NIR_METRIC_LD(reinterpret_cast<const uint2 *>(p));
+        const uint2 a = NIR_METRIC_LD_PAIR(reinterpret_cast<const uint2 *>(p));
         unpack2(a.x, v[0], v[1]); unpack2(a.y, v[2], v[3]);
     }
     static __device__ __forceinline__ void load2(const __nv_bfloat16 *p, float (&v)[2])
     {
-        unpack2(NIR_METRIC_LD(reinterpret_cast<const unsigned *>(p)), v[0], v[1]);
+        unpack2(NIR_METRIC_LD_PAIR(reinterpret_cast<const unsigned *>(p)), v[0], v[1]);
     }
     template <int K> static __device__ __forceinline__ void load8(const double *, float (&)[K]) {}
     template <int K> static __device__ __forceinline__ void load4(const double *, float (&)[K]) {}
@@ -857,12 +892,12 @@ struct Config {
     static constexpr int EPU = PAIR ? EPB / 2 : EPB;
     // Per-unit stride of the group buffers.  Odd, so that one structural index of 32 units
     // spans the 32 banks.  With fewer units per group a warp's items span KW = 32 / EPU
-    // structural indices; the fused FP32/BF16 stages then take S = KW (mod 32), so that units
-    // e and neighbouring indices s (an odd step apart) land on distinct banks: e S + s covers
-    // 0..31 once (P = 6 hexes: 16 elements per group, +13 %).  Paired units (8 bytes) and FP64
-    // keep the odd stride.
+    // structural indices, and no single stride keeps every stage's neighbours on distinct
+    // banks: the fused FP32/BF16 stages take the stride with the least summed bank degree
+    // over their neighbour steps (pick_stride; P = 6 hexes: 16 elements per group, +13 %).
+    // Paired units (8 bytes) and FP64 keep the odd stride.
     static constexpr int KW = EPU < 32 ? 32 / EPU : 1;
-    static constexpr int S = (FUSED && !PAIR && KW > 1) ? S0 + ((KW - S0 % 32) % 32 + 32) % 32 : S0;
+    static constexpr int S = (FUSED && !PAIR && KW > 1) ? pick_stride(S0, EPU, KW, N, Q) : S0;
     // Threads: 256 (up to 512 for the fused FP32/BF16 Helmholtz): the fused
     // stages have Q^2 (3-D) or Q (2-D) pencils per element, and the CTA is
     // sized so that its heaviest stages run in whole rounds (two, or more when
