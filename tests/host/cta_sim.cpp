@@ -385,8 +385,14 @@ int by_n(int P, int variant, const Input &in)
     case 4: return by_variant<SH, 4, T, OP>(variant, in);
     case 5: return by_variant<SH, 5, T, OP>(variant, in);
 #ifdef SIM_HIGH_P
-    case 7: return by_variant<SH, 7, T, OP>(variant, in);
-    case 10: return by_variant<SH, 10, T, OP>(variant, in);
+    // high orders for the Helmholtz only (groups of 4 to 16 elements: the strides
+    // chosen for small groups)
+    case 7:
+        if constexpr (OP == OP_HELM) return by_variant<SH, 7, T, OP>(variant, in);
+        else return 4;
+    case 10:
+        if constexpr (OP == OP_HELM) return by_variant<SH, 10, T, OP>(variant, in);
+        else return 4;
 #endif
     default: return 4;
     }

@@ -52,7 +52,7 @@ def sims(tmp_path_factory):
     def build(shape):
         exe = str(out / f"cta_{shape}")
         cmd = [gxx, "-O0", "-g1", "-std=c++17", "-w", "-fno-omit-frame-pointer", "-fsanitize=address",
-               f"-DSIM_SHAPE={SHAPES[shape]}", "-I", CUDA_INC, "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+               "-DSIM_HIGH_P", f"-DSIM_SHAPE={SHAPES[shape]}", "-I", CUDA_INC, "-I", CSRC, "-I", os.path.join(ROOT, "include"),
                os.path.join(ROOT, "tests", "host", "cta_sim.cpp"), os.path.join(CSRC, "nir_basis.cpp"),
                "-o", exe, "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -262,6 +262,17 @@ def test_helmholtz_variants_fields_and_bf16(sims, shape):
         cases += [dict(shape=shape, P=P, op="helm", prec=prec, variant=5, orders=SHUFFLED)
                   for prec in ("f32", "bf16") for P in (1, 2, 3, 4)]
         cases += [dict(shape=shape, P=3, op="helm", prec="f32", variant=5, nfields=3)]
+    run_cases(sims, cases)
+
+
+@pytest.mark.parametrize("shape", list(SHAPES))
+def test_high_order_helmholtz(sims, shape):
+    """P = 6 and 9: groups of 4 to 16 elements, whose buffer strides are chosen
+    for the warp's bank mapping, every launch variant in FP32, the default one
+    in BF16 and FP64."""
+    variants = (0, 1, 2, 3) + ((5,) if shape in ("quad", "hex") else ())
+    cases = [dict(shape=shape, P=P, op="helm", prec="f32", variant=v) for P in (6, 9) for v in variants]
+    cases += [dict(shape=shape, P=P, op="helm", prec=prec) for P in (6, 9) for prec in ("bf16", "f64")]
     run_cases(sims, cases)
 
 
