@@ -18,8 +18,8 @@
 //
 // argv: shape P op prec variant.  stdin: E geo_pp lambda nodal nfields, then
 // the metric (geo_pp: [E][Nq][NG], else [E][NG]) and the inputs; stdout: the
-// outputs (E = 0: prints the configuration's elements per group and threads
-// per CTA instead).  Ops 0..5 as nirk::Op; prec 0 FP64, 1 FP32, 2 BF16;
+// outputs (E = 0: prints the configuration's elements per group, threads per
+// CTA, per-unit buffer stride and units per group instead).  Ops 0..5 as nirk::Op; prec 0 FP64, 1 FP32, 2 BF16;
 // variant 0 the default group, 1 half, 2 double (Helmholtz only), 3 the
 // persistent mesh kernel's form (fixed thread count, tables from shared
 // memory), 5 two elements per thread (FP32/BF16 Helmholtz, quad and hex).
@@ -197,8 +197,8 @@ int run(const Input &in)
     constexpr int NG = (OP == OP_PHYSDERIV || OP == OP_IPROD_DERIV) ? nlam(SH) : ngeo(SH);
     constexpr bool PACK = sizeof(T) < 8 && NG == ngeo(SH);
     constexpr bool FUSED = C::FUSED && !MESH;
-    if (in.E == 0) {  // query: the group size and thread count of this configuration
-        std::printf("%d %d\n", EPB, NT);
+    if (in.E == 0) {  // query: group size, threads per CTA, unit stride, units per group
+        std::printf("%d %d %d %d\n", EPB, NT, S, C::EPU);
         return 0;
     }
     const long long E = in.E;

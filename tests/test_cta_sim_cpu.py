@@ -215,7 +215,7 @@ def check(sims, shape, P, op, prec, variant=0, deformed=True, nfields=1, lam=1.3
     """Run one case in every order; returns the relative error against the oracle
     (asserting bit-identical results across orders and the tolerance)."""
     exe = sims[shape]
-    epb, _ = run_sim(exe, shape, P, op, prec, variant, 0, 1, lam, 0, [], None)
+    epb = run_sim(exe, shape, P, op, prec, variant, 0, 1, lam, 0, [], None)[0]
     E, pp, metric, fields, ref = case(shape, P, op, prec, variant, deformed, nfields, lam, seed, epb, nodal)
     ys = [run_sim(exe, shape, P, op, prec, variant, E, pp, lam, nodal, fields, metric, order=o, env=env)
           for o in orders]
@@ -285,6 +285,40 @@ def test_per_element_factors_and_nodal_basis(sims, shape):
     cases += [dict(shape=shape, P=P, op="helm", prec="f32", variant=5, **kw)
               for P in (2, 4) for kw in (dict(deformed=None), dict(nodal=1))]
     run_cases(sims, cases)
+
+
+def bank_degree(S, step, units, kw):
+    """Most 4-byte addresses u*S + step*s (u < units, s < kw) on one of 32 banks."""
+    cnt = [0] * 32
+    for u in range(units):
+        for s in range(kw):
+            cnt[(u * S + step * s) % 32] += 1
+    return max(cnt)
+
+
+@pytest.mark.parametrize("shape", list(SHAPES))
+def test_buffer_strides(sims, shape):
+    """The per-unit stride of every FP32 Helmholtz group size at P = 1..4, 6, 9:
+    odd (one structural index of 32 units covers the banks) for groups of 32 or
+    more units; otherwise within 32 of the odd stride and no worse than it over
+    the neighbour steps 1, N and Q (recounted here), and never below the
+    points per element.  Paired units keep the odd stride."""
+    seen = 0
+    for P in (1, 2, 3, 4, 6, 9):
+        N, Q = P + 1, P + 2
+        nq = orc.num_points(shape, Q)
+        s0 = nq + 1 if nq % 2 == 0 else nq
+        for v in (0, 1, 2) + ((5,) if shape in ("quad", "hex") else ()):
+            epb, nt, S, epu = run_sim(sims[shape], shape, P, "helm", "f32", v, 0, 1, 1.0, 0, [], None)
+            assert S >= nq and nt % 32 == 0
+            if epu >= 32 or v == 5:
+                assert S == s0, (P, v, S)
+                continue
+            kw = 32 // epu
+            cost = lambda x: sum(bank_degree(x, st, epu, kw) for st in (1, N, Q))
+            assert s0 <= S < s0 + 32 and cost(S) <= cost(s0), (P, v, S, cost(S), cost(s0))
+            seen += 1
+    assert seen > 0 or orc.dim(shape) == 2   # 2-D groups hold 32 or more elements
 
 
 @pytest.mark.parametrize("shape,op,prec,variant", [("hex", "helm", "f32", 0), ("hex", "helm", "f32", 3),
