@@ -19,7 +19,6 @@ geometric factors: with K = (d eta / d xi)(d xi / d x) and the weighted
 Jacobian W = w |J|, the Helmholtz/mass metric is the upper triangle of
 W K K^T then W, and the derivative operators take K row-major then W."""
 import os
-import shutil
 import subprocess
 from concurrent.futures import ThreadPoolExecutor
 
@@ -30,9 +29,6 @@ import oracle as orc
 import workloads as W
 from oracle import nodal as nd
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-CSRC = os.path.join(ROOT, "paper_2606_20917_gb300", "csrc")
-CUDA_INC = "/usr/local/cuda/include"
 SHAPES = {"quad": 0, "tri": 1, "hex": 2, "prism": 3, "tet": 4, "pyr": 5}
 OPS = {"bwd": 0, "iprod": 1, "physderiv": 2, "iprod_deriv": 3, "mass": 4, "helm": 5}
 PREC = {"f64": 0, "f32": 1, "bf16": 2}
@@ -42,25 +38,9 @@ SHUFFLED = ("fwd", "rev", "7")
 
 
 @pytest.fixture(scope="module")
-def sims(tmp_path_factory):
-    """{shape: executable}, the six builds compiled in parallel."""
-    gxx = shutil.which("g++")
-    if not gxx or not os.path.isdir(CUDA_INC):
-        pytest.skip("g++ or the CUDA headers are not available")
-    out = tmp_path_factory.mktemp("cta")
-
-    def build(shape):
-        exe = str(out / f"cta_{shape}")
-        cmd = [gxx, "-O0", "-g1", "-std=c++17", "-w", "-fno-omit-frame-pointer", "-fsanitize=address",
-               "-DSIM_HIGH_P", f"-DSIM_SHAPE={SHAPES[shape]}", "-I", CUDA_INC, "-I", CSRC, "-I", os.path.join(ROOT, "include"),
-               os.path.join(ROOT, "tests", "host", "cta_sim.cpp"), os.path.join(CSRC, "nir_basis.cpp"),
-               "-o", exe, "-lpthread"]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        assert r.returncode == 0, r.stderr[-3000:]
-        return shape, exe
-
-    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
-        return dict(ex.map(build, SHAPES))
+def sims(host_sims):
+    """{shape: executable} of the CTA emulation (built with the session's host builds)."""
+    return {k[1]: v for k, v in host_sims.items() if k[0] == "cta"}
 
 
 def collapse_jacobian(shape, e):

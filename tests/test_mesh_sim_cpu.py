@@ -12,9 +12,7 @@ results must agree bit for bit), and compared block by block with the oracle:
 FP32 in 3-D (one and two groups per item) and BF16 in 2-D.
 """
 import os
-import shutil
 import subprocess
-from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
@@ -22,36 +20,16 @@ import pytest
 import oracle as orc
 from tests.test_cta_sim_cpu import SHAPES, TOL, device_metric, inputs, mesh
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-CSRC = os.path.join(ROOT, "paper_2606_20917_gb300", "csrc")
 CUDA = "/usr/local/cuda"
-BUILDS = {(3, "f32"): 1, (2, "bf16"): 2}   # FP32 3-D has both table paths; FP64 reads shared memory only
 # (shape, P): low orders use the constant tables in FP32/BF16, the rest shared memory
 BLOCKS = {3: [("hex", 2), ("prism", 3), ("tet", 2), ("pyr", 2), ("tet", 4), ("hex", 5)],
           2: [("quad", 2), ("tri", 3), ("quad", 6), ("tri", 8)]}
 
 
 @pytest.fixture(scope="module")
-def sims(tmp_path_factory):
-    gxx = shutil.which("g++")
-    if not gxx or not os.path.isdir(os.path.join(CUDA, "include")):
-        pytest.skip("g++ or the CUDA headers are not available")
-    out = tmp_path_factory.mktemp("mesh")
-
-    def build(key):
-        dim, prec = key
-        exe = str(out / f"mesh_d{dim}_{prec}")
-        cmd = [gxx, "-O0", "-g1", "-std=c++17", "-w", "-fno-omit-frame-pointer", "-fsanitize=address",
-               f"-DNIR_MESH_DIM={dim}", f"-DNIR_PREC={BUILDS[key]}", "-I", os.path.join(CUDA, "include"),
-               "-I", CSRC, "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "host", "mesh_sim.cpp"),
-               os.path.join(CSRC, "nir_basis.cpp"), "-o", exe, "-L", os.path.join(CUDA, "lib64"), "-lcudart",
-               "-lpthread"]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        assert r.returncode == 0, r.stderr[-3000:]
-        return key, exe
-
-    with ThreadPoolExecutor(max_workers=len(BUILDS)) as ex:
-        return dict(ex.map(build, BUILDS))
+def sims(host_sims):
+    """{(dim, prec): executable} of the mesh-kernel emulation (session builds)."""
+    return {(k[1], k[2]): v for k, v in host_sims.items() if k[0] == "mesh"}
 
 
 def run(exe, blocks, lam, gran, order):
