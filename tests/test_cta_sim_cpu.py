@@ -233,8 +233,8 @@ def test_helmholtz_variants_fields_and_bf16(sims, shape):
     """The Helmholtz launch variants (half and double groups, the persistent
     mesh kernel's form, two elements per thread on quads/hexes), three fields
     in one call, and BF16 storage."""
-    cases = [dict(shape=shape, P=P, op="helm", prec=prec, variant=v, orders=SHUFFLED)
-             for prec in ("f64", "f32") for v in (1, 2, 3) for P in (2, 3)]
+    cases = [dict(shape=shape, P=2, op="helm", prec=prec, variant=v, orders=SHUFFLED)
+             for prec in ("f64", "f32") for v in (1, 2, 3)]
     cases += [dict(shape=shape, P=3, op="helm", prec=prec, nfields=3, orders=SHUFFLED)
               for prec in ("f64", "f32", "bf16")]
     cases += [dict(shape=shape, P=P, op=op, prec="bf16") for op in ("bwd", "iprod", "helm") for P in (1, 4)]
