@@ -26,7 +26,8 @@ def orc():
 # Host emulations of the kernels (tests/host/*.cpp), compiled once per session
 # and all at once: AddressSanitizer builds of the CTA emulation (one per shape),
 # the persistent mesh kernel (per dimension and precision), the
-# threading-over-elements kernel (per shape) and the CG vector kernels.
+# threading-over-elements kernel (per shape), the CG vector kernels and the
+# geometric-factor kernel.
 CSRC = os.path.join(ROOT, "paper_2606_20917_gb300", "csrc")
 CUDA = "/usr/local/cuda"
 HOST_BUILDS = {}
@@ -35,6 +36,7 @@ for _name, _sh in (("quad", 0), ("tri", 1), ("hex", 2), ("prism", 3), ("tet", 4)
     if _name != "pyr":
         HOST_BUILDS[("toe", _name)] = ("toe_sim.cpp", [f"-DSIM_SHAPE={_sh}"], [])
 HOST_BUILDS[("cg",)] = ("cg_sim.cpp", ["-ffp-contract=off"], ["-L", os.path.join(CUDA, "lib64"), "-lcudart"])
+HOST_BUILDS[("geom",)] = ("geom_sim.cpp", [], [])
 for _dim, _prec, _code in ((3, "f32", 1), (2, "bf16", 2)):
     HOST_BUILDS[("mesh", _dim, _prec)] = ("mesh_sim.cpp", [f"-DNIR_MESH_DIM={_dim}", f"-DNIR_PREC={_code}"],
                                           ["-L", os.path.join(CUDA, "lib64"), "-lcudart"])
@@ -60,6 +62,6 @@ def host_sims(tmp_path_factory):
         return key, exe
 
     # the slowest builds first
-    keys = sorted(HOST_BUILDS, key=lambda k: {"cta": 0, "mesh": 1, "toe": 2, "cg": 3}[k[0]])
+    keys = sorted(HOST_BUILDS, key=lambda k: {"cta": 0, "mesh": 1, "toe": 2, "cg": 3, "geom": 4}[k[0]])
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
         return dict(ex.map(build, keys))
