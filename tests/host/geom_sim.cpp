@@ -11,7 +11,8 @@
 //
 // argv: shape P gorder pp.  stdin: E, then the nodes ([E][nodes per element][d]);
 // stdout: the metric per unit ([E][Nq or 1][NG]) then d eta/d x and W
-// ([E][Nq or 1][d*d + 1]), read back from the library's layouts.
+// ([E][Nq or 1][d*d + 1]), read back from the library's layouts; per point,
+// then the whole FP32 copy of the metric as k_pack_metric lays it out.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -108,5 +109,10 @@ int main(int argc, char **argv)
         for (int n = 0; n < per; ++n)
             for (int c = 0; c < nl; ++c)
                 std::printf("%.17g\n", pp ? Lam[(((e >> 5) * NQ + n) * nl + c) * 32 + (e & 31)] : Lam[e * nl + c]);
+    if (pp) {  // the FP32 copy the fused kernels read: packed by k_pack_metric, printed raw
+        std::vector<float> packed((size_t)units * ng, -1.0f);
+        nirk::k_pack_metric<float>(G.data(), packed.data(), epad / 32 * NQ, ng);  // one thread: the whole loop
+        for (float v : packed) std::printf("%.9g\n", (double)v);
+    }
     return 0;
 }

@@ -7,7 +7,8 @@ vertices of straight-sided simplices, prisms and pyramids, the pyramid's
 rational map included) to the per-point metric W K K^T and W and the
 derivative factors K and W, with K = (d eta / d xi)(d xi / d x) and W = w |J|;
 per element (times the reference weight at the points) for affine quads and
-hexes.  The same convention is what the kernel emulations of the other host
+hexes; and the FP32 copy packed by ``k_pack_metric`` against the packed layout
+restated here.  The same convention is what the kernel emulations of the other host
 tests are fed with (``device_metric``), so this ties them to the library's own
 geometry.  Outputs exactly sized (64-element padding as allocated by the
 library) under AddressSanitizer."""
@@ -43,10 +44,22 @@ def test_metric_matches_oracle_factors(sim, shape, P):
     geo = device_metric(shape, Q, g, nodes, "geo")
     lam = device_metric(shape, Q, g, nodes, "lam")
     out = run(sim, shape, P, g, 1, np.ascontiguousarray(nodes))
-    assert out.size == geo.size + lam.size
-    got_g, got_l = out[:geo.size].reshape(geo.shape), out[geo.size:].reshape(lam.shape)
+    epad, NQ, NG = (E + 63) // 64 * 64, geo.shape[1], geo.shape[2]
+    assert out.size == geo.size + lam.size + epad * NQ * NG
+    got_g, got_l = out[:geo.size].reshape(geo.shape), out[geo.size:geo.size + lam.size].reshape(lam.shape)
     assert np.abs(got_g - geo).max() <= 1e-12 * np.abs(geo).max(), np.abs(got_g - geo).max()
     assert np.abs(got_l - lam).max() <= 1e-12 * np.abs(lam).max(), np.abs(got_l - lam).max()
+    # the packed FP32 copy: per 32-element chunk and point, the elements' (G00 G01 G02 G11)
+    # quads, then their (G12 G22) pairs, then their W (2-D: one quad (G00 G01 G11 W))
+    packed = out[geo.size + lam.size:]
+    for e in range(E):
+        for n in range(NQ):
+            blk = ((e // 32) * NQ + n) * NG * 32
+            l = e % 32
+            offs = [l * 4 + c for c in range(4)] if NG == 4 else \
+                [l * 4 + c for c in range(4)] + [128 + l * 2, 128 + l * 2 + 1, 192 + l]
+            np.testing.assert_array_equal(packed[[blk + o for o in offs]].astype(np.float32),
+                                          got_g[e, n].astype(np.float32))
 
 
 @pytest.mark.parametrize("shape", ["quad", "hex"])
